@@ -1,0 +1,338 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test ties one oracle function to something other than itself: closed
+forms, the exact lattice Green's function, complex symmetry of the row-scaled
+operator, dense brute-force solves, the boundary-value-problem form of the
+transmission operators, the paper's printed index formulas, the m=1 special
+case, the naive O(m^2) superposition and a brute-force minimal-residual
+Krylov solution.  A plausible slip in the oracle (dropped term, wrong sign,
+wrong half-point or layer index, transposed ordering, wrong trace side) fails
+at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import fgmres, operator, partition, pml, subproblems, sweeping
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- PML profile
+
+def test_pml_profile_integral_and_edges():
+    """sigma integrates to C/3 over each PML (quadratic profile of Section 2),
+    vanishes on [eta, 1-eta] and reaches C/eta at the Dirichlet nodes."""
+    n, gamma, C = 255, 16, 20.0
+    g = pml.global_profile(n, gamma, C)
+    h, eta = 1.0 / (n + 1), gamma / (n + 1)
+    x = np.linspace(0.0, eta, 200001)
+    integral = np.trapezoid(g.sigma(x), x)
+    assert abs(integral - C / 3) < 1e-6 * C
+    assert np.allclose(g.sigma(np.array([0.0, 1.0])), C / eta)
+    inner = np.linspace(eta, 1 - eta, 101)
+    assert np.all(g.sigma(inner) == 0.0)
+    # s = (1 + i sigma/omega)^-1 has |s| <= 1 and Im s <= 0 where sigma > 0 (absorbing)
+    s = g.s(np.linspace(0, 1, 1001), 10.0)
+    assert np.all(np.abs(s) <= 1 + 1e-15) and np.all(s.imag <= 0)
+
+
+# ------------------------------------------------------------- operator A
+
+@pytest.mark.parametrize("dim,n", [(1, 40), (2, 12), (3, 6)])
+def test_operator_sine_eigenpairs_without_pml(dim, n):
+    """C = 0 (no PML), constant c: A sin-mode = lambda sin-mode with
+    lambda = -(4/h^2) sum_j sin^2(pi k_j h/2) + omega^2/c^2 (Dirichlet Laplacian)."""
+    omega, cval = 7.3, 1.3
+    h = 1.0 / (n + 1)
+    A = operator.helmholtz_matrix(dim, n, omega, np.full((n,) * dim, cval), 3, 0.0)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        ks = rng.integers(1, n + 1, size=dim)
+        xs = W.grid_nodes(n, dim)
+        mode = np.ones((n,) * dim)
+        lam = omega**2 / cval**2
+        for ax in range(dim):
+            mode = mode * np.sin(math.pi * ks[ax] * xs[ax])
+            lam -= 4.0 / h**2 * math.sin(math.pi * ks[ax] * h / 2) ** 2
+        y = (A @ mode.reshape(-1)).reshape(mode.shape)
+        assert np.allclose(y, lam * mode, rtol=1e-12, atol=1e-9 * abs(lam))
+
+
+def test_operator_1d_matches_lattice_greens_function():
+    """1D, constant c, PML on both ends: the solution of A u = delta_{i0}/h in the
+    physical region equals the free-space outgoing lattice Green's function
+    u_j = h e^{i theta |j-j0|} / (2 i sin theta), 2 cos theta = 2 - (omega h)^2,
+    up to the PML's reflection.  An amplifying (sign-flipped) PML or a wrong
+    scale fails this."""
+    n, gamma, C = 511, 24, 20.0
+    omega = 2 * math.pi * 16  # 32 points per wavelength
+    h = 1.0 / (n + 1)
+    A = operator.helmholtz_matrix(1, n, omega, np.ones(n), gamma, C)
+    j0 = 200
+    f = np.zeros(n, dtype=complex)
+    f[j0 - 1] = 1.0 / h
+    u = sp.linalg.spsolve(A.tocsc(), f)
+    theta = math.acos(1 - (omega * h) ** 2 / 2)
+    j = np.arange(1, n + 1)
+    exact = h * np.exp(1j * theta * np.abs(j - j0)) / (2j * math.sin(theta))
+    phys = (j >= gamma) & (j <= n + 1 - gamma)
+    err = np.max(np.abs(u[phys] - exact[phys])) / np.max(np.abs(exact))
+    assert err < 2e-3, err
+
+
+@pytest.mark.parametrize("dim,n", [(1, 30), (2, 14), (3, 7)])
+def test_row_scaled_operator_is_complex_symmetric(dim, n):
+    """Section 3.1, practical remark 4: dividing row (i1,..) by s_{i1} s_{i2}..
+    makes A complex symmetric (not Hermitian).  A misplaced half-point or a
+    mismatched coefficient breaks the symmetry."""
+    omega, gamma, C = 9.0, 3, 20.0
+    c = W.lens_velocity(n, dim) if dim > 1 else np.linspace(0.9, 1.2, n)
+    A = operator.helmholtz_matrix(dim, n, omega, c, gamma, C).toarray()
+    g = pml.global_profile(n, gamma, C)
+    s = g.s(np.arange(1, n + 1) / (n + 1), omega)
+    d = np.ones((n,) * dim, dtype=complex)
+    for ax in range(dim):
+        shape = [1] * dim
+        shape[dim - 1 - ax] = n
+        d = d * s.reshape(shape)
+    S = A / d.reshape(-1)[:, None]
+    assert np.allclose(S, S.T, rtol=0, atol=1e-12 * np.abs(S).max())
+    assert not np.allclose(S, S.conj().T, atol=1e-6 * np.abs(S).max())
+
+
+# ----------------------------------------------------------- partition
+
+def test_partition_matches_printed_index_formulas():
+    rows = [ln.split() for ln in open(os.path.join(GOLD, "partition_gamma3_b2_m4.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    part = partition.make_partition(12, 3, 2)
+    assert part.m == 4
+    for kind, p, lo, hi in rows:
+        L = part.layers[int(p) - 1]
+        got = {"X": (L.x_lo, L.x_hi), "M": (L.m_lo, L.m_hi), "R": (L.r_lo, L.r_hi),
+               "L": (L.l_lo, L.l_hi)}[kind]
+        assert got == (int(lo), int(hi)), (kind, p, got)
+
+
+def test_partition_experiment_layer_widths_and_remainder():
+    """Section 3.2: gamma=9, b=8 gives a leftmost layer of b+gamma-1 = 16 nodes.
+    Ragged case: the last layer absorbs the remainder and layers tile [1, n]."""
+    part = partition.make_partition(40, 9, 8)
+    L1 = part.layers[0]
+    assert L1.x_hi - L1.x_lo + 1 == 16
+    for n, gamma, b in [(127, 12, 4), (511, 16, 4), (1023, 20, 4), (95, 8, 4), (41, 5, 3)]:
+        part = partition.make_partition(n, gamma, b)
+        cover = []
+        for L in part.layers:
+            cover.extend(range(L.x_lo, L.x_hi + 1))
+        assert cover == list(range(1, n + 1))
+        P = n + 2 - 2 * gamma
+        assert part.m == P // b
+        last = part.layers[-1]
+        assert last.phys_hi - last.phys_lo + 1 == b + P - part.m * b
+
+
+# --------------------------------------------------------- subproblems
+
+def _small(dim, n, omega, gamma, b, vel="lens"):
+    P = W.small_problem(dim, n, omega, gamma, b, vel)
+    part = partition.make_partition(n, gamma, b)
+    return P, part
+
+
+@pytest.mark.parametrize("dim,n,gamma,b", [(1, 25, 4, 3), (2, 17, 4, 3), (3, 9, 3, 2)])
+def test_banded_lu_solve_matches_dense_solve(dim, n, gamma, b):
+    """Every subproblem: the banded LU (quasi-1D ordering, partial pivoting)
+    solves H v = g like a dense solve of H in the paper's natural ordering."""
+    omega = 2 * math.pi * 2.5
+    P, part = _small(dim, n, omega, gamma, b, "lens" if dim > 1 else "const")
+    rng = np.random.default_rng(1)
+    for p in range(1, part.m + 1):
+        for kind in ("M", "R", "L"):
+            if (kind == "R" and p == 1) or (kind == "L" and p == part.m):
+                continue
+            F = subproblems.factor_subproblem(dim, n, omega, P.c, gamma, P.C, part, p, kind)
+            Hn = subproblems.subproblem_matrix(dim, n, omega, P.c, gamma, P.C, part, p, kind)
+            g = rng.standard_normal((F.w, F.T)) + 1j * rng.standard_normal((F.w, F.T))
+            v = F.solve(g)
+            vd = np.linalg.solve(Hn.toarray(), g.reshape(-1)).reshape(g.shape)
+            assert np.allclose(v, vd, rtol=0, atol=1e-11 * np.abs(vd).max())
+
+
+def test_subproblems_without_pml_are_principal_submatrices():
+    """C = 0: H_q^M, H_p^R, H_p^L are the Dirichlet truncations of A to their
+    padded grids (same stencil, no auxiliary absorption)."""
+    n, gamma, b, omega = 15, 3, 2, 5.0
+    c = W.lens_velocity(n, 2)
+    part = partition.make_partition(n, gamma, b)
+    A = operator.helmholtz_matrix(2, n, omega, c, gamma, 0.0).toarray()
+    for p in range(1, part.m + 1):
+        L = part.layers[p - 1]
+        for kind, (lo, hi) in (("M", (L.m_lo, L.m_hi)), ("R", (L.r_lo, L.r_hi)),
+                               ("L", (L.l_lo, L.l_hi))):
+            H = subproblems.subproblem_matrix(2, n, omega, c, gamma, 0.0, part, p, kind).toarray()
+            idx = np.arange((lo - 1) * n, hi * n)
+            assert np.allclose(H, A[np.ix_(idx, idx)], atol=1e-9)
+
+
+def _bvp_solution(dim, n, omega, c, gamma, C, part, p, kind, w):
+    """Independent form of G~_p^R w / G~_p^L w: the boundary value problem of
+    Section 3.1 with v = w held on the boundary column (x2 = alpha_p - 1 for R,
+    beta_p + 1 for L), assembled on the grid extended by that column, and
+    solved densely."""
+    L = part.layers[p - 1]
+    lo, hi = (L.r_lo, L.r_hi) if kind == "R" else (L.l_lo, L.l_hi)
+    elo, ehi = (lo - 1, hi) if kind == "R" else (lo, hi + 1)
+    prof = partition.sweep_profile(part, p, kind, C)
+    # sweep-axis operator on the extended range, with the subproblem's profile
+    Ds = operator.second_difference(elo, ehi, n, prof, omega).toarray()
+    Dt = operator.transverse_operator(dim, n, gamma, C, omega).toarray()
+    T = n ** (dim - 1)
+    we = ehi - elo + 1
+    cc = np.asarray(c).reshape(n, T)[elo - 1:ehi]
+    K = np.kron(Ds, np.eye(T)) + np.kron(np.eye(we), Dt) + np.diag((omega**2 / cc**2).reshape(-1))
+    bcol = 0 if kind == "R" else we - 1
+    rows = np.arange(we * T).reshape(we, T)
+    K[rows[bcol]] = 0.0
+    K[rows[bcol], rows[bcol]] = 1.0
+    rhs = np.zeros(we * T, dtype=complex)
+    rhs[rows[bcol]] = w
+    v = np.linalg.solve(K, rhs).reshape(we, T)
+    inner = v[1:] if kind == "R" else v[:-1]
+    return inner[L.x_lo - lo: L.x_hi - lo + 1]
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_transmission_operators_solve_the_boundary_value_problem(dim):
+    """G~_p^R w (g = (-1/h^2)[w, 0, ...]) and G~_p^L w (g on the last column)
+    equal the restriction to X_p of the Helmholtz solution on D_p^R / D_p^L
+    with v = w on the left / right boundary and zero elsewhere (Section 3.1).
+    A wrong sign, scale or side of g fails this."""
+    n, gamma, b, omega, C = (30, 4, 3, 12.0, 20.0) if dim == 1 else (13, 3, 2, 9.0, 20.0)
+    c = np.linspace(0.9, 1.1, n) if dim == 1 else W.lens_velocity(n, 2)
+    part = partition.make_partition(n, gamma, b)
+    rng = np.random.default_rng(3)
+    T = n ** (dim - 1)
+    for p in range(2, part.m):
+        w = rng.standard_normal(T) + 1j * rng.standard_normal(T)
+        for kind, G in (("R", subproblems.G_R), ("L", subproblems.G_L)):
+            F = subproblems.factor_subproblem(dim, n, omega, c, gamma, C, part, p, kind)
+            z = G(F, w, part.h)
+            zb = _bvp_solution(dim, n, omega, c, gamma, C, part, p, kind, w)
+            assert np.allclose(z, zb, rtol=0, atol=1e-10 * np.abs(zb).max()), (kind, p)
+
+
+# ------------------------------------------------------ preconditioner
+
+@pytest.mark.parametrize("dim,n,gamma,b", [(1, 40, 4, 3), (2, 23, 4, 3), (3, 11, 3, 2)])
+def test_accumulated_sweep_equals_naive_superposition(dim, n, gamma, b):
+    """Section 2.2: accumulating boundary values gives exactly (by linearity)
+    the O(m^2) superposition u~_p = sum_q u~_{p,q} of Section 2.1."""
+    omega = 2 * math.pi * 2.0
+    P = W.small_problem(dim, n, omega, gamma, b, "lens" if dim > 1 else "const", nrhs=2)
+    pc = sweeping.Preconditioner(dim, n, omega, P.c, gamma, b, P.C)
+    assert pc.m >= 3
+    z1 = pc.apply(P.f)
+    z2 = pc.apply_naive(P.f)
+    assert np.linalg.norm(z1 - z2) <= 1e-12 * np.linalg.norm(z1)
+
+
+@pytest.mark.parametrize("dim,n", [(1, 20), (2, 11), (3, 7)])
+def test_single_layer_preconditioner_is_exact_inverse(dim, n):
+    """m = 1: X_1 is the whole grid with the boundary PML on both sides, so
+    H_1^M = A and the preconditioner is A^-1; FGMRES converges in 1 iteration."""
+    gamma, omega = 4, 6.0
+    b = n + 2 - 2 * gamma  # all physical nodes in one layer
+    c = W.lens_velocity(n, dim) if dim > 1 else np.ones(n)
+    pc = sweeping.Preconditioner(dim, n, omega, c, gamma, b)
+    assert pc.m == 1
+    A = operator.helmholtz_matrix(dim, n, omega, c, gamma, 20.0)
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal((n,) * dim) + 1j * rng.standard_normal((n,) * dim)
+    z = pc.apply(f)
+    ref = np.linalg.solve(A.toarray(), f.reshape(-1)).reshape(f.shape)
+    assert np.allclose(z, ref, atol=1e-11 * np.abs(ref).max())
+    u, its, res = fgmres.solve(pc, A, f[..., None], tol=1e-10)
+    assert its[0] == 1 and res[0] < 1e-10
+
+
+def test_preconditioner_approximates_the_green_operator():
+    """The sweeping preconditioner approximates A^-1 (Section 2: each piece is
+    an outgoing wave through absorbing layers): for constant c its error is far
+    below 1, while a wrong trace side or sweep direction gives O(1) error."""
+    n, gamma, b = 63, 8, 4
+    omega = (n + 1) * math.pi / 8
+    P = W.small_problem(2, n, omega, gamma, b, "const", nrhs=1)
+    pc = sweeping.Preconditioner(2, n, omega, P.c, gamma, b, P.C)
+    A = operator.helmholtz_matrix(2, n, omega, P.c, gamma, P.C)
+    f = P.f[..., 0]
+    u = sp.linalg.spsolve(A.tocsc(), f.reshape(-1)).reshape(f.shape)
+    z = pc.apply(f)
+    assert np.linalg.norm(z - u) / np.linalg.norm(u) < 0.05
+
+
+# --------------------------------------------------------------- FGMRES
+
+def test_fgmres_identity_preconditioner_is_minimal_residual():
+    """With M = I, FGMRES after k steps returns the minimal-residual vector of
+    the Krylov space span{f, Af, ..., A^{k-1} f}; compare with a brute-force
+    least-squares solve over an explicit (orthonormalised) Krylov basis."""
+    rng = np.random.default_rng(11)
+    N = 40
+    A = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N)) + 6 * np.eye(N)
+    f = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    for k in (1, 3, 7):
+        x, its, _ = fgmres.fgmres(lambda v: A @ v, lambda v: v, f, fixed_iters=k)
+        K = np.stack([np.linalg.matrix_power(A, j) @ f for j in range(k)], axis=1)
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(A @ Q, f, rcond=None)
+        xb = Q @ y
+        assert its == k
+        assert np.allclose(x, xb, atol=1e-10 * np.abs(xb).max())
+
+
+def test_fgmres_restart_and_convergence_against_dense_solve():
+    rng = np.random.default_rng(12)
+    N = 60
+    A = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N)) + 12 * np.eye(N)
+    f = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    x, its, hist = fgmres.fgmres(lambda v: A @ v, lambda v: v, f, tol=1e-10, restart=5, maxit=400)
+    ref = np.linalg.solve(A, f)
+    assert np.linalg.norm(A @ x - f) / np.linalg.norm(f) <= 1e-10 * 1.01
+    assert np.allclose(x, ref, atol=1e-8 * np.abs(ref).max())
+    assert its > 5  # needed at least one restart
+
+
+def test_preconditioned_solve_matches_direct_solve():
+    n, gamma, b = 31, 5, 3
+    omega = (n + 1) * math.pi / 8
+    P = W.small_problem(2, n, omega, gamma, b, "layered", nrhs=2)
+    pc = sweeping.Preconditioner(2, n, omega, P.c, gamma, b, P.C)
+    A = operator.helmholtz_matrix(2, n, omega, P.c, gamma, P.C)
+    u, its, res = fgmres.solve(pc, A, P.f, tol=1e-10)
+    for r in range(2):
+        ref = sp.linalg.spsolve(A.tocsc(), P.f[..., r].reshape(-1)).reshape(P.f.shape[:-1])
+        assert res[r] <= 1e-10 * 1.01
+        assert np.linalg.norm(u[..., r] - ref) / np.linalg.norm(ref) < 1e-7
+        assert its[r] <= 12
+
+
+def test_iteration_counts_small_and_nearly_frequency_independent():
+    """Soft check (Section 3.2, Tables 1-3): iteration counts stay small and
+    grow at most slowly with omega at a fixed number of points per wavelength."""
+    counts = []
+    for n in (63, 127, 255):
+        gamma = {63: 8, 127: 12, 255: 14}[n]
+        omega = (n + 1) * math.pi / 8
+        P = W.small_problem(2, n, omega, gamma, 4, "const", nrhs=1)
+        pc = sweeping.Preconditioner(2, n, omega, P.c, gamma, 4, P.C)
+        A = operator.helmholtz_matrix(2, n, omega, P.c, gamma, P.C)
+        _, its, res = fgmres.solve(pc, A, P.f, tol=1e-6)
+        counts.append(int(its[0]))
+        assert res[0] <= 1e-6
+    assert max(counts) <= 10 and max(counts) - min(counts) <= 3, counts
