@@ -1,0 +1,380 @@
+"""Benchmark: batched Helmholtz solves with the additive sweeping preconditioner.
+
+Workload (one step): the 2D n=1023 problem at omega = 128 pi (16 points per
+wavelength), 16 random smoothed horizontal velocity layers, PML 20 points,
+layers of b = 4 columns, 32 Gaussian point sources -- factor all 3m-2 = 736
+layer subproblems in complex64 (Algorithm 1, plus the dense trace-transfer
+maps of the two sweeps) and solve all 32 right-hand sides to a relative FP64
+residual of 1e-6 with right-preconditioned FGMRES(40) (Algorithm 2 as the
+preconditioner).  Metric: solves per second (right-hand sides solved per
+second of step time), whole job over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl asp|reference]
+
+N > 1 runs under torchrun, one independent replica per GPU (the path has no
+cross-GPU exchange: replicas only).  ``--impl reference`` times the CPU FP64
+oracle (test infrastructure) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s (2D n=1023, omega=128pi, 32 RHS, to 1e-6 FP64 residual)"
+UNIT = "solves/s"
+WORKLOAD = {"workload": "2d_helmholtz_n1023_layered_omega128pi_pml20_b4_32rhs", "n": 1023,
+            "omega": "128*pi", "pml": 20, "b": 4, "nrhs": 32, "velocity": "16 random layers, smoothed 3h",
+            "factor_precision": "complex64", "krylov": "FGMRES(40) FP64", "tol": 1e-6,
+            "l2": "no flush needed: factors 11.5 GB + transfer maps 4.1 GB exceed the 129 MB L2"}
+PHASES = ["factor", "tmap", "embed", "chain", "fill", "elementwise", "matvec", "krylov"]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self, device_index: int = 0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != device_index:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def _layer_widths(n, gamma, b):
+    P = n + 2 - 2 * gamma
+    m = P // b
+    r = P - m * b
+    wM = [2 * gamma + b - 2 + (r if q == m else 0) for q in range(1, m + 1)]
+    wR = [gamma + b - 1 + (r if q == m else 0) for q in range(2, m + 1)]
+    wL = [gamma + b - 1 for q in range(1, m)]
+    wT = [gamma + b - 1 for q in range(2, m)]  # maps exist for p = 2..m-1 (both kinds)
+    return m, wM, wR, wL, wT
+
+
+def algorithmic(n, gamma, b, nrhs, esz):
+    """Algorithmic bytes and flops per launch of each phase:
+    a banded solve reads its L and U band once, n*w*(2w+1) entries, and does
+    8*(2w+1) real flops per entry row per right-hand side."""
+    m, wM, wR, wL, wT = _layer_widths(n, gamma, b)
+    band = lambda ws: sum(n * w * (2 * w + 1) for w in ws)  # noqa: E731
+    N = n * n
+    vec = N * nrhs * esz
+    out = {}
+    out["embed"] = {"bytes": band(wM) * esz + 2 * vec, "flops": 8.0 * nrhs * band(wM)}
+    out["fill"] = {"bytes": (band(wR) + band(wL)) * esz + 2 * vec, "flops": 8.0 * nrhs * (band(wR) + band(wL))}
+    out["tmap"] = {"bytes": 2 * band(wT) * esz + 2 * len(wT) * n * n * esz,
+                   "flops": 2 * 8.0 * 1.5 * n * band(wT)}
+    out["chain"] = {"bytes": 2 * len(wT) * n * n * esz, "flops": 8.0 * nrhs * 2 * len(wT) * n * n}
+    out["factor"] = {"bytes": (band(wM) + band(wR) + band(wL)) * esz,
+                     "flops": 8.0 * n * sum(w ** 3 for w in wM + wR + wL)}
+    out["matvec"] = {"bytes": 2 * N * nrhs * 16 + N * 8, "flops": 8.0 * 5 * N * nrhs}
+    return out
+
+
+def _traffic_from_profile(kernel_phase):
+    """dram bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "btsolve_n1023_traffic.txt")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    except OSError:
+        return None
+    src = os.path.join(ROOT, "paper_1504_04058_gb300", "csrc", "btsolve.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if kv.get("btsolve_sha256_16") != sha:
+        return None
+    v = kv.get(f"{kernel_phase}_dram_bytes_per_launch")
+    return float(v) if v else None
+
+
+def run_asp(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_1504_04058_gb300 as asp
+    import workloads as W
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    P = W.problem_2d_n1023_layered(nrhs=32, seed=1504 + rank)
+    prm = asp.make_params(P.n, P.omega, P.pml, P.b, C=P.C, precision="c64", max_rhs=P.nrhs, restart=40)
+    h = asp.asp_setup(P.c, prm)
+    f_host = torch.from_numpy(P.f).pin_memory()
+    f = f_host.to(dev)
+    u = torch.empty_like(f)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h.factor()
+        _, info = h.gmres_solve(f, u, tol=P.tol, maxit=200)
+        return info
+
+    for _ in range(args.warmup):
+        info = step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    h.take_launch_count()
+    h.set_phase_timing(True)
+    h.phase_times()
+    clocks = ClockSampler()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    its = []
+    for _ in range(args.steps):
+        info = step()
+        its.append(max(i["iterations"] for i in info))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop(dev.index)
+    phases = h.phase_times()
+    h.set_phase_timing(False)
+    launches = h.take_launch_count()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        if world > 1:
+            torch.distributed.barrier()
+    conv = all(i["converged"] for i in info)
+    worst_res = max(i["rel_res_true"] for i in info)
+
+    # ---- factor-resident solve rate (serving: factors cached, solve only)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    h.gmres_solve(f, u, tol=P.tol, maxit=200)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    solve_ms = s0.elapsed_time(s1)
+
+    # ---- end to end through the public API with host buffers
+    u_host = torch.empty_like(f_host).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    for _ in range(e2e_steps):
+        f.copy_(f_host, non_blocking=True)
+        h.factor()
+        h.gmres_solve(f, u, tol=P.tol, maxit=200)
+        u_host.copy_(u, non_blocking=True)
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = x0.elapsed_time(x1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    nbytes = P.f.size * 16
+
+    # ---- roofline of the dominant kernel (live CUDA-event phase times)
+    peaks, peak_kind = _peaks()
+    alg = algorithmic(P.n, P.pml, P.b, P.nrhs, 8)
+    dom = max((p for p in PHASES if p in alg), key=lambda p: phases[p][0])
+    tot_ms, nl = phases[dom]
+    avg_ms = tot_ms / max(nl, 1)
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # TFLOP/s at max clock
+    if dom in ("embed", "fill", "tmap", "factor"):
+        ach = alg[dom]["flops"] / (avg_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "kernel": f"btsolve/btfactor ({dom})",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived, see DESIGN.md)"}
+    else:
+        ach = alg[dom]["bytes"] / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "kernel": dom, "peak_source": f"hbm_gbs ({peak_kind})"}
+    roof["traffic"] = _traffic_from_profile(dom)
+    roof["avg_launch_ms"] = avg_ms
+    roof["hbm_view"] = {"algorithmic_bytes": alg[dom]["bytes"],
+                        "GBps": alg[dom]["bytes"] / (avg_ms * 1e-3) / 1e9,
+                        "frac_of_measured_hbm": alg[dom]["bytes"] / (avg_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    phase_ms = {p: round(phases[p][0] / args.steps, 3) for p in PHASES}
+    value = world * P.nrhs / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 factors / f64 krylov", "data": "synthetic",
+        "config": dict(WORKLOAD, parallelism=f"replicas x{world}"),
+        "iterations_max": max(its), "converged": conv, "worst_rel_res_true": worst_res,
+        "solve_only_solves_per_s": world * P.nrhs / (solve_ms * 1e-3),
+        "phase_ms_per_step": phase_ms,
+        "e2e": {"value": world * P.nrhs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clk,
+    }
+    h.destroy()
+    return line
+
+
+def cpu_baseline_sample(iterations: int, threads: int = 1):
+    """Time the oracle as it stands on a bounded sample of the workload in a
+    child process (numpy/LAPACK limited to `threads` threads): factor and solve
+    2 subproblems of each kind plus one sparse matvec at n=1023, then scale to
+    one solve of the 32-right-hand-side batch with the given iteration count."""
+    code = r"""
+import json, math, sys, time
+sys.path.insert(0, %r)
+import numpy as np
+import workloads as W
+from oracle import operator, partition, subproblems
+P = W.problem_2d_n1023_layered(nrhs=1)
+part = partition.make_partition(P.n, P.pml, P.b)
+m = part.m
+rng = np.random.default_rng(0)
+t_fac = {"M": [], "R": [], "L": []}
+t_sol = {"M": [], "R": [], "L": []}
+for kind, ps in (("M", (1, m // 2)), ("R", (2, m // 2)), ("L", (m // 3, m - 1))):
+    for p in ps:
+        t0 = time.perf_counter()
+        F = subproblems.factor_subproblem(2, P.n, P.omega, P.c, P.pml, P.C, part, p, kind)
+        t1 = time.perf_counter()
+        g = rng.standard_normal((F.w, F.T)) + 0j
+        F.solve(g)
+        t2 = time.perf_counter()
+        t_fac[kind].append(t1 - t0); t_sol[kind].append(t2 - t1)
+A = operator.helmholtz_matrix(2, P.n, P.omega, P.c, P.pml, P.C)
+x = P.f[..., 0].reshape(-1)
+t0 = time.perf_counter(); A @ x; t_mv = time.perf_counter() - t0
+avg = lambda v: sum(v) / len(v)
+setup = m * avg(t_fac["M"]) + (m - 1) * (avg(t_fac["R"]) + avg(t_fac["L"]))
+apply1 = m * avg(t_sol["M"]) + (m - 1) * (avg(t_sol["R"]) + avg(t_sol["L"]))
+print(json.dumps({"setup_s": setup, "apply_s_per_rhs": apply1, "matvec_s_per_rhs": t_mv}))
+""" % ROOT
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    t0 = time.perf_counter()
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    wall = time.perf_counter() - t0
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": threads, "kind": "oracle", "error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    nrhs = 32
+    # one batch: factor once, then `iterations` applies + matvecs per right-hand side
+    t_batch = d["setup_s"] + nrhs * iterations * (d["apply_s_per_rhs"] + d["matvec_s_per_rhs"])
+    return {"value": nrhs / t_batch, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": ("oracle factor+solve of 2 M, 2 R, 2 L layer subproblems and one sparse matvec at "
+                       f"n=1023 (of 736 subproblems), scaled to one 32-RHS batch with {iterations} "
+                       "FGMRES iterations; Krylov vector work not counted"),
+            "sample_wall_s": wall, "extrapolated_batch_s": t_batch, **d}
+
+
+def run_reference(args):
+    """The oracle arm: the CPU FP64 oracle on the host cores, each step a bounded
+    sample of the same workload (see cpu_baseline_sample)."""
+    its = 6
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        last = cpu_baseline_sample(its)
+        if i >= args.warmup and last.get("value"):
+            vals.append(last["value"])
+    value = statistics.median(vals) if vals else None
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": (32 / value * 1e3) if value else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD, parallelism="cpu oracle, 1 thread"),
+            "impl": "reference",
+            "cpu_baseline": {k: last.get(k) for k in ("value", "unit", "cores", "kind", "sample")} if last else None,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["asp", "reference"], default="asp")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    from paper_1504_04058_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    line = run_asp(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_sample(line["iterations_max"])
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

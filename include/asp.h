@@ -1,0 +1,196 @@
+/*
+ * asp.h -- C ABI of the GB300 additive sweeping preconditioner library (libasp.so).
+ *
+ * The library solves the PML-truncated Helmholtz equation
+ *     Delta u + omega^2 / c(x)^2 u = f   on (0,1)^d,  u = 0 on the boundary,
+ * (Liu & Ying, "Additive Sweeping Preconditioner for the Helmholtz Equation",
+ * 2016, Section 1, Eq. (1)) discretized by the central-difference scheme with a
+ * perfectly matched layer on every side (Section 2, Eq. (2); Section 3.1, Eq. (4);
+ * Section 3.2 puts the PML on all sides), preconditioned by the additive sweeping
+ * preconditioner (Section 3.1, Algorithms 1 and 2) inside flexible GMRES
+ * (Section 3.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid.  n interior nodes per axis, h = 1/(n+1), node i at x = i*h (Section 2).
+ *        dim = 2 only in this version of the library (3D is rejected with
+ *        ASP_ERR_UNSUPPORTED).
+ * Vectors.  A batch of nrhs grid functions is stored point-major with the
+ *        right-hand side fastest ("RHS-interleaved"):
+ *            element (i1, i2, r) at offset ((i2-1)*n + (i1-1))*nrhs + r,
+ *        i.e. for nrhs = 1 exactly the paper's column-major ordering (x1 fastest,
+ *        Section 3.1).  The sweep axis is x2.  Complex numbers are interleaved
+ *        (re, im) pairs: complex128 = two doubles.  All vector arguments are
+ *        DEVICE pointers unless the name says _host.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *        stream).  Work is enqueued on it; calls return once it is enqueued, except
+ *        where a call says it synchronizes.
+ * Ownership.  The caller owns every pointer it passes; the library copies what it
+ *        keeps (the velocity field).  The library owns the device memory it
+ *        allocates for a handle (factors, transfer maps, Krylov workspace) and
+ *        frees it in asp_destroy.
+ * Errors.  Every int-returning call returns ASP_OK (0) or a negative ASP_ERR_*
+ *        code; asp_error_string() names it and asp_last_error_detail() gives a
+ *        one-line description of the most recent failure on the calling thread.
+ *        No call traps, asserts or spins without a bound on the device: device
+ *        waits have iteration limits and report ASP_ERR_TIMEOUT.
+ */
+#ifndef ASP_H
+#define ASP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define ASP_OK 0
+#define ASP_ERR_INVALID -1        /* argument out of range / inconsistent sizes   */
+#define ASP_ERR_OOM -2            /* device allocation failed                     */
+#define ASP_ERR_CUDA -3           /* a CUDA runtime call failed                   */
+#define ASP_ERR_SMALL_PIVOT -4    /* zero or non-finite pivot in a layer factor   */
+#define ASP_ERR_NOT_CONVERGED -5  /* FGMRES hit maxit before the tolerance        */
+#define ASP_ERR_TIMEOUT -6        /* a bounded device-side wait gave up           */
+#define ASP_ERR_STATE -7          /* call made in the wrong order (e.g. no factor) */
+#define ASP_ERR_UNSUPPORTED -8    /* valid request this build does not implement  */
+
+/* ---- precision of the layer factors and preconditioner applies ---------- */
+#define ASP_PREC_C128 0 /* complex128 factors and applies (plain FP64 path)      */
+#define ASP_PREC_C64 1  /* complex64 factors and applies inside FP64 FGMRES      */
+
+/* Problem parameters (Section 2 and Section 3.1 notation).
+ *   dim        spatial dimension (2)
+ *   n          interior nodes per axis; h = 1/(n+1)
+ *   omega      angular frequency (> 0)
+ *   pml        gamma: boundary PML width eta = gamma*h (>= 2)
+ *   pml_aux    gamma_a: width of the auxiliary PMLs of the padded layer grids
+ *              (Section 3.1, practical remark 2); 0 means gamma_a = gamma
+ *   b          interior layer width in grid columns along x2 (>= 1); with
+ *              P = n + 2 - 2*gamma physical columns there are m = floor(P/b)
+ *              layers and the last one absorbs the remainder P - m*b
+ *   C          PML strength: sigma = (C/eta) (d/eta)^2 at distance d past the
+ *              physical edge (Section 2); > 0
+ *   factor_prec ASP_PREC_C128 or ASP_PREC_C64
+ *   max_rhs    largest nrhs that later calls will pass (1..256); sizes the
+ *              apply and Krylov workspaces
+ *   restart    FGMRES restart length the workspace is sized for (1..64)       */
+typedef struct asp_params {
+  int dim;
+  int n;
+  double omega;
+  int pml;
+  int pml_aux;
+  int b;
+  double C;
+  int factor_prec;
+  int max_rhs;
+  int restart;
+} asp_params;
+
+typedef struct asp_handle asp_handle;
+
+/* Per-right-hand-side result of asp_gmres_solve (host memory, caller-owned). */
+typedef struct asp_solve_info {
+  int iterations;       /* preconditioner applications until the estimate met tol */
+  int converged;        /* 1 if the true relative residual is <= tol               */
+  double rel_res_est;   /* FGMRES residual estimate / ||f|| at exit                */
+  double rel_res_true;  /* ||f - A u|| / ||f|| recomputed in FP64 at exit          */
+} asp_solve_info;
+
+/* asp_setup: validate `p`, build the layer partition (Section 3.1: X_p, X_q^M,
+ * X_p^R, X_p^L), compute the PML profiles, copy the velocity c (n^dim doubles,
+ * natural ordering, HOST memory if c_is_device == 0, else DEVICE) and allocate
+ * the handle's device memory.  Returns ASP_ERR_INVALID for out-of-range
+ * parameters or a non-positive / non-finite velocity, ASP_ERR_OOM if the
+ * footprint does not fit.  Synchronizes the device before returning. */
+int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle** out);
+
+/* Bytes of device memory asp_setup + asp_factor will hold for these
+ * parameters (factors, transfer maps, apply and Krylov workspaces).  Pure
+ * function of `p`; 0 for invalid parameters. */
+size_t asp_footprint_bytes(const asp_params* p);
+
+/* Number of layers m, and the partition of layer p (1-based): X_p = [x_lo, x_hi]
+ * along x2 (global 1-based indices).  Returns ASP_ERR_INVALID for a bad p. */
+int asp_num_layers(const asp_handle* h);
+int asp_layer_range(const asp_handle* h, int p, int* x_lo, int* x_hi);
+
+/* asp_factor: Algorithm 1.  Factors H_q^M (q=1..m), H_p^R (p=2..m) and H_p^L
+ * (p=1..m-1) in the precision chosen at setup, all in one batched launch, and
+ * builds the dense trace-transfer maps of the R and L sweeps (the linear maps
+ * from a layer's incoming boundary trace to the outgoing trace of G~_p^R /
+ * G~_p^L, Section 3.1 "Putting together").  Enqueued on `stream`; the pivot
+ * check synchronizes `stream` and returns ASP_ERR_SMALL_PIVOT if any block
+ * pivot was zero or non-finite. */
+int asp_factor(asp_handle* h, void* stream);
+
+/* z = M^-1 r: Algorithm 2 (M-solves of every layer, right-going and
+ * left-going sweeps with accumulated boundary values, and the sum), for nrhs
+ * right-hand sides.  r and z are complex128 DEVICE vectors in the
+ * RHS-interleaved layout; they may not alias.  1 <= nrhs <= max_rhs.  Requires
+ * asp_factor.  Enqueued on `stream`. */
+int asp_apply_preconditioner(asp_handle* h, const void* r, void* z, int nrhs, void* stream);
+
+/* y = A x: the 5-point operator of Eq. (4) with the PML on all four sides, for
+ * nrhs complex128 DEVICE vectors (RHS-interleaved, no aliasing).  Needs only
+ * asp_setup.  Enqueued on `stream`. */
+int asp_matvec(asp_handle* h, const void* x, void* y, int nrhs, void* stream);
+
+/* One layer subproblem on its own (for checking): v = H^-1 g for the
+ * subproblem kind (0 = H_p^M, 1 = H_p^R, 2 = H_p^L) of layer p, with g and v
+ * complex128 DEVICE arrays of shape [w][n][nrhs] (padded x2 columns of the
+ * subproblem outermost, x1, then the right-hand side), w = asp_subproblem_width.
+ * Uses the stored factors.  Enqueued on `stream`. */
+int asp_subproblem_width(const asp_handle* h, int kind, int p);
+int asp_subproblem_solve(asp_handle* h, int kind, int p, const void* g, void* v, int nrhs,
+                         void* stream);
+
+/* asp_gmres_solve: right-preconditioned flexible GMRES (Section 3.2), zero
+ * initial guess, restart `restart` (<= the setup value), FP64 Arnoldi
+ * (classical Gram-Schmidt applied twice) and Givens rotations on the device,
+ * independent Krylov spaces per right-hand side.  Stops a right-hand side when
+ * its residual estimate / ||f|| <= tol; stops when all have stopped or after
+ * `maxit` iterations.  tol = 0 with maxit = k runs exactly k iterations.
+ * f and u are complex128 DEVICE vectors (RHS-interleaved); u is written even
+ * when ASP_ERR_NOT_CONVERGED is returned.  info_host (nrhs entries, HOST) may
+ * be NULL.  Synchronizes `stream` once per iteration to read the convergence
+ * flags, and before returning. */
+int asp_gmres_solve(asp_handle* h, const void* f, void* u, int nrhs, double tol, int restart,
+                    int maxit, asp_solve_info* info_host, void* stream);
+
+/* Number of kernel launches this handle has issued since the last call (the
+ * counter is reset by the call).  Used to report how many of the library's
+ * kernels ran in a timed region. */
+long long asp_take_launch_count(asp_handle* h);
+
+/* Phase timing (measurement).  When enabled, the library records a CUDA event
+ * before and after each of its launches on the launching stream and attributes
+ * the interval to a phase:
+ *   0 factor (block inversions)      1 transfer maps     2 M-solves (EMBED)
+ *   3 sweep chain                    4 sweep fills       5 sum
+ *   6 matvec                         7 FGMRES vector kernels
+ * asp_phase_times synchronizes the device, writes per-phase total milliseconds
+ * and launch counts (HOST arrays of nphases <= ASP_NUM_PHASES entries) and
+ * resets the records.  Timing adds two event records per launch; it is off by
+ * default. */
+#define ASP_NUM_PHASES 8
+int asp_set_phase_timing(asp_handle* h, int enable);
+int asp_phase_times(asp_handle* h, double* ms, long long* launches, int nphases);
+
+/* Free everything the handle owns.  NULL is accepted; calling it twice on the
+ * same pointer is undefined (the handle is gone after the first call). */
+void asp_destroy(asp_handle* h);
+
+/* Static name of an error code ("ASP_OK", "ASP_ERR_INVALID", ...). */
+const char* asp_error_string(int code);
+
+/* One-line description of the last failure on the calling thread (static
+ * thread-local storage, overwritten by the next failure). */
+const char* asp_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASP_H */

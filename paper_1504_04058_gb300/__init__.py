@@ -1,0 +1,182 @@
+"""GB300-native additive sweeping preconditioner for the PML Helmholtz equation.
+
+Python face of libasp.so (include/asp.h).  The names follow the C ABI:
+``asp_setup`` returns an :class:`AspHandle` whose methods ``factor``,
+``apply_preconditioner``, ``matvec``, ``subproblem_solve`` and ``gmres_solve``
+call ``asp_factor`` ... ``asp_gmres_solve`` with torch tensors' device
+pointers and the current CUDA stream.  Vectors are complex128 CUDA tensors of
+shape ``(n, n, nrhs)`` indexed ``[i2-1, i1-1, r]`` (x1 fastest per right-hand
+side block, right-hand side fastest overall), which is the RHS-interleaved
+layout of the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (ASP_PREC_C64, ASP_PREC_C128, KIND_L, KIND_M, KIND_R, AspError,  # noqa: F401
+                   asp_params, asp_solve_info)
+
+__all__ = ["asp_setup", "asp_footprint_bytes", "AspHandle", "make_params", "AspError",
+           "ASP_PREC_C64", "ASP_PREC_C128", "KIND_M", "KIND_R", "KIND_L"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev_vec(t, n: int, name: str):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128):
+        raise TypeError(f"{name} must be a complex128 CUDA tensor")
+    if t.dim() != 3 or t.shape[0] != n or t.shape[1] != n or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with shape (n, n, nrhs) = ({n}, {n}, nrhs)")
+    return t
+
+
+def make_params(n: int, omega: float, pml: int, b: int, pml_aux: int = 0, C: float = 20.0,
+                precision: str = "c128", max_rhs: int = 1, restart: int = 40, dim: int = 2) -> asp_params:
+    prec = {"c128": ASP_PREC_C128, "c64": ASP_PREC_C64}[precision]
+    return asp_params(dim, n, float(omega), pml, pml_aux, b, float(C), prec, max_rhs, restart)
+
+
+def asp_footprint_bytes(params: asp_params) -> int:
+    return int(_lib.load().asp_footprint_bytes(ctypes.byref(params)))
+
+
+class AspHandle:
+    """An asp_handle: the factored preconditioner of one (velocity, omega, grid)."""
+
+    def __init__(self, ptr: int, params: asp_params):
+        self._ptr = ctypes.c_void_p(ptr)
+        self.params = params
+        self.n = params.n
+
+    # -------------------------------------------------------------- info
+    @property
+    def num_layers(self) -> int:
+        return int(_lib.load().asp_num_layers(self._ptr))
+
+    def layer_range(self, p: int) -> tuple[int, int]:
+        lo, hi = ctypes.c_int(), ctypes.c_int()
+        _lib.check(_lib.load().asp_layer_range(self._ptr, p, ctypes.byref(lo), ctypes.byref(hi)),
+                   "asp_layer_range")
+        return lo.value, hi.value
+
+    def subproblem_width(self, kind: int, p: int) -> int:
+        w = int(_lib.load().asp_subproblem_width(self._ptr, kind, p))
+        if w < 0:
+            raise AspError(w, "asp_subproblem_width", "no such subproblem")
+        return w
+
+    def take_launch_count(self) -> int:
+        return int(_lib.load().asp_take_launch_count(self._ptr))
+
+    def set_phase_timing(self, enable: bool) -> None:
+        _lib.check(_lib.load().asp_set_phase_timing(self._ptr, 1 if enable else 0), "asp_set_phase_timing")
+
+    def phase_times(self) -> dict:
+        """{phase: (milliseconds, launches)} since the last call (synchronizes)."""
+        k = len(_lib.PHASES)
+        ms = (ctypes.c_double * k)()
+        cnt = (ctypes.c_longlong * k)()
+        _lib.check(_lib.load().asp_phase_times(self._ptr, ms, cnt, k), "asp_phase_times")
+        return {name: (ms[i], int(cnt[i])) for i, name in enumerate(_lib.PHASES)}
+
+    # -------------------------------------------------------------- compute
+    def factor(self, stream=None) -> None:
+        _lib.check(_lib.load().asp_factor(self._ptr, ctypes.c_void_p(_stream_ptr(stream))), "asp_factor")
+
+    def apply_preconditioner(self, r, z=None, stream=None):
+        torch = _torch()
+        _dev_vec(r, self.n, "r")
+        if z is None:
+            z = torch.empty_like(r)
+        _dev_vec(z, self.n, "z")
+        _lib.check(_lib.load().asp_apply_preconditioner(
+            self._ptr, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()), r.shape[2],
+            ctypes.c_void_p(_stream_ptr(stream))), "asp_apply_preconditioner")
+        return z
+
+    def matvec(self, x, y=None, stream=None):
+        torch = _torch()
+        _dev_vec(x, self.n, "x")
+        if y is None:
+            y = torch.empty_like(x)
+        _dev_vec(y, self.n, "y")
+        _lib.check(_lib.load().asp_matvec(self._ptr, ctypes.c_void_p(x.data_ptr()),
+                                          ctypes.c_void_p(y.data_ptr()), x.shape[2],
+                                          ctypes.c_void_p(_stream_ptr(stream))), "asp_matvec")
+        return y
+
+    def subproblem_solve(self, kind: int, p: int, g, v=None, stream=None):
+        """v = H^-1 g for one subproblem; g, v complex128 of shape (w, n, nrhs)."""
+        torch = _torch()
+        w = self.subproblem_width(kind, p)
+        if not (g.is_cuda and g.dtype == torch.complex128 and tuple(g.shape[:2]) == (w, self.n)
+                and g.is_contiguous()):
+            raise ValueError(f"g must be a contiguous complex128 CUDA tensor of shape ({w}, {self.n}, nrhs)")
+        if v is None:
+            v = torch.empty_like(g)
+        _lib.check(_lib.load().asp_subproblem_solve(
+            self._ptr, kind, p, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(v.data_ptr()), g.shape[2],
+            ctypes.c_void_p(_stream_ptr(stream))), "asp_subproblem_solve")
+        return v
+
+    def gmres_solve(self, f, u=None, tol: float = 1e-6, restart: int | None = None, maxit: int = 200,
+                    stream=None, raise_on_nonconvergence: bool = True):
+        """FGMRES; returns (u, info) with info a list of dicts per right-hand side."""
+        torch = _torch()
+        _dev_vec(f, self.n, "f")
+        if u is None:
+            u = torch.empty_like(f)
+        _dev_vec(u, self.n, "u")
+        nrhs = f.shape[2]
+        info = (asp_solve_info * nrhs)()
+        rs = self.params.restart if restart is None else restart
+        code = _lib.load().asp_gmres_solve(self._ptr, ctypes.c_void_p(f.data_ptr()),
+                                           ctypes.c_void_p(u.data_ptr()), nrhs, float(tol), rs, maxit, info,
+                                           ctypes.c_void_p(_stream_ptr(stream)))
+        if code != _lib.ASP_OK and (raise_on_nonconvergence or code != _lib.ASP_ERR_NOT_CONVERGED):
+            _lib.check(code, "asp_gmres_solve")
+        out = [{"iterations": i.iterations, "converged": bool(i.converged), "rel_res_est": i.rel_res_est,
+                "rel_res_true": i.rel_res_true} for i in info]
+        return u, out
+
+    def destroy(self) -> None:
+        if self._ptr:
+            _lib.load().asp_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def asp_setup(c, params: asp_params) -> AspHandle:
+    """Set up a handle for velocity ``c`` (n x n float64, numpy or CUDA tensor)."""
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    if isinstance(c, np.ndarray):
+        arr = np.ascontiguousarray(c, dtype=np.float64)
+        if arr.size != params.n ** params.dim:
+            raise ValueError("velocity has the wrong number of nodes")
+        code = lib.asp_setup(ctypes.byref(params), arr.ctypes.data_as(ctypes.c_void_p), 0, ctypes.byref(out))
+    else:
+        torch = _torch()
+        t = c.contiguous().to(torch.float64)
+        code = lib.asp_setup(ctypes.byref(params), ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0,
+                             ctypes.byref(out))
+    _lib.check(code, "asp_setup")
+    return AspHandle(out.value, params)

@@ -1,0 +1,818 @@
+// api.cu -- the C ABI of libasp (include/asp.h): setup, factor, apply,
+// matvec, FGMRES, and the small element-wise kernels of the apply.
+//
+// Setup builds, on the host in FP64, everything the kernels read:
+//  * the layer partition of Section 3.1 (X_p, X_q^M, X_p^R, X_p^L) with
+//    m = floor(P/b) layers over the P = n+2-2*gamma physical columns, the last
+//    layer taking the remainder;
+//  * the PML functions sigma(x) = (C/eta)(d/eta)^2, s = (1 + i sigma/omega)^-1
+//    (Section 2), for the boundary PML on both axes and for the auxiliary
+//    profiles sigma_q^M, sigma_p^R, sigma_p^L of every subproblem;
+//  * the stencil weights s_i s_{i+-1/2}/h^2 of Eq. (2)/(4) at every node.
+// All device memory of a handle is allocated here (asp_footprint_bytes gives
+// the total in advance) and released by asp_destroy.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace asp {
+
+int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int restart, int maxit,
+              asp_solve_info* info, cudaStream_t s);
+size_t krylov_state_bytes(int restart, int nrhs, size_t* n2, size_t* nd, size_t* ni);
+
+static thread_local std::string g_detail;
+
+static cudaEvent_t pool_event(Handle& H) {
+  if (!H.evpool.empty()) {
+    cudaEvent_t e = H.evpool.back();
+    H.evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void phase_begin(Handle& H, int phase, cudaStream_t s) {
+  if (!H.timing) return;
+  H.open_phase = phase;
+  H.open_ev = pool_event(H);
+  if (H.open_ev) cudaEventRecord(H.open_ev, s);
+}
+
+void phase_end(Handle& H, cudaStream_t s) {
+  if (!H.timing || H.open_phase < 0 || !H.open_ev) return;
+  cudaEvent_t b = pool_event(H);
+  if (b) {
+    cudaEventRecord(b, s);
+    H.recs.push_back({H.open_phase, H.open_ev, b});
+  } else {
+    H.evpool.push_back(H.open_ev);
+  }
+  H.open_phase = -1;
+  H.open_ev = nullptr;
+}
+void set_detail(const std::string& s) { g_detail = s; }
+int fail(int code, const std::string& detail) {
+  g_detail = detail;
+  return code;
+}
+
+namespace {
+
+// ---------------------------------------------------------------- PML
+// sigma = 0 on [lo_edge, hi_edge]; (C/eta)(d/eta)^2 at distance d outside, on the
+// sides that carry a layer.
+struct Profile {
+  bool lo_on = false, hi_on = false;
+  double lo_edge = 0, hi_edge = 0, eta_lo = 1, eta_hi = 1, C = 0;
+  double sigma(double x) const {
+    if (lo_on && x < lo_edge) {
+      const double d = lo_edge - x;
+      return (C / eta_lo) * (d / eta_lo) * (d / eta_lo);
+    }
+    if (hi_on && x > hi_edge) {
+      const double d = x - hi_edge;
+      return (C / eta_hi) * (d / eta_hi) * (d / eta_hi);
+    }
+    return 0.0;
+  }
+  // s = 1 / (1 + i sigma/omega)
+  double2 s(double x, double omega) const {
+    const double t = sigma(x) / omega;
+    const double den = 1.0 + t * t;
+    return make_double2(1.0 / den, -t / den);
+  }
+};
+
+double2 hmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+double2 hscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+double2 hadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+struct Sizes {
+  int m = 0, wmax = 0, wmaxRL = 0, nsub = 0;
+  size_t W_elems = 0, tmap_elems = 0, coef = 0;
+  size_t esz = 0;
+  long long N = 0;
+  size_t zslot = 0;
+  int zslots = 0;
+  size_t bytes = 0;
+};
+
+bool valid(const asp_params* p, std::string* why) {
+  if (!p) { *why = "null params"; return false; }
+  if (p->dim != 2) { *why = p->dim == 3 ? "3D is not implemented in this build" : "dim must be 2"; return false; }
+  if (p->n < 3 || p->n > 16383) { *why = "n out of range [3, 16383]"; return false; }
+  if (!(p->omega > 0) || !isfinite(p->omega)) { *why = "omega must be positive and finite"; return false; }
+  if (p->pml < 2) { *why = "pml (gamma) must be >= 2"; return false; }
+  if (p->pml_aux < 0) { *why = "pml_aux must be >= 0"; return false; }
+  if (p->b < 1) { *why = "b must be >= 1"; return false; }
+  if (!(p->C > 0) || !isfinite(p->C)) { *why = "C must be positive and finite"; return false; }
+  if (p->factor_prec != ASP_PREC_C128 && p->factor_prec != ASP_PREC_C64) { *why = "bad factor_prec"; return false; }
+  if (p->max_rhs < 1 || p->max_rhs > 256) { *why = "max_rhs out of range [1, 256]"; return false; }
+  if (p->restart < 1 || p->restart > 64) { *why = "restart out of range [1, 64]"; return false; }
+  const int P = p->n + 2 - 2 * p->pml;
+  if (P < p->b) { *why = "n too small for the PML width and layer width (need n >= 2*gamma + b - 2)"; return false; }
+  const int ga = p->pml_aux ? p->pml_aux : p->pml;
+  if (ga > p->pml + p->b) { *why = "pml_aux too wide for the layer width"; return false; }
+  return true;
+}
+
+struct Part {
+  int m;
+  std::vector<int> x_lo, x_hi, alpha, beta, m_lo, m_hi;
+};
+
+Part partition(int n, int gamma, int ga, int b) {
+  Part P;
+  const int phys = n + 2 - 2 * gamma;
+  P.m = phys / b;
+  const int m = P.m;
+  P.x_lo.assign(m + 1, 0); P.x_hi = P.x_lo; P.alpha = P.x_lo; P.beta = P.x_lo; P.m_lo = P.x_lo; P.m_hi = P.x_lo;
+  for (int p = 1; p <= m; ++p) {
+    P.alpha[p] = gamma + (p - 1) * b;
+    P.beta[p] = (p < m) ? gamma + p * b - 1 : n + 1 - gamma;
+    P.x_lo[p] = (p == 1) ? 1 : P.alpha[p];
+    P.x_hi[p] = (p == m) ? n : P.beta[p];
+    P.m_lo[p] = (p == 1) ? 1 : P.alpha[p] - ga + 1;
+    P.m_hi[p] = (p == m) ? n : P.beta[p] + ga - 1;
+  }
+  return P;
+}
+
+int fmax_rhs_cap(int prec) { return prec == ASP_PREC_C64 ? 64 : 16; }
+
+Sizes sizes_for(const asp_params* p, int num_sms) {
+  Sizes Z;
+  const int n = p->n, gamma = p->pml, ga = p->pml_aux ? p->pml_aux : p->pml, b = p->b;
+  Part P = partition(n, gamma, ga, b);
+  Z.m = P.m;
+  Z.esz = p->factor_prec == ASP_PREC_C128 ? 16 : 8;
+  Z.N = (long long)n * n;
+  auto addsub = [&](int lo, int hi, bool rl) {
+    const int w = hi - lo + 1;
+    const int wp = (p->factor_prec == ASP_PREC_C64) ? ((w + 1) & ~1) : w;
+    Z.W_elems += (size_t)n * w * wp;
+    Z.coef += w;
+    Z.wmax = std::max(Z.wmax, w);
+    if (rl) Z.wmaxRL = std::max(Z.wmaxRL, w);
+    Z.nsub++;
+  };
+  for (int q = 1; q <= P.m; ++q) addsub(P.m_lo[q], P.m_hi[q], false);
+  for (int q = 2; q <= P.m; ++q) addsub(P.alpha[q], P.m_hi[q], true);
+  for (int q = 1; q <= P.m - 1; ++q) addsub(P.m_lo[q], P.beta[q], true);
+  Z.tmap_elems = P.m >= 3 ? (size_t)2 * (P.m - 2) * n * n : 0;
+  Z.zslots = std::max(1, 2 * num_sms);
+  Z.zslot = (size_t)n * Z.wmax * fmax_rhs_cap(p->factor_prec);
+  const long long R = p->restart;
+  const long long mr = p->max_rhs;
+  size_t n2, nd, ni;
+  const size_t kst = krylov_state_bytes(p->restart, p->max_rhs, &n2, &nd, &ni);
+  size_t bytes = 0;
+  bytes += Z.N * sizeof(double) + 3 * (size_t)n * sizeof(double2);              // k2, ca, cc, cd
+  bytes += Z.coef * sizeof(SweepCoef) + Z.nsub * sizeof(SubDesc);
+  bytes += Z.W_elems * Z.esz + Z.tmap_elems * Z.esz;
+  bytes += (size_t)Z.N * mr * Z.esz * (3 + (Z.esz == 8 ? 1 : 0));              // uM uR uL (+ r_lo)
+  bytes += (size_t)2 * (P.m + 1) * n * mr * Z.esz;                               // accR, accL
+  bytes += (size_t)Z.zslots * Z.zslot * Z.esz;                                   // forward scratch
+  bytes += (size_t)(2 * R + 2) * Z.N * mr * sizeof(double2);                     // V, Z, work
+  bytes += (size_t)num_sms * 2 * 8 * mr * sizeof(double2);                       // dot partials
+  bytes += kst + 64;
+  Z.bytes = bytes;
+  return Z;
+}
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+// ---------------------------------------------------------------- small kernels
+template <typename R>
+__global__ void to_prec_kernel(const double2* __restrict__ in, Cx<R>* __restrict__ out, long long count) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = cvt<R>(in[e]);
+}
+
+// z = uM + uR (except on X_1, where there is no right-going part) + uL (except on X_m)
+template <typename R>
+__global__ void sum3_kernel(const Cx<R>* __restrict__ a, const Cx<R>* __restrict__ b, const Cx<R>* __restrict__ c,
+                            double2* __restrict__ z, long long count, long long per_col, long long r_from,
+                            long long l_below) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long col = e / per_col;  // 0-based x2 index
+    const Cx<R> va = a[e];
+    double re = (double)va.x, im = (double)va.y;
+    if (col >= r_from) { const Cx<R> vb = b[e]; re += (double)vb.x; im += (double)vb.y; }
+    if (col < l_below) { const Cx<R> vc = c[e]; re += (double)vc.x; im += (double)vc.y; }
+    z[e] = make_double2(re, im);
+  }
+}
+
+int vec_grid(long long count, int sms) {
+  long long g = (count + 255) / 256;
+  g = std::min<long long>(g, (long long)std::max(sms, 1) * 8);
+  return (int)std::max<long long>(g, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_to_prec(const double2* in, void* out, long long count, int prec, cudaStream_t s) {
+  if (prec == ASP_PREC_C64)
+    to_prec_kernel<float><<<vec_grid(count, 152), 256, 0, s>>>(in, (float2*)out, count);
+  else
+    to_prec_kernel<double><<<vec_grid(count, 152), 256, 0, s>>>(in, (double2*)out, count);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- job lists
+namespace {
+
+struct JobList {
+  Job* d = nullptr;
+  int n = 0, cap = 0, wmax = 0;
+};
+
+struct JobCache {
+  std::map<int, JobList> embed, fill;
+  std::map<long long, JobList> sub;  // key: subproblem index * 1024 + nrhs
+  JobList tmap;
+  bool have_tmap = false;
+  std::vector<void*> owned;
+  ~JobCache() {
+    for (void* p : owned) cudaFree(p);
+  }
+};
+
+std::map<const Handle*, JobCache>& caches() {
+  static std::map<const Handle*, JobCache> c;
+  return c;
+}
+
+int upload_jobs(Handle& H, const std::vector<Job>& jobs, int cap, int wmax, JobList* out) {
+  out->n = (int)jobs.size();
+  out->cap = cap;
+  out->wmax = wmax;
+  if (jobs.empty()) return ASP_OK;
+  void* d = nullptr;
+  if (cudaMalloc(&d, jobs.size() * sizeof(Job)) != cudaSuccess) return fail(ASP_ERR_OOM, "job list allocation");
+  if (cudaMemcpy(d, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return fail(ASP_ERR_CUDA, "job list upload");
+  }
+  caches()[&H].owned.push_back(d);
+  out->d = (Job*)d;
+  return ASP_OK;
+}
+
+int get_embed_jobs(Handle& H, int nrhs, JobList** out) {
+  JobCache& c = caches()[&H];
+  auto it = c.embed.find(nrhs);
+  if (it == c.embed.end()) {
+    int wm = 0;
+    for (int q = 1; q <= H.m; ++q) wm = std::max(wm, H.subs[H.subM[q]].w);
+    const int cap = btsolve_rhs_capacity(nrhs, wm, H.prec, false);
+    std::vector<Job> jobs;
+    for (int q = 1; q <= H.m; ++q)
+      for (int r0 = 0; r0 < nrhs; r0 += cap) jobs.push_back({H.subM[q], MODE_EMBED, r0, std::min(cap, nrhs - r0)});
+    JobList L;
+    int rc = upload_jobs(H, jobs, cap, wm, &L);
+    if (rc != ASP_OK) return rc;
+    it = c.embed.emplace(nrhs, L).first;
+  }
+  *out = &it->second;
+  return ASP_OK;
+}
+
+int get_fill_jobs(Handle& H, int nrhs, JobList** out) {
+  JobCache& c = caches()[&H];
+  auto it = c.fill.find(nrhs);
+  if (it == c.fill.end()) {
+    const int wm = std::max(1, H.wmaxRL);
+    const int cap = btsolve_rhs_capacity(nrhs, wm, H.prec, false);
+    std::vector<Job> jobs;
+    for (int p = 1; p <= H.m; ++p) {
+      for (int r0 = 0; r0 < nrhs; r0 += cap) {
+        if (p >= 2) jobs.push_back({H.subR[p], MODE_FILL_R, r0, std::min(cap, nrhs - r0)});
+        if (p <= H.m - 1) jobs.push_back({H.subL[p], MODE_FILL_L, r0, std::min(cap, nrhs - r0)});
+      }
+    }
+    JobList L;
+    int rc = upload_jobs(H, jobs, cap, wm, &L);
+    if (rc != ASP_OK) return rc;
+    it = c.fill.emplace(nrhs, L).first;
+  }
+  *out = &it->second;
+  return ASP_OK;
+}
+
+SolveParams base_params(Handle& H, int ldv) {
+  SolveParams P{};
+  P.subs = H.d_subs;
+  P.n = H.n;
+  P.ldv = ldv;
+  P.inv_h2 = H.inv_h2;
+  P.W = H.W;
+  P.ca = H.ca;
+  P.cc = H.cc;
+  P.outM = H.uM;
+  P.outR = H.uR;
+  P.outL = H.uL;
+  P.accR = H.accR;
+  P.accL = H.accL;
+  P.tmap = H.tmap;
+  P.zscr = H.zscr;
+  P.zslot = H.zslot;
+  P.err = H.err;
+  return P;
+}
+
+int check_err(Handle& H, cudaStream_t s, const char* what) {
+  int e[2] = {0, 0};
+  if (cudaMemcpyAsync(e, H.err, sizeof(e), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(ASP_ERR_CUDA, std::string(what) + ": ") ;
+  if (e[0] != 0) {
+    cudaMemsetAsync(H.err, 0, 2 * sizeof(int), s);
+    return fail(e[0], std::string(what) + ": device reported " + asp_error_string(e[0]) + " (detail " +
+                          std::to_string(e[1]) + ")");
+  }
+  return ASP_OK;
+}
+
+}  // namespace
+
+int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_t s) {
+  if (!H.factored) return fail(ASP_ERR_STATE, "apply before factor");
+  const long long count = H.N * nrhs;
+  const void* in = r;
+  if (H.prec == ASP_PREC_C64) {
+    phase_begin(H, PH_SUM, s);
+    if (launch_to_prec(r, H.r_lo, count, H.prec, s) != cudaSuccess) return fail(ASP_ERR_CUDA, "to_prec launch");
+    phase_end(H, s);
+    H.launches += 1;
+    in = H.r_lo;
+  }
+  JobList *je = nullptr, *jf = nullptr;
+  int rc = get_embed_jobs(H, nrhs, &je);
+  if (rc != ASP_OK) return rc;
+  rc = get_fill_jobs(H, nrhs, &jf);
+  if (rc != ASP_OK) return rc;
+  // 1. M-solves of every layer (Algorithm 2, first loop) + traces
+  SolveParams P = base_params(H, nrhs);
+  P.in = in;
+  P.jobs = je->d;
+  P.njobs = je->n;
+  phase_begin(H, PH_EMBED, s);
+  cudaError_t ce = launch_btsolve(H, P, je->cap, je->wmax, s);
+  phase_end(H, s);
+  if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("M-solve launch: ") + cudaGetErrorString(ce));
+  // 2. accumulated traces of both sweeps (Algorithm 2, second and third loops)
+  const size_t esz = H.prec == ASP_PREC_C128 ? sizeof(double2) : sizeof(float2);
+  for (int r0 = 0; r0 < nrhs; r0 += 32) {
+    ChainParams C{};
+    C.n = H.n; C.m = H.m; C.ldv = nrhs; C.nrhs = std::min(32, nrhs - r0);
+    C.tmap = H.tmap; C.toffR = H.d_toffR; C.toffL = H.d_toffL;
+    C.accR = (char*)H.accR + r0 * esz;
+    C.accL = (char*)H.accL + r0 * esz;
+    C.bar = H.bar; C.err = H.err;
+    phase_begin(H, PH_CHAIN, s);
+    ce = launch_chain(H, C, s);
+    phase_end(H, s);
+    if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("sweep chain launch: ") + cudaGetErrorString(ce));
+  }
+  // 3. the right- and left-going layer fields from the accumulated traces
+  P.jobs = jf->d;
+  P.njobs = jf->n;
+  phase_begin(H, PH_FILL, s);
+  ce = launch_btsolve(H, P, jf->cap, jf->wmax, s);
+  phase_end(H, s);
+  if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("fill launch: ") + cudaGetErrorString(ce));
+  // 4. u~_p = u~_{p,1:p-1} + u~_{p,p} + u~_{p,p+1:m}
+  const long long per_col = (long long)H.n * nrhs;
+  const long long r_from = H.x_hi[1];     // 0-based first column of X_2
+  const long long l_below = H.x_lo[H.m] - 1;  // 0-based first column of X_m
+  phase_begin(H, PH_SUM, s);
+  if (H.prec == ASP_PREC_C64)
+    sum3_kernel<float><<<vec_grid(count, H.num_sms), 256, 0, s>>>((float2*)H.uM, (float2*)H.uR, (float2*)H.uL, z,
+                                                                  count, per_col, r_from, l_below);
+  else
+    sum3_kernel<double><<<vec_grid(count, H.num_sms), 256, 0, s>>>((double2*)H.uM, (double2*)H.uR,
+                                                                   (double2*)H.uL, z, count, per_col, r_from,
+                                                                   l_below);
+  phase_end(H, s);
+  H.launches += 1;
+  ce = cudaGetLastError();
+  if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("sum launch: ") + cudaGetErrorString(ce));
+  return ASP_OK;
+}
+
+}  // namespace asp
+
+using namespace asp;
+
+extern "C" {
+
+const char* asp_error_string(int code) {
+  switch (code) {
+    case ASP_OK: return "ASP_OK";
+    case ASP_ERR_INVALID: return "ASP_ERR_INVALID";
+    case ASP_ERR_OOM: return "ASP_ERR_OOM";
+    case ASP_ERR_CUDA: return "ASP_ERR_CUDA";
+    case ASP_ERR_SMALL_PIVOT: return "ASP_ERR_SMALL_PIVOT";
+    case ASP_ERR_NOT_CONVERGED: return "ASP_ERR_NOT_CONVERGED";
+    case ASP_ERR_TIMEOUT: return "ASP_ERR_TIMEOUT";
+    case ASP_ERR_STATE: return "ASP_ERR_STATE";
+    case ASP_ERR_UNSUPPORTED: return "ASP_ERR_UNSUPPORTED";
+  }
+  return "ASP_ERR_UNKNOWN";
+}
+
+const char* asp_last_error_detail(void) { return g_detail.c_str(); }
+
+size_t asp_footprint_bytes(const asp_params* p) {
+  std::string why;
+  if (!valid(p, &why)) return 0;
+  int sms = device_sms();
+  if (sms <= 0) sms = 152;
+  return sizes_for(p, sms).bytes;
+}
+
+int asp_num_layers(const asp_handle* h) { return h ? h->h.m : ASP_ERR_INVALID; }
+
+int asp_layer_range(const asp_handle* h, int p, int* x_lo, int* x_hi) {
+  if (!h || p < 1 || p > h->h.m) return fail(ASP_ERR_INVALID, "layer index out of range");
+  if (x_lo) *x_lo = h->h.x_lo[p];
+  if (x_hi) *x_hi = h->h.x_hi[p];
+  return ASP_OK;
+}
+
+int asp_set_phase_timing(asp_handle* hd, int enable) {
+  if (!hd) return fail(ASP_ERR_INVALID, "null handle");
+  hd->h.timing = enable != 0;
+  return ASP_OK;
+}
+
+int asp_phase_times(asp_handle* hd, double* ms, long long* launches, int nphases) {
+  if (!hd || nphases < 0 || nphases > ASP_NUM_PHASES) return fail(ASP_ERR_INVALID, "bad arguments");
+  Handle& H = hd->h;
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(ASP_ERR_CUDA, "synchronize for phase times");
+  for (int i = 0; i < nphases; ++i) {
+    if (ms) ms[i] = 0.0;
+    if (launches) launches[i] = 0;
+  }
+  for (auto& r : H.recs) {
+    float t = 0.f;
+    if (r.phase < nphases && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      if (ms) ms[r.phase] += t;
+      if (launches) launches[r.phase] += 1;
+    }
+    H.evpool.push_back(r.a);
+    H.evpool.push_back(r.b);
+  }
+  H.recs.clear();
+  return ASP_OK;
+}
+
+void asp_destroy(asp_handle* hd) {
+  if (!hd) return;
+  Handle& H = hd->h;
+  for (auto& r : H.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : H.evpool) cudaEventDestroy(e);
+  caches().erase(&H);
+  void* ptrs[] = {H.k2, H.ca, H.cc, H.cd, H.d_subs, H.d_coef, H.W, H.tmap, H.d_toffR, H.d_toffL, H.r_lo,
+                  H.uM, H.uR, H.uL, H.accR, H.accL, H.zscr, H.bar, H.V, H.Z, H.wv, H.red, H.hess, H.kstate,
+                  H.kflags, H.err};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (H.h_flags) cudaFreeHost(H.h_flags);
+  delete hd;
+}
+
+int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle** out) {
+  std::string why;
+  if (!out) return fail(ASP_ERR_INVALID, "out is null");
+  *out = nullptr;
+  if (!valid(p, &why)) return fail(p && p->dim == 3 ? ASP_ERR_UNSUPPORTED : ASP_ERR_INVALID, why);
+  if (!c) return fail(ASP_ERR_INVALID, "velocity pointer is null");
+  const int n = p->n;
+  const long long N = (long long)n * n;
+  std::vector<double> ch(N);
+  if (c_is_device) {
+    if (cudaMemcpy(ch.data(), c, N * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(ASP_ERR_CUDA, "copying the velocity from the device");
+  } else {
+    memcpy(ch.data(), c, N * sizeof(double));
+  }
+  for (long long i = 0; i < N; ++i)
+    if (!(ch[i] > 0) || !isfinite(ch[i])) return fail(ASP_ERR_INVALID, "velocity must be positive and finite");
+  const int sms = device_sms();
+  if (sms <= 0) return fail(ASP_ERR_CUDA, "no CUDA device");
+
+  asp_handle* hd = new asp_handle();
+  Handle& H = hd->h;
+  H.prm = *p;
+  H.n = n;
+  H.N = N;
+  H.prec = p->factor_prec;
+  H.gamma = p->pml;
+  H.gamma_a = p->pml_aux ? p->pml_aux : p->pml;
+  H.b = p->b;
+  H.h = 1.0 / (n + 1);
+  H.inv_h2 = 1.0 / (H.h * H.h);
+  H.num_sms = sms;
+  const double h = H.h, omega = p->omega, ih2 = H.inv_h2;
+  Part P = partition(n, H.gamma, H.gamma_a, H.b);
+  H.m = P.m;
+  H.x_lo = P.x_lo; H.x_hi = P.x_hi; H.alpha = P.alpha; H.beta = P.beta;
+  const int m = H.m;
+  Sizes Z = sizes_for(p, sms);
+
+  // ---- global stencil weights (same boundary PML on x1 and x2)
+  Profile g;
+  g.lo_on = g.hi_on = true;
+  g.lo_edge = H.gamma * h;
+  g.hi_edge = (n + 1 - H.gamma) * h;
+  g.eta_lo = g.eta_hi = H.gamma * h;
+  g.C = p->C;
+  std::vector<double2> ca(n), cc(n), cd(n);
+  for (int k = 0; k < n; ++k) {
+    const double x = (k + 1) * h;
+    const double2 sk = g.s(x, omega), sm = g.s(x - 0.5 * h, omega), sp = g.s(x + 0.5 * h, omega);
+    ca[k] = hscale(hmul(sk, sm), ih2);
+    cc[k] = hscale(hmul(sk, sp), ih2);
+    cd[k] = hscale(hadd(ca[k], cc[k]), -1.0);
+  }
+  std::vector<double> k2(N);
+  for (long long i = 0; i < N; ++i) k2[i] = omega * omega / (ch[i] * ch[i]);
+
+  // ---- subproblems and their sweep-axis profiles
+  H.subM.assign(m + 1, -1); H.subR.assign(m + 1, -1); H.subL.assign(m + 1, -1);
+  long long woff = 0;
+  auto add = [&](int kind, int q, int lo, int hi, const Profile& pr) {
+    SubDesc S{};
+    S.kind = kind; S.p = q; S.lo = lo; S.w = hi - lo + 1;
+    S.wp = (H.prec == ASP_PREC_C64) ? ((S.w + 1) & ~1) : S.w;
+    S.xoff = H.x_lo[q] - lo;
+    S.xw = H.x_hi[q] - H.x_lo[q] + 1;
+    S.prof = (int)H.coef.size();
+    S.woff = woff;
+    S.toff = -1;
+    woff += (long long)n * S.w * S.wp;
+    for (int j = 0; j < S.w; ++j) {
+      const double x = (lo + j) * h;
+      const double2 sj = pr.s(x, omega), sm = pr.s(x - 0.5 * h, omega), sp = pr.s(x + 0.5 * h, omega);
+      SweepCoef cf;
+      cf.up = hscale(hmul(sj, sp), ih2);
+      cf.dn = hscale(hmul(sj, sm), ih2);
+      cf.dg = hscale(hadd(cf.up, cf.dn), -1.0);
+      H.coef.push_back(cf);
+    }
+    H.subs.push_back(S);
+    H.wmax = std::max(H.wmax, S.w);
+    if (kind != KIND_M) H.wmaxRL = std::max(H.wmaxRL, S.w);
+    return (int)H.subs.size() - 1;
+  };
+  const double eta = H.gamma * h, eta_a = H.gamma_a * h;
+  for (int q = 1; q <= m; ++q) {
+    Profile pr;  // sigma_q^M: zero on [alpha_q h, beta_q h]
+    pr.C = p->C;
+    pr.lo_on = pr.hi_on = true;
+    pr.lo_edge = H.alpha[q] * h; pr.eta_lo = (q == 1) ? eta : eta_a;
+    pr.hi_edge = H.beta[q] * h;  pr.eta_hi = (q == m) ? eta : eta_a;
+    H.subM[q] = add(KIND_M, q, P.m_lo[q], P.m_hi[q], pr);
+  }
+  for (int q = 2; q <= m; ++q) {
+    Profile pr;  // sigma_q^R: no layer on the left
+    pr.C = p->C;
+    pr.hi_on = true;
+    pr.hi_edge = H.beta[q] * h; pr.eta_hi = (q == m) ? eta : eta_a;
+    H.subR[q] = add(KIND_R, q, H.alpha[q], P.m_hi[q], pr);
+  }
+  for (int q = 1; q <= m - 1; ++q) {
+    Profile pr;  // sigma_q^L: no layer on the right
+    pr.C = p->C;
+    pr.lo_on = true;
+    pr.lo_edge = H.alpha[q] * h; pr.eta_lo = (q == 1) ? eta : eta_a;
+    H.subL[q] = add(KIND_L, q, P.m_lo[q], H.beta[q], pr);
+  }
+  H.W_elems = (size_t)woff;
+  // transfer maps T_p^R, T_p^L for p = 2..m-1
+  H.toffR.assign(m + 1, 0); H.toffL.assign(m + 1, 0);
+  long long toff = 0;
+  for (int q = 2; q <= m - 1; ++q) {
+    H.toffR[q] = toff; H.subs[H.subR[q]].toff = toff; toff += (long long)n * n;
+    H.toffL[q] = toff; H.subs[H.subL[q]].toff = toff; toff += (long long)n * n;
+  }
+  H.tmap_elems = (size_t)toff;
+
+  // ---- device allocations
+  const size_t esz = Z.esz;
+  const int mr = p->max_rhs;
+  bool ok = true;
+  auto dal = [&](void** ptr, size_t bytes) {
+    if (!ok) return;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) { ok = false; *ptr = nullptr; }
+  };
+  dal((void**)&H.k2, N * sizeof(double));
+  dal((void**)&H.ca, n * sizeof(double2));
+  dal((void**)&H.cc, n * sizeof(double2));
+  dal((void**)&H.cd, n * sizeof(double2));
+  dal((void**)&H.d_subs, H.subs.size() * sizeof(SubDesc));
+  dal((void**)&H.d_coef, H.coef.size() * sizeof(SweepCoef));
+  dal(&H.W, H.W_elems * esz);
+  dal(&H.tmap, H.tmap_elems * esz);
+  dal((void**)&H.d_toffR, (m + 1) * sizeof(long long));
+  dal((void**)&H.d_toffL, (m + 1) * sizeof(long long));
+  if (H.prec == ASP_PREC_C64) dal(&H.r_lo, (size_t)N * mr * esz);
+  dal(&H.uM, (size_t)N * mr * esz);
+  dal(&H.uR, (size_t)N * mr * esz);
+  dal(&H.uL, (size_t)N * mr * esz);
+  dal(&H.accR, (size_t)(m + 1) * n * mr * esz);
+  dal(&H.accL, (size_t)(m + 1) * n * mr * esz);
+  H.zslots = Z.zslots;
+  H.zslot = (long long)Z.zslot;
+  dal(&H.zscr, (size_t)Z.zslots * Z.zslot * esz);
+  dal((void**)&H.bar, 64);
+  const int R = p->restart;
+  dal((void**)&H.V, (size_t)(R + 1) * N * mr * sizeof(double2));
+  dal((void**)&H.Z, (size_t)R * N * mr * sizeof(double2));
+  dal((void**)&H.wv, (size_t)N * mr * sizeof(double2));
+  dal((void**)&H.red, (size_t)sms * 2 * 8 * mr * sizeof(double2));
+  size_t n2, nd, ni;
+  krylov_state_bytes(R, mr, &n2, &nd, &ni);
+  dal((void**)&H.hess, n2 * sizeof(double2));
+  dal((void**)&H.kstate, nd * sizeof(double));
+  dal((void**)&H.kflags, ni * sizeof(int));
+  dal((void**)&H.err, 2 * sizeof(int));
+  if (ok && cudaMallocHost((void**)&H.h_flags, 64) != cudaSuccess) ok = false;
+  if (!ok) {
+    asp_destroy(hd);
+    cudaGetLastError();
+    return fail(ASP_ERR_OOM, "device allocation failed (footprint " + std::to_string(Z.bytes) + " bytes)");
+  }
+  bool up = true;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    if (up && bytes && cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) up = false;
+  };
+  cp(H.k2, k2.data(), N * sizeof(double));
+  cp(H.ca, ca.data(), n * sizeof(double2));
+  cp(H.cc, cc.data(), n * sizeof(double2));
+  cp(H.cd, cd.data(), n * sizeof(double2));
+  cp(H.d_subs, H.subs.data(), H.subs.size() * sizeof(SubDesc));
+  cp(H.d_coef, H.coef.data(), H.coef.size() * sizeof(SweepCoef));
+  cp(H.d_toffR, H.toffR.data(), (m + 1) * sizeof(long long));
+  cp(H.d_toffL, H.toffL.data(), (m + 1) * sizeof(long long));
+  if (up && cudaMemset(H.W, 0, H.W_elems * esz) != cudaSuccess) up = false;
+  if (up && cudaMemset(H.err, 0, 2 * sizeof(int)) != cudaSuccess) up = false;
+  if (up && cudaDeviceSynchronize() != cudaSuccess) up = false;
+  if (!up) {
+    asp_destroy(hd);
+    return fail(ASP_ERR_CUDA, "uploading the setup data");
+  }
+  *out = hd;
+  return ASP_OK;
+}
+
+int asp_factor(asp_handle* hd, void* stream) {
+  if (!hd) return fail(ASP_ERR_INVALID, "null handle");
+  Handle& H = hd->h;
+  cudaStream_t s = (cudaStream_t)stream;
+  phase_begin(H, PH_FACTOR, s);
+  cudaError_t ce = launch_factor(H, s);
+  phase_end(H, s);
+  if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString(ce));
+  // transfer maps: columns of T_p^R and T_p^L in chunks of right-hand sides
+  if (H.m >= 3) {
+    const int cap = btsolve_rhs_capacity(H.n, H.wmaxRL, H.prec, true);
+    JobCache& jc = caches()[&H];
+    if (!jc.have_tmap) {
+      std::vector<Job> jobs;
+      for (int r0 = 0; r0 < H.n; r0 += cap)
+        for (int q = 2; q <= H.m - 1; ++q) {
+          jobs.push_back({H.subR[q], MODE_TMAP_R, r0, std::min(cap, H.n - r0)});
+          jobs.push_back({H.subL[q], MODE_TMAP_L, r0, std::min(cap, H.n - r0)});
+        }
+      int rc = upload_jobs(H, jobs, cap, H.wmaxRL, &jc.tmap);
+      if (rc != ASP_OK) return rc;
+      jc.have_tmap = true;
+    }
+    const JobList& L = jc.tmap;
+    SolveParams P = base_params(H, 1);
+    P.jobs = L.d;
+    P.njobs = L.n;
+    phase_begin(H, PH_TMAP, s);
+    ce = launch_btsolve(H, P, cap, H.wmaxRL, s);
+    phase_end(H, s);
+    if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("transfer-map launch: ") + cudaGetErrorString(ce));
+  }
+  int rc = check_err(H, s, "factor");
+  if (rc != ASP_OK) return rc;
+  H.factored = true;
+  return ASP_OK;
+}
+
+int asp_apply_preconditioner(asp_handle* hd, const void* r, void* z, int nrhs, void* stream) {
+  if (!hd || !r || !z) return fail(ASP_ERR_INVALID, "null argument");
+  Handle& H = hd->h;
+  if (nrhs < 1 || nrhs > H.prm.max_rhs) return fail(ASP_ERR_INVALID, "nrhs out of range");
+  if (r == z) return fail(ASP_ERR_INVALID, "r and z alias");
+  return apply_precond(H, (const double2*)r, (double2*)z, nrhs, (cudaStream_t)stream);
+}
+
+int asp_matvec(asp_handle* hd, const void* x, void* y, int nrhs, void* stream) {
+  if (!hd || !x || !y) return fail(ASP_ERR_INVALID, "null argument");
+  Handle& H = hd->h;
+  if (nrhs < 1 || nrhs > H.prm.max_rhs) return fail(ASP_ERR_INVALID, "nrhs out of range");
+  if (x == y) return fail(ASP_ERR_INVALID, "x and y alias");
+  phase_begin(H, PH_MATVEC, (cudaStream_t)stream);
+  cudaError_t ce = launch_matvec(H, (const double2*)x, (double2*)y, nrhs, (cudaStream_t)stream);
+  phase_end(H, (cudaStream_t)stream);
+  if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("matvec launch: ") + cudaGetErrorString(ce));
+  return ASP_OK;
+}
+
+int asp_subproblem_width(const asp_handle* hd, int kind, int p) {
+  if (!hd) return ASP_ERR_INVALID;
+  const Handle& H = hd->h;
+  if (p < 1 || p > H.m) return ASP_ERR_INVALID;
+  int idx = kind == KIND_M ? H.subM[p] : kind == KIND_R ? H.subR[p] : kind == KIND_L ? H.subL[p] : -1;
+  if (idx < 0) return ASP_ERR_INVALID;
+  return H.subs[idx].w;
+}
+
+int asp_subproblem_solve(asp_handle* hd, int kind, int p, const void* g, void* v, int nrhs, void* stream) {
+  if (!hd || !g || !v) return fail(ASP_ERR_INVALID, "null argument");
+  Handle& H = hd->h;
+  if (!H.factored) return fail(ASP_ERR_STATE, "subproblem solve before factor");
+  if (nrhs < 1 || nrhs > H.prm.max_rhs) return fail(ASP_ERR_INVALID, "nrhs out of range");
+  if (p < 1 || p > H.m) return fail(ASP_ERR_INVALID, "layer index out of range");
+  int idx = kind == KIND_M ? H.subM[p] : kind == KIND_R ? H.subR[p] : kind == KIND_L ? H.subL[p] : -1;
+  if (idx < 0) return fail(ASP_ERR_INVALID, "no such subproblem (H^R needs p >= 2, H^L needs p <= m-1)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int w = H.subs[idx].w;
+  const void* in = g;
+  if (H.prec == ASP_PREC_C64) {
+    if (launch_to_prec((const double2*)g, H.r_lo, (long long)w * H.n * nrhs, H.prec, s) != cudaSuccess)
+      return fail(ASP_ERR_CUDA, "to_prec launch");
+    in = H.r_lo;
+  }
+  const int cap = btsolve_rhs_capacity(nrhs, w, H.prec, false);
+  JobCache& jc = caches()[&H];
+  const long long key = (long long)idx * 1024 + nrhs;
+  auto it = jc.sub.find(key);
+  if (it == jc.sub.end()) {
+    std::vector<Job> jobs;
+    for (int r0 = 0; r0 < nrhs; r0 += cap) jobs.push_back({idx, MODE_SUB, r0, std::min(cap, nrhs - r0)});
+    JobList L0;
+    int rc = upload_jobs(H, jobs, cap, w, &L0);
+    if (rc != ASP_OK) return rc;
+    it = jc.sub.emplace(key, L0).first;
+  }
+  const JobList& L = it->second;
+  SolveParams P = base_params(H, nrhs);
+  P.in = in;
+  P.outSub = v;
+  P.jobs = L.d;
+  P.njobs = L.n;
+  cudaError_t ce = launch_btsolve(H, P, cap, w, s);
+  if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("subproblem launch: ") + cudaGetErrorString(ce));
+  return ASP_OK;
+}
+
+int asp_gmres_solve(asp_handle* hd, const void* f, void* u, int nrhs, double tol, int restart, int maxit,
+                    asp_solve_info* info_host, void* stream) {
+  if (!hd || !f || !u) return fail(ASP_ERR_INVALID, "null argument");
+  Handle& H = hd->h;
+  if (!H.factored) return fail(ASP_ERR_STATE, "solve before factor");
+  if (nrhs < 1 || nrhs > H.prm.max_rhs) return fail(ASP_ERR_INVALID, "nrhs out of range");
+  if (restart < 1 || restart > H.prm.restart) return fail(ASP_ERR_INVALID, "restart exceeds the setup value");
+  if (maxit < 1 || !(tol >= 0)) return fail(ASP_ERR_INVALID, "maxit must be >= 1 and tol >= 0");
+  if (f == u) return fail(ASP_ERR_INVALID, "f and u alias");
+  int rc = gmres_run(H, (const double2*)f, (double2*)u, nrhs, tol, restart, maxit, info_host, (cudaStream_t)stream);
+  if (rc != ASP_OK && rc != ASP_ERR_NOT_CONVERGED) return rc;
+  int rc2 = check_err(H, (cudaStream_t)stream, "fgmres");
+  return rc2 != ASP_OK ? rc2 : rc;
+}
+
+long long asp_take_launch_count(asp_handle* hd) {
+  if (!hd) return 0;
+  long long v = hd->h.launches;
+  hd->h.launches = 0;
+  return v;
+}
+
+}  // extern "C"

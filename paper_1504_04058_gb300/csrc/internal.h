@@ -1,0 +1,193 @@
+// internal.h -- host-side state of a libasp handle and the launch interfaces
+// between the translation units.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "asp.h"
+
+namespace asp {
+
+// Subproblem kinds (Section 3.1): H_q^M, H_p^R, H_p^L.
+enum SubKind : int { KIND_M = 0, KIND_R = 1, KIND_L = 2 };
+
+// One layer subproblem on its padded grid [lo, lo+w-1] along x2 (global
+// 1-based), full x1 range.  Ordered x2-fastest ("quasi-1D", Section 3.1) it is
+// block tridiagonal with n blocks (one per x1 node) of size w x w.
+struct SubDesc {
+  int kind;          // KIND_M / KIND_R / KIND_L
+  int p;             // layer index, 1-based
+  int lo;            // global x2 index of local column 0
+  int w;             // padded width (columns along x2)
+  int wp;            // leading dimension of a stored w x w block (>= w)
+  int xoff;          // X_p = local columns [xoff, xoff + xw)
+  int xw;
+  int prof;          // offset of this subproblem's sweep-axis coefficients
+  long long woff;    // element offset of block 0 of its factor
+  long long toff;    // element offset of its trace-transfer map (-1: none)
+};
+
+// Solve modes of the batched block-tridiagonal solver (btsolve.cu).
+enum SolveMode : int {
+  MODE_EMBED = 0,   // G~_q^M: right-hand side = input restricted to X_q
+  MODE_FILL_R = 1,  // G~_p^R: right-hand side = -(1/h^2) accR[p-1] on local column 0
+  MODE_FILL_L = 2,  // G~_p^L: right-hand side = -(1/h^2) accL[p+1] on local column w-1
+  MODE_TMAP_R = 3,  // transfer map of G~_p^R: unit boundary data, keep last column of X_p
+  MODE_TMAP_L = 4,  // transfer map of G~_p^L: unit boundary data, keep first column of X_p
+  MODE_SUB = 5,     // plain H^-1 g on the whole padded grid (checking entry point)
+};
+
+struct Job {
+  int sub;   // index into the SubDesc table
+  int mode;  // SolveMode
+  int rhs0;  // first right-hand side of this job
+  int nr;    // number of right-hand sides in this job
+};
+
+// Coefficients of the sweep-axis (x2) second difference of one subproblem,
+// local column j: up[j] couples j -> j+1, dn[j] couples j -> j-1, dg[j] is the
+// x2 part of the diagonal (Eq. (4) with the subproblem's s-profile).
+struct SweepCoef {
+  double2 up, dn, dg;
+};
+
+struct SolveParams {
+  const SubDesc* subs;
+  const Job* jobs;
+  int njobs;
+  int n;            // blocks per subproblem (= x1 nodes)
+  int ldv;          // right-hand-side stride of the vectors (= nrhs of the call)
+  double inv_h2;
+  const void* W;    // factor blocks W_k = S_k^-1
+  const double2* ca;  // a_k: coupling of block k to block k-1 (x1 stencil)
+  const double2* cc;  // c_k: coupling of block k to block k+1
+  const void* in;   // EMBED / SUB input (factor precision, RHS-interleaved)
+  void* outM;       // EMBED output restricted to X_q (factor precision)
+  void* outR;       // FILL_R output
+  void* outL;       // FILL_L output
+  void* accR;       // [m+1][n][ldv] right traces / accumulated right-going traces
+  void* accL;       // [m+1][n][ldv] left traces
+  void* tmap;       // transfer maps base
+  void* outSub;     // MODE_SUB output (complex128, [w][n][ldv])
+  void* zscr;       // forward-pass scratch, one slot per resident CTA
+  long long zslot;  // elements per slot
+  int* err;
+};
+
+struct ChainParams {
+  int n, m, ldv, nrhs;
+  const void* tmap;        // maps
+  const long long* toffR;  // [m+1] element offset of T_p^R (p = 2..m-1)
+  const long long* toffL;  // [m+1] element offset of T_p^L
+  void* accR;              // [m+1][n][ldv]
+  void* accL;
+  unsigned int* bar;       // two grid-barrier counters (R, L), zeroed before launch
+  int* err;
+};
+
+struct Handle;
+
+enum Phase : int {
+  PH_FACTOR = 0, PH_TMAP = 1, PH_EMBED = 2, PH_CHAIN = 3, PH_FILL = 4, PH_SUM = 5, PH_MATVEC = 6,
+  PH_KRYLOV = 7, PH_COUNT = 8
+};
+
+// Records CUDA events around launches when phase timing is enabled.
+void phase_begin(Handle& H, int phase, cudaStream_t s);
+void phase_end(Handle& H, cudaStream_t s);
+
+// ---- launchers (one translation unit each) ----
+cudaError_t launch_matvec(const Handle& H, const double2* x, double2* y, int nrhs, cudaStream_t s);
+cudaError_t launch_factor(Handle& H, cudaStream_t s);
+cudaError_t launch_btsolve(Handle& H, const SolveParams& P, int rhs_per_job, int wmax, cudaStream_t s);
+int btsolve_rhs_capacity(int nrhs, int wmax, int prec, bool tmap);
+cudaError_t launch_chain(Handle& H, const ChainParams& P, cudaStream_t s);
+cudaError_t launch_to_prec(const double2* in, void* out, long long count, int prec, cudaStream_t s);
+cudaError_t launch_sum3(const void* a, const void* b, const void* c, double2* z, long long count, int prec,
+                        cudaStream_t s);
+
+// ---- handle ----
+struct Handle {
+  asp_params prm{};
+  int n = 0, m = 0, prec = 0, gamma = 0, gamma_a = 0, b = 0;
+  double h = 0, inv_h2 = 0;
+  long long N = 0;  // n^2 grid points
+
+  // partition (host), 1-based arrays sized m+1
+  std::vector<int> x_lo, x_hi, alpha, beta;
+
+  // device: velocity term omega^2/c^2 (natural order), global x1/x2 stencil
+  // coefficients per node (the same profile on both axes)
+  double* k2 = nullptr;
+  double2* ca = nullptr;  // a_k = s_k s_{k-1/2} / h^2
+  double2* cc = nullptr;  // c_k = s_k s_{k+1/2} / h^2
+  double2* cd = nullptr;  // d_k = -s_k (s_{k+1/2} + s_{k-1/2}) / h^2
+
+  // subproblems
+  std::vector<SubDesc> subs;
+  SubDesc* d_subs = nullptr;
+  std::vector<SweepCoef> coef;  // concatenated sweep-axis coefficients
+  SweepCoef* d_coef = nullptr;
+  std::vector<int> subM, subR, subL;  // subproblem index per layer (-1 if none), size m+1
+  int wmax = 0, wmaxRL = 0;
+
+  // factors and transfer maps
+  void* W = nullptr;
+  size_t W_elems = 0;
+  void* tmap = nullptr;
+  size_t tmap_elems = 0;
+  std::vector<long long> toffR, toffL;
+  long long* d_toffR = nullptr;
+  long long* d_toffL = nullptr;
+  bool factored = false;
+
+  // apply workspace (factor precision), sized for max_rhs
+  void* r_lo = nullptr;   // converted input (c64 path only)
+  void* uM = nullptr;
+  void* uR = nullptr;
+  void* uL = nullptr;
+  void* accR = nullptr;
+  void* accL = nullptr;
+  void* zscr = nullptr;
+  long long zslot = 0;
+  int zslots = 0;
+  unsigned int* bar = nullptr;
+  Job* d_jobs = nullptr;
+  int jobs_cap = 0;
+
+  // Krylov workspace (complex128)
+  double2* V = nullptr;   // (restart+1) vectors
+  double2* Z = nullptr;   // restart vectors
+  double2* wv = nullptr;  // work vector
+  double* red = nullptr;  // reduction partials
+  double2* hess = nullptr;
+  double* kstate = nullptr;
+  int* kflags = nullptr;
+  int* h_flags = nullptr;  // pinned
+  double* h_state = nullptr;
+
+  int* err = nullptr;  // device error word [2]
+  long long launches = 0;
+  int num_sms = 0;
+
+  // phase timing
+  bool timing = false;
+  struct Rec { int phase; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> evpool;
+  int open_phase = -1;
+  cudaEvent_t open_ev = nullptr;
+};
+
+void set_detail(const std::string& s);
+int fail(int code, const std::string& detail);
+
+}  // namespace asp
+
+struct asp_handle {
+  asp::Handle h;
+};

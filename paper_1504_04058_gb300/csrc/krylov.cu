@@ -1,0 +1,473 @@
+// krylov.cu -- the FP64 outer solver: the 5-point PML operator A (Eq. (4) with
+// the PML on all four sides, Section 3.2) and right-preconditioned flexible
+// GMRES with restart (the Krylov solver of Section 3.2), with every vector
+// operation on the device.
+//
+// Vectors are complex128 in the RHS-interleaved layout (element (point, r) at
+// point*nrhs + r); each right-hand side has its own Krylov space.  Reductions
+// are two-stage and in a fixed order, so results do not depend on scheduling.
+// Arnoldi uses classical Gram-Schmidt applied twice (CGS2): equal to modified
+// Gram-Schmidt in exact arithmetic and two passes over the basis instead of j.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace asp {
+
+int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_t s);
+
+namespace {
+
+constexpr int kVecThreads = 256;
+constexpr int kDotChunk = 8;
+
+__device__ __forceinline__ double2 dmul(double2 a, double2 b) { return cmul(a, b); }
+
+// ------------------------------------------------------------------ matvec
+// (Au)_{i1,i2} = a_{i1} u_{i1-1} + c_{i1} u_{i1+1} + a_{i2} u_{i2-1} + c_{i2} u_{i2+1}
+//                + (d_{i1} + d_{i2} + omega^2/c^2) u,  zero outside the grid.
+__global__ void matvec_kernel(const double* __restrict__ k2, const double2* __restrict__ ca,
+                              const double2* __restrict__ cc, const double2* __restrict__ cd, int n,
+                              int nrhs, const double2* __restrict__ x, double2* __restrict__ y) {
+  const long long total = (long long)n * n * nrhs;
+  const long long rowst = (long long)n * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long pt = e / nrhs;
+    const int i1 = (int)(pt % n), i2 = (int)(pt / n);
+    const double2 u = x[e];
+    const double2 d1 = cd[i1], d2 = cd[i2];
+    double2 diag = make_double2(d1.x + d2.x + k2[pt], d1.y + d2.y);
+    double2 acc = dmul(diag, u);
+    if (i1 > 0) cfma(acc, ca[i1], x[e - nrhs]);
+    if (i1 < n - 1) cfma(acc, cc[i1], x[e + nrhs]);
+    if (i2 > 0) cfma(acc, ca[i2], x[e - rowst]);
+    if (i2 < n - 1) cfma(acc, cc[i2], x[e + rowst]);
+    y[e] = acc;
+  }
+}
+
+struct VecList {
+  const double2* v[kDotChunk];
+};
+
+// partial[b][j][r] = sum over this block's elements of conj(v_j) * w
+__global__ void multidot_kernel(VecList V, int J, const double2* __restrict__ w, long long count, int nrhs,
+                                double2* __restrict__ partial) {
+  __shared__ double2 red[kVecThreads];
+  const int bt = blockDim.x;  // a multiple of nrhs
+  const int t = threadIdx.x;
+  double2 acc[kDotChunk];
+#pragma unroll
+  for (int j = 0; j < kDotChunk; ++j) acc[j] = make_double2(0, 0);
+  for (long long e = (long long)blockIdx.x * bt + t; e < count; e += (long long)gridDim.x * bt) {
+    const double2 we = w[e];
+#pragma unroll
+    for (int j = 0; j < kDotChunk; ++j)
+      if (j < J) {
+        const double2 v = V.v[j][e];
+        acc[j].x = fma(v.x, we.x, fma(v.y, we.y, acc[j].x));
+        acc[j].y = fma(v.x, we.y, fma(-v.y, we.x, acc[j].y));
+      }
+  }
+  for (int j = 0; j < J; ++j) {
+    red[t] = acc[j];
+    __syncthreads();
+    if (t < nrhs) {
+      double2 s = make_double2(0, 0);
+      for (int q = t; q < bt; q += nrhs) { s.x += red[q].x; s.y += red[q].y; }
+      partial[((long long)blockIdx.x * kDotChunk + j) * nrhs + t] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// out[(j0 + j)][r] = sum_b partial[b][j][r]   (fixed block order)
+__global__ void dot_finish_kernel(const double2* __restrict__ partial, int nblocks, int J, int nrhs, int j0,
+                                  double2* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= J * nrhs) return;
+  const int j = idx / nrhs, r = idx % nrhs;
+  double2 s = make_double2(0, 0);
+  for (int b = 0; b < nblocks; ++b) {
+    const double2 v = partial[((long long)b * kDotChunk + j) * nrhs + r];
+    s.x += v.x; s.y += v.y;
+  }
+  out[(long long)(j0 + j) * nrhs + r] = s;
+}
+
+// w[e] += sgn * sum_j coef[(j0+j)][r] * v_j[e]
+__global__ void multiaxpy_kernel(VecList V, int J, const double2* __restrict__ coef, int j0, double sgn,
+                                 double2* __restrict__ w, long long count, int nrhs) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % nrhs);
+    double2 acc = w[e];
+#pragma unroll
+    for (int j = 0; j < kDotChunk; ++j)
+      if (j < J) {
+        double2 c = coef[(long long)(j0 + j) * nrhs + r];
+        c.x *= sgn; c.y *= sgn;
+        cfma(acc, c, V.v[j][e]);
+      }
+    w[e] = acc;
+  }
+}
+
+// dst[e] = src[e] * s[r]  (s real)
+__global__ void scale_kernel(const double2* __restrict__ src, const double* __restrict__ sc,
+                             double2* __restrict__ dst, long long count, int nrhs) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double s = sc[e % nrhs];
+    const double2 v = src[e];
+    dst[e] = make_double2(v.x * s, v.y * s);
+  }
+}
+
+// dst = a - b
+__global__ void sub_kernel(const double2* __restrict__ a, const double2* __restrict__ b, double2* __restrict__ dst,
+                           long long count) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double2 x = a[e], y = b[e];
+    dst[e] = make_double2(x.x - y.x, x.y - y.y);
+  }
+}
+
+// Per-right-hand-side Krylov state (all arrays [...][nrhs]).
+struct KState {
+  double2* h1;    // [restart+1][nrhs]  first CGS pass
+  double2* h2;    // [restart+1][nrhs]  second CGS pass
+  double2* hn2;   // [1][nrhs]  ||w||^2 (re)
+  double2* Rm;    // [restart][restart+1][nrhs]  rotated Hessenberg columns
+  double* cs;     // [restart][nrhs]
+  double2* sn;    // [restart][nrhs]
+  double2* g;     // [restart+1][nrhs]
+  double2* y;     // [restart][nrhs]
+  double* fnorm;  // [nrhs]
+  double* est;    // [nrhs]
+  double* inv;    // [nrhs] scale for the next basis vector
+  int* done;      // [nrhs] 1 once converged (or broke down)
+  int* kcur;      // [nrhs] columns in the current cycle
+  int* its;       // [nrhs] iterations until done
+  int* active;    // [1] number of right-hand sides still iterating
+};
+
+// Start of a restart cycle: beta = ||r||, g = [beta, 0..], inv = 1/beta.
+// On the first cycle also records ||f|| (r = f there).
+__global__ void cycle_start_kernel(KState K, int nrhs, int first, double tol) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const double beta = sqrt(K.hn2[r].x);
+  if (first) {
+    K.fnorm[r] = beta;
+    K.done[r] = (beta == 0.0);
+    K.its[r] = 0;
+    K.est[r] = beta == 0.0 ? 0.0 : 1.0;
+  }
+  K.kcur[r] = 0;
+  K.g[r] = make_double2(K.done[r] ? 0.0 : beta, 0.0);
+  K.inv[r] = (K.done[r] || beta == 0.0) ? 0.0 : 1.0 / beta;
+}
+
+// Column j of the Hessenberg matrix: h = h1 + h2 (rows 0..j), h_{j+1} = ||w||.
+// Applies the previous Givens rotations, forms the new one, updates g and the
+// residual estimate, and decides convergence.
+__global__ void arnoldi_update_kernel(KState K, int nrhs, int j, int restart, double tol, int its_now) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const double hn = sqrt(K.hn2[r].x);
+  if (K.done[r]) {
+    K.inv[r] = 0.0;
+    return;
+  }
+  double2* col = K.Rm + (long long)j * (restart + 1) * nrhs;
+  for (int i = 0; i <= j; ++i) {
+    double2 a = K.h1[(long long)i * nrhs + r], b = K.h2[(long long)i * nrhs + r];
+    col[(long long)i * nrhs + r] = make_double2(a.x + b.x, a.y + b.y);
+  }
+  double2 hj1 = make_double2(hn, 0.0);
+  for (int i = 0; i < j; ++i) {
+    const double c = K.cs[(long long)i * nrhs + r];
+    const double2 s = K.sn[(long long)i * nrhs + r];
+    const double2 hi = col[(long long)i * nrhs + r];
+    const double2 hi1 = (i + 1 == j + 1) ? hj1 : col[(long long)(i + 1) * nrhs + r];
+    // [c s; -conj(s) c] [hi; hi1]
+    double2 t = make_double2(c * hi.x, c * hi.y);
+    cfma(t, s, hi1);
+    double2 u = make_double2(c * hi1.x, c * hi1.y);
+    const double2 sc = make_double2(s.x, -s.y);
+    cfms(u, sc, hi);
+    col[(long long)i * nrhs + r] = t;
+    col[(long long)(i + 1) * nrhs + r] = u;
+  }
+  const double2 a = col[(long long)j * nrhs + r];
+  const double2 b = hj1;
+  double c;
+  double2 s;
+  const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+  if (bb == 0.0) {
+    c = 1.0; s = make_double2(0, 0);
+  } else if (aa == 0.0) {
+    c = 0.0; s = make_double2(b.x / bb, -b.y / bb);
+  } else {
+    const double rho = hypot(aa, bb);
+    c = aa / rho;
+    const double2 ph = make_double2(a.x / aa, a.y / aa);
+    const double2 cb = make_double2(b.x / rho, -b.y / rho);
+    s = cmul(ph, cb);
+  }
+  // new diagonal: c a + s b
+  double2 d = make_double2(c * a.x, c * a.y);
+  cfma(d, s, b);
+  col[(long long)j * nrhs + r] = d;
+  col[(long long)(j + 1) * nrhs + r] = make_double2(0, 0);
+  K.cs[(long long)j * nrhs + r] = c;
+  K.sn[(long long)j * nrhs + r] = s;
+  const double2 gj = K.g[(long long)j * nrhs + r];
+  const double2 sc = make_double2(s.x, -s.y);
+  double2 gj1 = cmul(sc, gj);
+  gj1.x = -gj1.x; gj1.y = -gj1.y;
+  K.g[(long long)(j + 1) * nrhs + r] = gj1;
+  K.g[(long long)j * nrhs + r] = make_double2(c * gj.x, c * gj.y);
+  K.kcur[r] = j + 1;
+  const double est = hypot(gj1.x, gj1.y) / K.fnorm[r];
+  K.est[r] = est;
+  bool stop = (tol > 0.0 && est <= tol) || hn == 0.0;
+  if (stop) {
+    K.done[r] = 1;
+    K.its[r] = its_now;
+  }
+  K.inv[r] = (stop || hn == 0.0) ? 0.0 : 1.0 / hn;
+}
+
+__global__ void count_active_kernel(KState K, int nrhs) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int a = 0;
+    for (int r = 0; r < nrhs; ++r) a += K.done[r] ? 0 : 1;
+    *K.active = a;
+  }
+}
+
+// y = R^{-1} g per right-hand side (k = kcur[r] columns); entries >= k are 0.
+__global__ void ysolve_kernel(KState K, int nrhs, int restart) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const int k = K.kcur[r];
+  for (int i = restart - 1; i >= 0; --i) {
+    if (i >= k) {
+      K.y[(long long)i * nrhs + r] = make_double2(0, 0);
+      continue;
+    }
+    double2 acc = K.g[(long long)i * nrhs + r];
+    for (int l = i + 1; l < k; ++l) {
+      const double2 Ril = K.Rm[((long long)l * (restart + 1) + i) * nrhs + r];
+      cfms(acc, Ril, K.y[(long long)l * nrhs + r]);
+    }
+    const double2 Rii = K.Rm[((long long)i * (restart + 1) + i) * nrhs + r];
+    K.y[(long long)i * nrhs + r] = cmul(acc, crecip(Rii));
+  }
+}
+
+int grid_for(long long count, int threads, int sms) {
+  long long g = (count + threads - 1) / threads;
+  long long cap = (long long)sms * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_matvec(const Handle& H, const double2* x, double2* y, int nrhs, cudaStream_t s) {
+  const long long total = H.N * nrhs;
+  matvec_kernel<<<grid_for(total, kVecThreads, H.num_sms), kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n,
+                                                                                nrhs, x, y);
+  const_cast<Handle&>(H).launches += 1;
+  return cudaGetLastError();
+}
+
+namespace {
+
+struct Krylov {
+  Handle& H;
+  int nrhs, restart;
+  long long count;
+  cudaStream_t s;
+  KState K;
+  int dot_blocks, dot_threads;
+  double2* partial;
+
+  double2* Vv(int i) const { return H.V + (long long)i * count; }
+  double2* Zv(int i) const { return H.Z + (long long)i * count; }
+
+  // out[j0 + j][r] = conj(V_j)^T w for j < J (J arbitrary, processed in chunks)
+  cudaError_t dots(const double2* const* vs, int J, const double2* w, double2* out) {
+    for (int j0 = 0; j0 < J; j0 += kDotChunk) {
+      VecList L{};
+      const int Jc = std::min(kDotChunk, J - j0);
+      for (int j = 0; j < Jc; ++j) L.v[j] = vs[j0 + j];
+      for (int j = Jc; j < kDotChunk; ++j) L.v[j] = vs[j0];
+      multidot_kernel<<<dot_blocks, dot_threads, 0, s>>>(L, Jc, w, count, nrhs, partial);
+      dot_finish_kernel<<<(Jc * nrhs + 127) / 128, 128, 0, s>>>(partial, dot_blocks, Jc, nrhs, j0, out);
+      H.launches += 2;
+    }
+    return cudaGetLastError();
+  }
+  cudaError_t axpys(const double2* const* vs, int J, const double2* coef, double sgn, double2* w) {
+    for (int j0 = 0; j0 < J; j0 += kDotChunk) {
+      VecList L{};
+      const int Jc = std::min(kDotChunk, J - j0);
+      for (int j = 0; j < Jc; ++j) L.v[j] = vs[j0 + j];
+      for (int j = Jc; j < kDotChunk; ++j) L.v[j] = vs[j0];
+      multiaxpy_kernel<<<grid_for(count, kVecThreads, H.num_sms), kVecThreads, 0, s>>>(L, Jc, coef, j0, sgn, w,
+                                                                                         count, nrhs);
+      H.launches += 1;
+    }
+    return cudaGetLastError();
+  }
+  cudaError_t norm2(const double2* w, double2* out) {
+    const double2* v[1] = {w};
+    return dots(v, 1, w, out);
+  }
+};
+
+}  // namespace
+
+int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int restart, int maxit,
+              asp_solve_info* info, cudaStream_t s) {
+  Krylov G{H, nrhs, restart, H.N * nrhs, s, {}, 0, 0, nullptr};
+  // carve the Krylov state out of the handle's blob
+  {
+    const int R = H.prm.restart;
+    double2* p2 = H.hess;
+    auto take2 = [&](long long cnt) { double2* q = p2; p2 += cnt; return q; };
+    G.K.h1 = take2((long long)(R + 1) * nrhs);
+    G.K.h2 = take2((long long)(R + 1) * nrhs);
+    G.K.hn2 = take2(nrhs);
+    G.K.Rm = take2((long long)R * (R + 1) * nrhs);
+    G.K.sn = take2((long long)R * nrhs);
+    G.K.g = take2((long long)(R + 1) * nrhs);
+    G.K.y = take2((long long)R * nrhs);
+    double* pd = H.kstate;
+    G.K.cs = pd; pd += (long long)R * nrhs;
+    G.K.fnorm = pd; pd += nrhs;
+    G.K.est = pd; pd += nrhs;
+    G.K.inv = pd; pd += nrhs;
+    int* pi = H.kflags;
+    G.K.done = pi; pi += nrhs;
+    G.K.kcur = pi; pi += nrhs;
+    G.K.its = pi; pi += nrhs;
+    G.K.active = pi;
+  }
+  G.dot_threads = nrhs * std::max(1, kVecThreads / nrhs);
+  G.dot_blocks = H.num_sms * 2;
+  G.partial = reinterpret_cast<double2*>(H.red);
+  const long long count = G.count;
+  const int gv = grid_for(count, kVecThreads, H.num_sms);
+  const int gr = (nrhs + 127) / 128;
+  cudaError_t ce = cudaSuccess;
+#define CK(x)                                                                              \
+  do {                                                                                     \
+    ce = (x);                                                                              \
+    if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("fgmres: ") + cudaGetErrorString(ce)); \
+  } while (0)
+
+  CK(cudaMemsetAsync(u, 0, sizeof(double2) * count, s));
+  int its = 0;
+  bool first = true;
+  std::vector<const double2*> vl(restart + 1);
+  int rc = ASP_OK;
+  while (true) {
+    // r = f - A u (u = 0 on the first cycle, so r = f)
+    const double2* rvec = f;
+    if (!first) {
+      CK(launch_matvec(H, u, H.wv, nrhs, s));
+      sub_kernel<<<gv, kVecThreads, 0, s>>>(f, H.wv, H.wv, count);
+      H.launches += 1;
+      rvec = H.wv;
+    }
+    CK(G.norm2(rvec, G.K.hn2));
+    cycle_start_kernel<<<gr, 128, 0, s>>>(G.K, nrhs, first ? 1 : 0, tol);
+    scale_kernel<<<gv, kVecThreads, 0, s>>>(rvec, G.K.inv, G.Vv(0), count, nrhs);
+    H.launches += 2;
+    first = false;
+    int active = nrhs;
+    for (int j = 0; j < restart && its < maxit; ++j) {
+      rc = apply_precond(H, G.Vv(j), G.Zv(j), nrhs, s);
+      if (rc != ASP_OK) return rc;
+      double2* w = G.Vv(j + 1);
+      phase_begin(H, PH_MATVEC, s);
+      CK(launch_matvec(H, G.Zv(j), w, nrhs, s));
+      phase_end(H, s);
+      phase_begin(H, PH_KRYLOV, s);
+      for (int i = 0; i <= j; ++i) vl[i] = G.Vv(i);
+      CK(G.dots(vl.data(), j + 1, w, G.K.h1));
+      CK(G.axpys(vl.data(), j + 1, G.K.h1, -1.0, w));
+      CK(G.dots(vl.data(), j + 1, w, G.K.h2));
+      CK(G.axpys(vl.data(), j + 1, G.K.h2, -1.0, w));
+      CK(G.norm2(w, G.K.hn2));
+      ++its;
+      arnoldi_update_kernel<<<gr, 128, 0, s>>>(G.K, nrhs, j, H.prm.restart, tol, its);
+      scale_kernel<<<gv, kVecThreads, 0, s>>>(w, G.K.inv, w, count, nrhs);
+      count_active_kernel<<<1, 32, 0, s>>>(G.K, nrhs);
+      phase_end(H, s);
+      H.launches += 3;
+      CK(cudaMemcpyAsync(H.h_flags, G.K.active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      active = H.h_flags[0];
+      if (active == 0) break;
+    }
+    // u += Z y  (per right-hand side, its own number of columns)
+    ysolve_kernel<<<gr, 128, 0, s>>>(G.K, nrhs, H.prm.restart);
+    H.launches += 1;
+    std::vector<const double2*> zl(restart);
+    for (int i = 0; i < restart; ++i) zl[i] = G.Zv(i);
+    CK(G.axpys(zl.data(), restart, G.K.y, 1.0, u));
+    if (active == 0 || its >= maxit) break;
+  }
+  // true residual ||f - A u|| / ||f||
+  CK(launch_matvec(H, u, H.wv, nrhs, s));
+  sub_kernel<<<gv, kVecThreads, 0, s>>>(f, H.wv, H.wv, count);
+  H.launches += 1;
+  CK(G.norm2(H.wv, G.K.hn2));
+  std::vector<double2> hn2(nrhs);
+  std::vector<double> fn(nrhs), est(nrhs);
+  std::vector<int> done(nrhs), itv(nrhs);
+  CK(cudaMemcpyAsync(hn2.data(), G.K.hn2, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(fn.data(), G.K.fnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(est.data(), G.K.est, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(done.data(), G.K.done, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(itv.data(), G.K.its, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+#undef CK
+  bool all = true;
+  for (int r = 0; r < nrhs; ++r) {
+    const double rel = fn[r] > 0 ? sqrt(hn2[r].x) / fn[r] : 0.0;
+    const bool conv = tol > 0.0 ? (rel <= tol * 1.0000001 || fn[r] == 0.0) : true;
+    if (!conv) all = false;
+    if (info) {
+      info[r].iterations = done[r] ? itv[r] : its;
+      info[r].converged = conv ? 1 : 0;
+      info[r].rel_res_est = est[r];
+      info[r].rel_res_true = rel;
+    }
+  }
+  if (tol > 0.0 && !all) return fail(ASP_ERR_NOT_CONVERGED, "fgmres: tolerance not reached within maxit");
+  return ASP_OK;
+}
+
+size_t krylov_state_bytes(int restart, int nrhs, size_t* n2, size_t* nd, size_t* ni) {
+  const long long R = restart;
+  *n2 = (size_t)((R + 1) * nrhs * 2 + nrhs + R * (R + 1) * nrhs + R * nrhs + (R + 1) * nrhs + R * nrhs);
+  *nd = (size_t)(R * nrhs + 3 * nrhs);
+  *ni = (size_t)(3 * nrhs + 1);
+  return *n2 * sizeof(double2) + *nd * sizeof(double) + *ni * sizeof(int);
+}
+
+}  // namespace asp

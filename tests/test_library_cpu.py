@@ -1,0 +1,113 @@
+"""CPU-side checks of the C-ABI library: it builds for sm_103a, loads, exports
+every entry point include/asp.h declares, and rejects invalid parameters on the
+host (no GPU compute is called here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1504_04058_gb300 import build
+    build.build()
+    from paper_1504_04058_gb300 import _lib
+    return _lib.load()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "asp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(asp_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declarations_match_binding():
+    from paper_1504_04058_gb300 import _lib
+    assert declared_symbols() == sorted(_lib.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1504_04058_gb300 import _lib
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (asp_\w+)", out))
+    for name in declared_symbols():
+        assert name in exported, name
+        assert hasattr(lib, name)
+
+
+def test_error_strings(lib):
+    assert lib.asp_error_string(0) == b"ASP_OK"
+    assert lib.asp_error_string(-4) == b"ASP_ERR_SMALL_PIVOT"
+    assert lib.asp_error_string(12345) == b"ASP_ERR_UNKNOWN"
+
+
+def test_invalid_parameters_rejected_on_host(lib):
+    from paper_1504_04058_gb300 import _lib, make_params
+    bad = [
+        make_params(127, 50.0, 1, 4),             # gamma < 2
+        make_params(127, -1.0, 12, 4),            # omega <= 0
+        make_params(20, 50.0, 12, 4),             # n too small for the PML
+        make_params(127, 50.0, 12, 0),            # b < 1
+        make_params(127, 50.0, 12, 4, max_rhs=0),
+        make_params(127, 50.0, 12, 4, restart=0),
+    ]
+    for p in bad:
+        assert lib.asp_footprint_bytes(ctypes.byref(p)) == 0
+        out = ctypes.c_void_p()
+        import numpy as np
+        c = np.ones(p.n ** 2)
+        code = lib.asp_setup(ctypes.byref(p), c.ctypes.data_as(ctypes.c_void_p), 0, ctypes.byref(out))
+        assert code == _lib.ASP_ERR_INVALID
+        assert out.value is None
+        assert lib.asp_last_error_detail()
+
+
+def test_3d_request_reports_unsupported(lib):
+    import numpy as np
+    from paper_1504_04058_gb300 import _lib, make_params
+    p = make_params(31, 50.0, 4, 4, dim=3)
+    out = ctypes.c_void_p()
+    c = np.ones(31 ** 3)
+    assert lib.asp_setup(ctypes.byref(p), c.ctypes.data_as(ctypes.c_void_p), 0,
+                         ctypes.byref(out)) == _lib.ASP_ERR_UNSUPPORTED
+
+
+def test_nonpositive_velocity_rejected(lib):
+    import numpy as np
+    from paper_1504_04058_gb300 import _lib, make_params
+    p = make_params(31, 20.0, 4, 3)
+    c = np.ones(31 * 31)
+    c[100] = 0.0
+    out = ctypes.c_void_p()
+    code = lib.asp_setup(ctypes.byref(p), c.ctypes.data_as(ctypes.c_void_p), 0, ctypes.byref(out))
+    assert code == _lib.ASP_ERR_INVALID
+
+
+def test_footprint_matches_layer_sizes(lib):
+    """The footprint grows with n and includes the factor bytes of every layer
+    subproblem: sum over 3m-2 subproblems of n*w*w_pad elements."""
+    from paper_1504_04058_gb300 import make_params
+    p1 = make_params(127, 16 * 3.14159, 12, 4, precision="c64", max_rhs=1, restart=8)
+    p2 = make_params(255, 32 * 3.14159, 12, 4, precision="c64", max_rhs=1, restart=8)
+    f1 = lib.asp_footprint_bytes(ctypes.byref(p1))
+    f2 = lib.asp_footprint_bytes(ctypes.byref(p2))
+    assert 0 < f1 < f2
+    n, g, b = 127, 12, 4
+    m = (n + 2 - 2 * g) // b
+    r = n + 2 - 2 * g - m * b
+    fac = 0
+    for q in range(1, m + 1):  # X_q^M: 2*gamma+b-2 columns, the last layer + remainder
+        w = 2 * g + b - 2 + (r if q == m else 0)
+        fac += n * w * (w + (w % 2))
+    for q in range(2, m + 1):  # X_q^R: gamma+b-1 columns
+        w = g + b - 1 + (r if q == m else 0)
+        fac += n * w * (w + (w % 2))
+    for q in range(1, m):      # X_q^L
+        w = g + b - 1
+        fac += n * w * (w + (w % 2))
+    assert f1 > fac * 8
