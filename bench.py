@@ -156,8 +156,13 @@ def run_asp(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
-    P = W.problem_2d_n1023_layered(nrhs=32, seed=1504 + rank)
-    prm = asp.make_params(P.n, P.omega, P.pml, P.b, C=P.C, precision="c64", max_rhs=P.nrhs, restart=40)
+    restart = 40
+    if args.workload == "n1023":
+        P = W.problem_2d_n1023_layered(nrhs=32, seed=1504 + rank)
+    else:  # smaller case of the same kernels, for profiler captures
+        P = W.small_problem(2, 511, 64 * math.pi, 16, 4, "layered", nrhs=32, seed=1504 + rank)
+        restart = 16
+    prm = asp.make_params(P.n, P.omega, P.pml, P.b, C=P.C, precision="c64", max_rhs=P.nrhs, restart=restart)
     h = asp.asp_setup(P.c, prm)
     f_host = torch.from_numpy(P.f).pin_memory()
     f = f_host.to(dev)
@@ -258,7 +263,8 @@ def run_asp(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64 factors / f64 krylov", "data": "synthetic",
-        "config": dict(WORKLOAD, parallelism=f"replicas x{world}"),
+        "config": dict(WORKLOAD, parallelism=f"replicas x{world}") if args.workload == "n1023" else
+        {"workload": "2d_helmholtz_n511_layered_omega64pi_pml16_b4_32rhs (profiling case)"},
         "iterations_max": max(its), "converged": conv, "worst_rel_res_true": worst_res,
         "solve_only_solves_per_s": world * P.nrhs / (solve_ms * 1e-3),
         "phase_ms_per_step": phase_ms,
@@ -352,6 +358,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["asp", "reference"], default="asp")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["n1023", "n511x32"], default="n1023",
+                    help="n511x32: the same kernels on a 2D n=511 problem with 32 RHS (profiling)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -169,7 +169,8 @@ Sizes sizes_for(const asp_params* p, int num_sms) {
   for (int q = 1; q <= P.m; ++q) addsub(P.m_lo[q], P.m_hi[q], false);
   for (int q = 2; q <= P.m; ++q) addsub(P.alpha[q], P.m_hi[q], true);
   for (int q = 1; q <= P.m - 1; ++q) addsub(P.m_lo[q], P.beta[q], true);
-  Z.tmap_elems = P.m >= 3 ? (size_t)2 * (P.m - 2) * n * n : 0;
+  const int ldT = (n + 1) & ~1;
+  Z.tmap_elems = P.m >= 3 ? (size_t)2 * (P.m - 2) * n * ldT : 0;
   Z.zslots = std::max(1, 2 * num_sms);
   Z.zslot = (size_t)n * Z.wmax * fmax_rhs_cap(p->factor_prec);
   const long long R = p->restart;
@@ -181,10 +182,10 @@ Sizes sizes_for(const asp_params* p, int num_sms) {
   bytes += Z.coef * sizeof(SweepCoef) + Z.nsub * sizeof(SubDesc);
   bytes += Z.W_elems * Z.esz + Z.tmap_elems * Z.esz;
   bytes += (size_t)Z.N * mr * Z.esz * (3 + (Z.esz == 8 ? 1 : 0));              // uM uR uL (+ r_lo)
-  bytes += (size_t)2 * (P.m + 1) * n * mr * Z.esz;                               // accR, accL
+  bytes += (size_t)2 * (P.m + 1) * n * ((mr + 1) & ~1) * Z.esz;                   // accR, accL
   bytes += (size_t)Z.zslots * Z.zslot * Z.esz;                                   // forward scratch
   bytes += (size_t)(2 * R + 2) * Z.N * mr * sizeof(double2);                     // V, Z, work
-  bytes += (size_t)num_sms * 2 * 8 * mr * sizeof(double2);                       // dot partials
+  bytes += (size_t)num_sms * 2 * 9 * mr * sizeof(double2);                       // dot partials
   bytes += kst + 64;
   Z.bytes = bytes;
   return Z;
@@ -205,20 +206,20 @@ __global__ void to_prec_kernel(const double2* __restrict__ in, Cx<R>* __restrict
     out[e] = cvt<R>(in[e]);
 }
 
-// z = uM + uR (except on X_1, where there is no right-going part) + uL (except on X_m)
+// z = uM + uR (except on X_1, where there is no right-going part) + uL (except
+// on X_m).  Grid: blockIdx.y = x2 column, blockIdx.x = chunk of its n*nrhs elements.
 template <typename R>
 __global__ void sum3_kernel(const Cx<R>* __restrict__ a, const Cx<R>* __restrict__ b, const Cx<R>* __restrict__ c,
-                            double2* __restrict__ z, long long count, long long per_col, long long r_from,
-                            long long l_below) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long col = e / per_col;  // 0-based x2 index
-    const Cx<R> va = a[e];
-    double re = (double)va.x, im = (double)va.y;
-    if (col >= r_from) { const Cx<R> vb = b[e]; re += (double)vb.x; im += (double)vb.y; }
-    if (col < l_below) { const Cx<R> vc = c[e]; re += (double)vc.x; im += (double)vc.y; }
-    z[e] = make_double2(re, im);
-  }
+                            double2* __restrict__ z, long long per_col, int r_from, int l_below) {
+  const long long er = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (er >= per_col) return;
+  const int col = blockIdx.y;  // 0-based x2 index
+  const long long e = (long long)col * per_col + er;
+  const Cx<R> va = a[e];
+  double re = (double)va.x, im = (double)va.y;
+  if (col >= r_from) { const Cx<R> vb = b[e]; re += (double)vb.x; im += (double)vb.y; }
+  if (col < l_below) { const Cx<R> vc = c[e]; re += (double)vc.x; im += (double)vc.y; }
+  z[e] = make_double2(re, im);
 }
 
 int vec_grid(long long count, int sms) {
@@ -323,10 +324,12 @@ SolveParams base_params(Handle& H, int ldv) {
   P.subs = H.d_subs;
   P.n = H.n;
   P.ldv = ldv;
+  P.ldacc = (ldv + 1) & ~1;
+  P.ldT = H.ldT;
   P.inv_h2 = H.inv_h2;
   P.W = H.W;
-  P.ca = H.ca;
-  P.cc = H.cc;
+  P.ca = H.prec == ASP_PREC_C64 ? (const void*)H.fc32.ca : (const void*)H.fc64.ca;
+  P.cc = H.prec == ASP_PREC_C64 ? (const void*)H.fc32.cc : (const void*)H.fc64.cc;
   P.outM = H.uM;
   P.outR = H.uR;
   P.outL = H.uL;
@@ -383,7 +386,7 @@ int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_
   const size_t esz = H.prec == ASP_PREC_C128 ? sizeof(double2) : sizeof(float2);
   for (int r0 = 0; r0 < nrhs; r0 += 32) {
     ChainParams C{};
-    C.n = H.n; C.m = H.m; C.ldv = nrhs; C.nrhs = std::min(32, nrhs - r0);
+    C.n = H.n; C.m = H.m; C.ldacc = (nrhs + 1) & ~1; C.ldT = H.ldT; C.nrhs = std::min(32, nrhs - r0);
     C.tmap = H.tmap; C.toffR = H.d_toffR; C.toffL = H.d_toffL;
     C.accR = (char*)H.accR + r0 * esz;
     C.accL = (char*)H.accL + r0 * esz;
@@ -402,16 +405,16 @@ int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("fill launch: ") + cudaGetErrorString(ce));
   // 4. u~_p = u~_{p,1:p-1} + u~_{p,p} + u~_{p,p+1:m}
   const long long per_col = (long long)H.n * nrhs;
-  const long long r_from = H.x_hi[1];     // 0-based first column of X_2
-  const long long l_below = H.x_lo[H.m] - 1;  // 0-based first column of X_m
+  const int r_from = H.x_hi[1];       // 0-based first column of X_2
+  const int l_below = H.x_lo[H.m] - 1;  // 0-based first column of X_m
   phase_begin(H, PH_SUM, s);
+  const dim3 sgrid((unsigned)((per_col + 255) / 256), (unsigned)H.n);
   if (H.prec == ASP_PREC_C64)
-    sum3_kernel<float><<<vec_grid(count, H.num_sms), 256, 0, s>>>((float2*)H.uM, (float2*)H.uR, (float2*)H.uL, z,
-                                                                  count, per_col, r_from, l_below);
+    sum3_kernel<float><<<sgrid, 256, 0, s>>>((float2*)H.uM, (float2*)H.uR, (float2*)H.uL, z, per_col, r_from,
+                                             l_below);
   else
-    sum3_kernel<double><<<vec_grid(count, H.num_sms), 256, 0, s>>>((double2*)H.uM, (double2*)H.uR,
-                                                                   (double2*)H.uL, z, count, per_col, r_from,
-                                                                   l_below);
+    sum3_kernel<double><<<sgrid, 256, 0, s>>>((double2*)H.uM, (double2*)H.uR, (double2*)H.uL, z, per_col, r_from,
+                                              l_below);
   phase_end(H, s);
   H.launches += 1;
   ce = cudaGetLastError();
@@ -496,6 +499,8 @@ void asp_destroy(asp_handle* hd) {
                   H.uM, H.uR, H.uL, H.accR, H.accL, H.zscr, H.bar, H.V, H.Z, H.wv, H.red, H.hess, H.kstate,
                   H.kflags, H.err};
   for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (void* p : H.coef_bufs)
     if (p) cudaFree(p);
   if (H.h_flags) cudaFreeHost(H.h_flags);
   delete hd;
@@ -609,12 +614,17 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
     H.subL[q] = add(KIND_L, q, P.m_lo[q], H.beta[q], pr);
   }
   H.W_elems = (size_t)woff;
+  if (H.wmax > 64) {
+    asp_destroy(hd);
+    return fail(ASP_ERR_UNSUPPORTED, "padded layer width 2*gamma_a + b - 2 (+ remainder) exceeds 64 columns");
+  }
   // transfer maps T_p^R, T_p^L for p = 2..m-1
   H.toffR.assign(m + 1, 0); H.toffL.assign(m + 1, 0);
+  H.ldT = (n + 1) & ~1;
   long long toff = 0;
   for (int q = 2; q <= m - 1; ++q) {
-    H.toffR[q] = toff; H.subs[H.subR[q]].toff = toff; toff += (long long)n * n;
-    H.toffL[q] = toff; H.subs[H.subL[q]].toff = toff; toff += (long long)n * n;
+    H.toffR[q] = toff; H.subs[H.subR[q]].toff = toff; toff += (long long)n * H.ldT;
+    H.toffL[q] = toff; H.subs[H.subL[q]].toff = toff; toff += (long long)n * H.ldT;
   }
   H.tmap_elems = (size_t)toff;
 
@@ -641,8 +651,8 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   dal(&H.uM, (size_t)N * mr * esz);
   dal(&H.uR, (size_t)N * mr * esz);
   dal(&H.uL, (size_t)N * mr * esz);
-  dal(&H.accR, (size_t)(m + 1) * n * mr * esz);
-  dal(&H.accL, (size_t)(m + 1) * n * mr * esz);
+  dal(&H.accR, (size_t)(m + 1) * n * ((mr + 1) & ~1) * esz);
+  dal(&H.accL, (size_t)(m + 1) * n * ((mr + 1) & ~1) * esz);
   H.zslots = Z.zslots;
   H.zslot = (long long)Z.zslot;
   dal(&H.zscr, (size_t)Z.zslots * Z.zslot * esz);
@@ -651,7 +661,7 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   dal((void**)&H.V, (size_t)(R + 1) * N * mr * sizeof(double2));
   dal((void**)&H.Z, (size_t)R * N * mr * sizeof(double2));
   dal((void**)&H.wv, (size_t)N * mr * sizeof(double2));
-  dal((void**)&H.red, (size_t)sms * 2 * 8 * mr * sizeof(double2));
+  dal((void**)&H.red, (size_t)sms * 2 * 9 * mr * sizeof(double2));
   size_t n2, nd, ni;
   krylov_state_bytes(R, mr, &n2, &nd, &ni);
   dal((void**)&H.hess, n2 * sizeof(double2));
@@ -676,6 +686,44 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   cp(H.d_coef, H.coef.data(), H.coef.size() * sizeof(SweepCoef));
   cp(H.d_toffR, H.toffR.data(), (m + 1) * sizeof(long long));
   cp(H.d_toffL, H.toffL.data(), (m + 1) * sizeof(long long));
+  // factor-precision copies of the layer coefficients
+  {
+    const size_t nc = H.coef.size();
+    std::vector<double2> upv(nc), dnv(nc), dgv(nc);
+    for (size_t i = 0; i < nc; ++i) { upv[i] = H.coef[i].up; dnv[i] = H.coef[i].dn; dgv[i] = H.coef[i].dg; }
+    auto put = [&](const void* hsrc, size_t bytes) -> void* {
+      void* d = nullptr;
+      if (!up || cudaMalloc(&d, bytes ? bytes : 16) != cudaSuccess) { up = false; return nullptr; }
+      H.coef_bufs.push_back(d);
+      if (bytes && cudaMemcpy(d, hsrc, bytes, cudaMemcpyHostToDevice) != cudaSuccess) up = false;
+      return d;
+    };
+    if (H.prec == ASP_PREC_C128) {
+      H.fc64.ca = (const double2*)put(ca.data(), n * sizeof(double2));
+      H.fc64.cc = (const double2*)put(cc.data(), n * sizeof(double2));
+      H.fc64.cd = (const double2*)put(cd.data(), n * sizeof(double2));
+      H.fc64.k2 = (const double*)put(k2.data(), N * sizeof(double));
+      H.fc64.up = (const double2*)put(upv.data(), nc * sizeof(double2));
+      H.fc64.dn = (const double2*)put(dnv.data(), nc * sizeof(double2));
+      H.fc64.dg = (const double2*)put(dgv.data(), nc * sizeof(double2));
+    } else {
+      auto f2 = [](const std::vector<double2>& v) {
+        std::vector<float2> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].x, (float)v[i].y);
+        return o;
+      };
+      std::vector<float> k2f(N);
+      for (long long i = 0; i < N; ++i) k2f[i] = (float)k2[i];
+      auto caf = f2(ca), ccf = f2(cc), cdf = f2(cd), upf = f2(upv), dnf = f2(dnv), dgf = f2(dgv);
+      H.fc32.ca = (const float2*)put(caf.data(), n * sizeof(float2));
+      H.fc32.cc = (const float2*)put(ccf.data(), n * sizeof(float2));
+      H.fc32.cd = (const float2*)put(cdf.data(), n * sizeof(float2));
+      H.fc32.k2 = (const float*)put(k2f.data(), N * sizeof(float));
+      H.fc32.up = (const float2*)put(upf.data(), nc * sizeof(float2));
+      H.fc32.dn = (const float2*)put(dnf.data(), nc * sizeof(float2));
+      H.fc32.dg = (const float2*)put(dgf.data(), nc * sizeof(float2));
+    }
+  }
   if (up && cudaMemset(H.W, 0, H.W_elems * esz) != cudaSuccess) up = false;
   if (up && cudaMemset(H.err, 0, 2 * sizeof(int)) != cudaSuccess) up = false;
   if (up && cudaDeviceSynchronize() != cudaSuccess) up = false;

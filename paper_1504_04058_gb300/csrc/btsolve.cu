@@ -7,12 +7,20 @@
 // btfactor.cu (W_k = S_k^{-1}):
 //     forward   z_k = W_k (g_k - a_k z_{k-1}),           k = k0 .. n-1
 //     backward  x_{n-1} = z_{n-1},  x_k = z_k - c_k W_k x_{k+1},   k = n-2 .. 0
-// Each step is a dense w x w block times a w x nr panel of right-hand sides.
-// The W_k blocks stream from HBM through a 3-stage shared-memory ring filled by
-// 1D bulk (TMA) copies that complete on mbarriers; the per-step right-hand
-// side entries (and, in the backward pass, the z_k saved by the forward pass)
-// stream through a per-thread cp.async ring.  One __syncthreads per step
-// publishes the new w x nr panel.
+// Each step multiplies the dense w x w block W_k by a w x NR panel of
+// right-hand sides.  Work split: every thread owns a 2-row x TC-column tile of
+// the panel (rows i0, i0+1; right-hand sides r0 .. r0+TC-1) for the whole job,
+// so the recurrences (z_{k-1} -> y_k, x_{k+1} -> x_k) stay in its registers;
+// a warp covers (32/LC)*2 rows x LC*TC right-hand sides, the CTA stacks warps
+// over rows (and, for 64 right-hand sides, over two column blocks).  The inner
+// product loads two rows of W_k (one 16-byte shared load for complex64) and TC
+// panel entries per column j and issues 8*TC FMAs.
+//
+// Data movement: the W_k blocks stream from HBM through a 3-stage
+// shared-memory ring filled by 1D bulk (TMA) copies that complete on
+// mbarriers; the per-step right-hand-side entries (and, in the backward pass,
+// the z_k saved by the forward pass in a per-CTA scratch slot) stream through
+// a per-thread cp.async ring.  One __syncthreads per step publishes the panel.
 //
 // Modes (what g_k is and what is written):
 //   EMBED   G~_q^M f_q: g = input on the rows of X_q;  writes x on X_q to outM,
@@ -36,41 +44,87 @@ constexpr int kRing = 3;    // per-thread input ring depth
 
 struct Geometry {
   int wcap;    // largest w in the launch
-  int wstage;  // elements of one W stage (largest w*wp)
+  int wstage;  // elements of one W stage (largest w*wp, plus slack for the row tiles)
 };
 
-template <typename R, int NT, int RL, int RQ, int RS>
-struct Layout {
+__host__ __device__ inline size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
+
+template <typename R, int TC, int LC, int NCW>
+struct Tiling {
   using C = Cx<R>;
-  static constexpr int NR = RL * RQ;
+  static constexpr int TR = 2;                 // rows per thread
+  static constexpr int WR = (32 / LC) * TR;    // rows per warp
+  static constexpr int WC = LC * TC;           // right-hand sides per warp
+  static constexpr int NR = WC * NCW;          // right-hand sides per CTA
+  static constexpr int E = TR * TC;            // panel entries per thread
   __host__ __device__ static size_t bars() { return 64; }
   __host__ __device__ static size_t wst(const Geometry& g) { return (size_t)kStages * g.wstage * sizeof(C); }
   __host__ __device__ static size_t ybuf(const Geometry& g) { return (size_t)2 * g.wcap * NR * sizeof(C); }
-  __host__ __device__ static size_t ring() { return (size_t)kRing * RS * RQ * NT * sizeof(C); }
-  __host__ __device__ static size_t total(const Geometry& g) {
-    auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
-    return al(bars()) + al(wst(g)) + al(ybuf(g)) + al(ring());
+  __host__ __device__ static size_t ring(int nt) { return (size_t)kRing * E * nt * sizeof(C); }
+  __host__ __device__ static size_t total(const Geometry& g, int nt) {
+    return align128(bars()) + align128(wst(g)) + align128(ybuf(g)) + align128(ring(nt));
   }
 };
 
-template <typename R, int NT, int RL, int RQ, int RS>
-__global__ void __launch_bounds__(NT) btsolve_kernel(SolveParams P, Geometry G) {
+// ---- vector shared-memory access of a complex pair / single
+template <typename C> struct Vec2;
+template <> struct Vec2<float2> {
+  __device__ static void ld(const float2* p, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+  }
+  __device__ static void st(float2* p, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+  }
+};
+template <> struct Vec2<double2> {
+  __device__ static void ld(const double2* p, double2& a, double2& b) { a = p[0]; b = p[1]; }
+  __device__ static void st(double2* p, double2 a, double2 b) { p[0] = a; p[1] = b; }
+};
+
+// A thread's TC panel entries: for TC = 1 one column; for TC >= 2 pairs of
+// adjacent columns placed 2*LC apart, so that the LC lanes sharing a row read
+// and write one contiguous span per pair (no shared-memory bank conflicts).
+template <typename C, int TC, int PS> __device__ __forceinline__ void ld_cols(const C* p, C (&v)[TC]) {
+  if constexpr (TC == 1) {
+    v[0] = p[0];
+  } else {
+#pragma unroll
+    for (int c = 0; c < TC; c += 2) Vec2<C>::ld(p + (c / 2) * PS, v[c], v[c + 1]);
+  }
+}
+template <typename C, int TC, int PS> __device__ __forceinline__ void st_cols(C* p, const C (&v)[TC]) {
+  if constexpr (TC == 1) {
+    p[0] = v[0];
+  } else {
+#pragma unroll
+    for (int c = 0; c < TC; c += 2) Vec2<C>::st(p + (c / 2) * PS, v[c], v[c + 1]);
+  }
+}
+
+template <typename R, int TC, int LC, int NCW>
+__global__ void __launch_bounds__(512) btsolve_kernel(SolveParams P, Geometry G) {
   using C = Cx<R>;
-  using LY = Layout<R, NT, RL, RQ, RS>;
-  constexpr int RG = NT / RL;
-  constexpr int NR = RL * RQ;
-  constexpr int RSQ = RS * RQ;
+  using T = Tiling<R, TC, LC, NCW>;
+  constexpr int TR = T::TR, WR = T::WR, WC = T::WC, NR = T::NR, E = T::E;
+  constexpr int CB = (int)sizeof(C);
   extern __shared__ __align__(128) unsigned char smem[];
-  auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
+  const int NT = blockDim.x;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  C* Wst = reinterpret_cast<C*>(smem + al(LY::bars()));
-  C* ybuf = reinterpret_cast<C*>(smem + al(LY::bars()) + al(LY::wst(G)));
-  C* ring = reinterpret_cast<C*>(smem + al(LY::bars()) + al(LY::wst(G)) + al(LY::ybuf(G)));
+  C* Wst = reinterpret_cast<C*>(smem + align128(T::bars()));
+  C* ybuf = reinterpret_cast<C*>(smem + align128(T::bars()) + align128(T::wst(G)));
+  C* ring = reinterpret_cast<C*>(smem + align128(T::bars()) + align128(T::wst(G)) + align128(T::ybuf(G)));
   __shared__ int s_abort;
 
   const int tid = threadIdx.x;
-  const int tr = tid % RL, ti = tid / RL;
-  const int n = P.n, ldv = P.ldv;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int wr = warp / NCW, wc = warp % NCW;
+  constexpr int PS = 2 * LC;                  // column distance between a thread's pairs
+  const int i0 = wr * WR + (lane / LC) * TR;  // first row of this thread's tile
+  const int r0 = wc * WC + (TC == 1 ? (lane % LC) : 2 * (lane % LC));  // its first column
+  auto rhs_of = [&](int c) { return TC == 1 ? r0 : r0 + (c & 1) + (c >> 1) * PS; };
+  const int n = P.n, ldv = P.ldv, lda = P.ldacc, ldT = P.ldT;
   const C* __restrict__ Wg = reinterpret_cast<const C*>(P.W);
   C* zslot = reinterpret_cast<C*>(P.zscr) + (long long)blockIdx.x * P.zslot;
   const C neg_ih2 = cmake<R>(R(-P.inv_h2), R(0));
@@ -81,7 +135,7 @@ __global__ void __launch_bounds__(NT) btsolve_kernel(SolveParams P, Geometry G) 
     fence_mbar_init();
   }
   __syncthreads();
-  uint32_t wuse = 0;  // W stages consumed so far (all threads track it identically)
+  uint32_t wuse = 0;  // W stages consumed so far (identical in every thread)
 
   for (int job = blockIdx.x; job < P.njobs; job += gridDim.x) {
     const Job J = P.jobs[job];
@@ -92,11 +146,11 @@ __global__ void __launch_bounds__(NT) btsolve_kernel(SolveParams P, Geometry G) 
     const int k0 = tmap ? rhs0 : 0;
     const int nf = n - k0;
     const int L = nf + (n - 1);
-    const uint32_t bbytes = (uint32_t)(w * wp * sizeof(C));
+    const uint32_t bbytes = (uint32_t)(w * wp * CB);
     const C* Wsub = Wg + S.woff;
     auto blk = [&](int q) { return q < nf ? k0 + q : n - 2 - (q - nf); };
 
-    __syncthreads();  // previous job's last reads of the W ring and ybuf are done
+    __syncthreads();  // the previous job's last reads of the W ring and panels are done
     if (tid == 0) {
       for (int t = 0; t < kStages && t < L; ++t) {
         const int st = (wuse + t) % kStages;
@@ -105,49 +159,43 @@ __global__ void __launch_bounds__(NT) btsolve_kernel(SolveParams P, Geometry G) 
       }
     }
 
-    // ---- per-thread input ring
+    // which of this thread's entries take input in the forward pass
+    auto row_has_input = [&](int i) {
+      if (mode == MODE_EMBED) return i >= xoff && i < xoff + xw;
+      if (mode == MODE_FILL_R) return i == 0;
+      if (mode == MODE_FILL_L) return i == w - 1;
+      if (mode == MODE_SUB) return i < w;
+      return false;
+    };
     const C* inM = reinterpret_cast<const C*>(P.in);
     const C* accRp = reinterpret_cast<const C*>(P.accR);
     const C* accLp = reinterpret_cast<const C*>(P.accL);
     auto load_step = [&](int q2) {
       if (q2 < L) {
         const int kk = blk(q2);
-        C* slot = ring + (size_t)(q2 % kRing) * RSQ * NT;
+        C* slot = ring + (size_t)(q2 % kRing) * E * NT;
         if (q2 < nf) {
-          if (mode == MODE_EMBED || mode == MODE_FILL_R || mode == MODE_FILL_L || mode == MODE_SUB) {
 #pragma unroll
-            for (int s = 0; s < RS; ++s) {
-              const int i = ti + RG * s;
-              if (i >= w) continue;
+          for (int a = 0; a < TR; ++a) {
+            const int i = i0 + a;
+            if (i >= w || !row_has_input(i)) continue;
+            const C* src;
+            if (mode == MODE_EMBED) src = inM + ((long long)(lo - 1 + i) * n + kk) * ldv + rhs0;
+            else if (mode == MODE_FILL_R) src = accRp + ((long long)(p - 1) * n + kk) * lda + rhs0;
+            else if (mode == MODE_FILL_L) src = accLp + ((long long)(p + 1) * n + kk) * lda + rhs0;
+            else src = inM + ((long long)i * n + kk) * ldv + rhs0;
 #pragma unroll
-              for (int qq = 0; qq < RQ; ++qq) {
-                const int r = tr + RL * qq;
-                if (r >= nr) continue;
-                const C* src = nullptr;
-                if (mode == MODE_EMBED) {
-                  if (i >= xoff && i < xoff + xw) src = inM + ((long long)(lo - 1 + i) * n + kk) * ldv + rhs0 + r;
-                } else if (mode == MODE_FILL_R) {
-                  if (i == 0) src = accRp + ((long long)(p - 1) * n + kk) * ldv + rhs0 + r;
-                } else if (mode == MODE_FILL_L) {
-                  if (i == w - 1) src = accLp + ((long long)(p + 1) * n + kk) * ldv + rhs0 + r;
-                } else {
-                  src = inM + ((long long)i * n + kk) * ldv + rhs0 + r;
-                }
-                if (src) cp_async<sizeof(C)>(slot + (size_t)(s * RQ + qq) * NT + tid, src);
-              }
-            }
+            for (int c = 0; c < TC; ++c)
+              if (rhs_of(c) < nr) cp_async<CB>(slot + (size_t)(a * TC + c) * NT + tid, src + rhs_of(c));
           }
         } else if (kk >= k0 && kk <= n - 3) {
 #pragma unroll
-          for (int s = 0; s < RS; ++s) {
-            const int i = ti + RG * s;
+          for (int a = 0; a < TR; ++a) {
+            const int i = i0 + a;
             if (i >= w) continue;
 #pragma unroll
-            for (int qq = 0; qq < RQ; ++qq) {
-              const int r = tr + RL * qq;
-              cp_async<sizeof(C)>(slot + (size_t)(s * RQ + qq) * NT + tid,
-                                  zslot + ((long long)kk * w + i) * NR + r);
-            }
+            for (int c = 0; c < TC; ++c)
+              cp_async<CB>(slot + (size_t)(a * TC + c) * NT + tid, zslot + ((long long)kk * w + i) * NR + rhs_of(c));
           }
         }
       }
@@ -155,53 +203,59 @@ __global__ void __launch_bounds__(NT) btsolve_kernel(SolveParams P, Geometry G) 
     };
     for (int t = 0; t < kRing - 1; ++t) load_step(t);
 
-    C zprev[RS][RQ], zkeep[RS][RQ], xprev[RS][RQ];
+    // carry: z_{k-1} in the forward pass, x_{k+1} in the backward pass
+    C carry[TR][TC], zkeep[TR][TC];
 #pragma unroll
-    for (int s = 0; s < RS; ++s)
+    for (int a = 0; a < TR; ++a)
 #pragma unroll
-      for (int qq = 0; qq < RQ; ++qq) zprev[s][qq] = zkeep[s][qq] = xprev[s][qq] = czero<R>();
+      for (int c = 0; c < TC; ++c) carry[a][c] = zkeep[a][c] = czero<R>();
 
+    const C* cap = reinterpret_cast<const C*>(P.ca);
+    const C* ccp = reinterpret_cast<const C*>(P.cc);
+    C ak_next = cap[blk(0)], ck_next = ccp[blk(0)];
     for (int q = 0; q < L; ++q) {
       const int k = blk(q);
       const bool fwd = q < nf;
+      const C a_k = ak_next;
+      const C c_k = ck_next;
+      if (q + 1 < L) {  // prefetch next step's coupling coefficients
+        const int kn = blk(q + 1);
+        ak_next = cap[kn];
+        ck_next = ccp[kn];
+      }
       load_step(q + kRing - 1);
       cp_async_wait<kRing - 1>();
-      const C* slot = ring + (size_t)(q % kRing) * RSQ * NT;
+      const C* slot = ring + (size_t)(q % kRing) * E * NT;
       C* yb = ybuf + (size_t)(q & 1) * G.wcap * NR;
 
-      // ---- right-hand panel of this step
-      const double2 ak = P.ca[k];
-      const C a_k = cmake<R>(R(ak.x), R(ak.y));
+      // ---- this step's panel rows of the thread's tile
 #pragma unroll
-      for (int s = 0; s < RS; ++s) {
-        const int i = ti + RG * s;
+      for (int a = 0; a < TR; ++a) {
+        const int i = i0 + a;
         if (i >= w) continue;
+        C y[TC];
+        if (fwd) {
+          const bool has = row_has_input(i);
 #pragma unroll
-        for (int qq = 0; qq < RQ; ++qq) {
-          const int r = tr + RL * qq;
-          C y;
-          if (fwd) {
+          for (int c = 0; c < TC; ++c) {
+            const int r = rhs_of(c);
             C g = czero<R>();
-            if (mode == MODE_EMBED) {
-              if (i >= xoff && i < xoff + xw && r < nr) g = slot[(size_t)(s * RQ + qq) * NT + tid];
-            } else if (mode == MODE_FILL_R) {
-              if (i == 0 && r < nr) g = cmul(neg_ih2, slot[(size_t)(s * RQ + qq) * NT + tid]);
-            } else if (mode == MODE_FILL_L) {
-              if (i == w - 1 && r < nr) g = cmul(neg_ih2, slot[(size_t)(s * RQ + qq) * NT + tid]);
-            } else if (mode == MODE_SUB) {
-              if (r < nr) g = slot[(size_t)(s * RQ + qq) * NT + tid];
+            if (has && r < nr) {
+              g = slot[(size_t)(a * TC + c) * NT + tid];
+              if (mode == MODE_FILL_R || mode == MODE_FILL_L) g = cmul(neg_ih2, g);
             } else if (mode == MODE_TMAP_R) {
               if (i == 0 && r < nr && k == rhs0 + r) g = neg_ih2;
-            } else {  // MODE_TMAP_L
+            } else if (mode == MODE_TMAP_L) {
               if (i == w - 1 && r < nr && k == rhs0 + r) g = neg_ih2;
             }
-            y = g;
-            cfms(y, a_k, zprev[s][qq]);
-          } else {
-            y = xprev[s][qq];
+            y[c] = g;
+            cfms(y[c], a_k, carry[a][c]);
           }
-          yb[i * NR + r] = y;
+        } else {
+#pragma unroll
+          for (int c = 0; c < TC; ++c) y[c] = carry[a][c];
         }
+        st_cols<C, TC, PS>(yb + (size_t)i * NR + r0, y);
       }
       __syncthreads();
       if (s_abort) return;
@@ -218,78 +272,75 @@ __global__ void __launch_bounds__(NT) btsolve_kernel(SolveParams P, Geometry G) 
       }
       const C* Wk = Wst + (size_t)st * G.wstage;
 
-      // ---- acc = W_k * panel
-      C acc[RS][RQ];
+      // ---- acc = W_k * panel on the thread's 2 x TC tile
+      C acc[TR][TC];
 #pragma unroll
-      for (int s = 0; s < RS; ++s)
+      for (int a = 0; a < TR; ++a)
 #pragma unroll
-        for (int qq = 0; qq < RQ; ++qq) acc[s][qq] = czero<R>();
+        for (int c = 0; c < TC; ++c) acc[a][c] = czero<R>();
+      if (i0 < w) {
 #pragma unroll 2
-      for (int j = 0; j < w; ++j) {
-        C yv[RQ];
+        for (int j = 0; j < w; ++j) {
+          C yv[TC];
+          ld_cols<C, TC, PS>(yb + (size_t)j * NR + r0, yv);
+          C w0, w1;
+          Vec2<C>::ld(Wk + (size_t)j * wp + i0, w0, w1);
 #pragma unroll
-        for (int qq = 0; qq < RQ; ++qq) yv[qq] = yb[j * NR + tr + RL * qq];
-        const C* Wc = Wk + j * wp;
-#pragma unroll
-        for (int s = 0; s < RS; ++s) {
-          const int i = ti + RG * s;
-          if (i < w) {
-            const C wv = Wc[i];
-#pragma unroll
-            for (int qq = 0; qq < RQ; ++qq) cfma(acc[s][qq], wv, yv[qq]);
+          for (int c = 0; c < TC; ++c) {
+            cfma(acc[0][c], w0, yv[c]);
+            cfma(acc[1][c], w1, yv[c]);
           }
         }
       }
 
       // ---- epilogue
-      const double2 ck = P.cc[k];
-      const C c_k = cmake<R>(R(ck.x), R(ck.y));
 #pragma unroll
-      for (int s = 0; s < RS; ++s) {
-        const int i = ti + RG * s;
+      for (int a = 0; a < TR; ++a) {
+        const int i = i0 + a;
         if (i >= w) continue;
+        C x[TC];
+        bool have_x = false;
+        if (fwd) {
+          if (k <= n - 3) st_cols<C, TC, PS>(zslot + ((long long)k * w + i) * NR + r0, acc[a]);
+          if (k == n - 1) {
 #pragma unroll
-        for (int qq = 0; qq < RQ; ++qq) {
-          const int r = tr + RL * qq;
-          C x;
-          bool have_x = false;
-          if (fwd) {
-            const C z = acc[s][qq];
-            if (k <= n - 3) zslot[((long long)k * w + i) * NR + r] = z;
-            if (k == n - 1) {
-              zkeep[s][qq] = zprev[s][qq];
-              x = z;
-              have_x = true;
-            }
-            zprev[s][qq] = z;
-          } else {
-            C z = czero<R>();
-            if (k >= k0) z = (k == n - 2) ? zkeep[s][qq] : slot[(size_t)(s * RQ + qq) * NT + tid];
-            x = z;
-            cfms(x, c_k, acc[s][qq]);
+            for (int c = 0; c < TC; ++c) { zkeep[a][c] = carry[a][c]; x[c] = acc[a][c]; }
             have_x = true;
           }
-          if (have_x) {
-            xprev[s][qq] = x;
-            if (r < nr) {
-              const long long gi = ((long long)(lo - 1 + i) * n + k) * ldv + rhs0 + r;
-              if (mode == MODE_EMBED) {
-                if (i >= xoff && i < xoff + xw) reinterpret_cast<C*>(P.outM)[gi] = x;
-                if (i == xoff + xw - 1) reinterpret_cast<C*>(P.accR)[((long long)p * n + k) * ldv + rhs0 + r] = x;
-                if (i == xoff) reinterpret_cast<C*>(P.accL)[((long long)p * n + k) * ldv + rhs0 + r] = x;
-              } else if (mode == MODE_FILL_R) {
-                if (i >= xoff && i < xoff + xw) reinterpret_cast<C*>(P.outR)[gi] = x;
-              } else if (mode == MODE_FILL_L) {
-                if (i >= xoff && i < xoff + xw) reinterpret_cast<C*>(P.outL)[gi] = x;
-              } else if (mode == MODE_TMAP_R) {
-                if (i == xoff + xw - 1) reinterpret_cast<C*>(P.tmap)[S.toff + (long long)k * n + rhs0 + r] = x;
-              } else if (mode == MODE_TMAP_L) {
-                if (i == xoff) reinterpret_cast<C*>(P.tmap)[S.toff + (long long)k * n + rhs0 + r] = x;
-              } else {
-                reinterpret_cast<double2*>(P.outSub)[((long long)i * n + k) * ldv + rhs0 + r] =
-                    make_double2((double)x.x, (double)x.y);
-              }
-            }
+#pragma unroll
+          for (int c = 0; c < TC; ++c) carry[a][c] = acc[a][c];
+        } else {
+#pragma unroll
+          for (int c = 0; c < TC; ++c) {
+            C z = czero<R>();
+            if (k >= k0) z = (k == n - 2) ? zkeep[a][c] : slot[(size_t)(a * TC + c) * NT + tid];
+            x[c] = z;
+            cfms(x[c], c_k, acc[a][c]);
+          }
+          have_x = true;
+        }
+        if (!have_x) continue;
+#pragma unroll
+        for (int c = 0; c < TC; ++c) {
+          carry[a][c] = x[c];
+          const int r = rhs_of(c);
+          if (r >= nr) continue;
+          const long long gi = ((long long)(lo - 1 + i) * n + k) * ldv + rhs0 + r;
+          if (mode == MODE_EMBED) {
+            if (i >= xoff && i < xoff + xw) reinterpret_cast<C*>(P.outM)[gi] = x[c];
+            if (i == xoff + xw - 1) reinterpret_cast<C*>(P.accR)[((long long)p * n + k) * lda + rhs0 + r] = x[c];
+            if (i == xoff) reinterpret_cast<C*>(P.accL)[((long long)p * n + k) * lda + rhs0 + r] = x[c];
+          } else if (mode == MODE_FILL_R) {
+            if (i >= xoff && i < xoff + xw) reinterpret_cast<C*>(P.outR)[gi] = x[c];
+          } else if (mode == MODE_FILL_L) {
+            if (i >= xoff && i < xoff + xw) reinterpret_cast<C*>(P.outL)[gi] = x[c];
+          } else if (mode == MODE_TMAP_R) {
+            if (i == xoff + xw - 1) reinterpret_cast<C*>(P.tmap)[S.toff + (long long)k * ldT + rhs0 + r] = x[c];
+          } else if (mode == MODE_TMAP_L) {
+            if (i == xoff) reinterpret_cast<C*>(P.tmap)[S.toff + (long long)k * ldT + rhs0 + r] = x[c];
+          } else {
+            reinterpret_cast<double2*>(P.outSub)[((long long)i * n + k) * ldv + rhs0 + r] =
+                make_double2((double)x[c].x, (double)x[c].y);
           }
         }
       }
@@ -302,34 +353,39 @@ __global__ void __launch_bounds__(NT) btsolve_kernel(SolveParams P, Geometry G) 
     for (int s = 0; s < kStages; ++s) mbar_inval(&bar[s]);
 }
 
-template <typename R, int NT, int RL, int RQ, int RS>
+template <typename R, int TC, int LC, int NCW>
 cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
+  using T = Tiling<R, TC, LC, NCW>;
+  const int nrw = (wcap + T::WR - 1) / T::WR;
+  const int nt = 32 * nrw * NCW;
+  if (nt > 512) return cudaErrorInvalidValue;
   Geometry G;
   G.wcap = wcap;
-  int wpc = (sizeof(R) == 4) ? ((wcap + 1) & ~1) : wcap;
-  G.wstage = wcap * wpc;
-  const size_t smem = Layout<R, NT, RL, RQ, RS>::total(G);
-  auto kern = btsolve_kernel<R, NT, RL, RQ, RS>;
+  const int wpc = (sizeof(R) == 4) ? ((wcap + 1) & ~1) : wcap;
+  // slack: the 2-row tiles of the last row block may read up to WR rows past
+  // column w-1 of a stage (their results are discarded)
+  G.wstage = wcap * wpc + T::WR * nrw + 2;
+  if (sizeof(R) == 4) G.wstage = (G.wstage + 1) & ~1;
+  const size_t smem = T::total(G, nt);
+  auto kern = btsolve_kernel<R, TC, LC, NCW>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = P.njobs < H.zslots ? P.njobs : H.zslots;
   if (grid <= 0) return cudaSuccess;
-  kern<<<grid, NT, smem, s>>>(P, G);
+  kern<<<grid, nt, smem, s>>>(P, G);
   H.launches += 1;
   return cudaGetLastError();
 }
 
 }  // namespace
 
-// Right-hand sides one CTA handles for a launch whose jobs have at most
-// `nrhs` right-hand sides and width <= wmax.  Returns 0 if no instance fits.
+// Right-hand sides one CTA handles, for jobs with at most `nrhs` right-hand
+// sides (`tmap`: the transfer-map construction, whose n columns are the
+// right-hand sides).  Returns 0 if no instance fits (w > 64).
 int btsolve_rhs_capacity(int nrhs, int wmax, int prec, bool tmap) {
   if (wmax > 64) return 0;
-  if (tmap && prec == ASP_PREC_C64 && wmax <= 32) return 64;
-  if (nrhs >= 32 || tmap) {
-    if (prec == ASP_PREC_C64 && wmax <= 64) return 32;
-    if (prec == ASP_PREC_C128 && wmax <= 64) return 16;
-  }
+  if (tmap) return prec == ASP_PREC_C64 ? 64 : 16;
+  if (nrhs >= 32) return prec == ASP_PREC_C64 ? 32 : 16;
   if (nrhs >= 16) return 16;
   if (nrhs >= 8) return 8;
   if (nrhs >= 4) return 4;
@@ -340,21 +396,21 @@ int btsolve_rhs_capacity(int nrhs, int wmax, int prec, bool tmap) {
 cudaError_t launch_btsolve(Handle& H, const SolveParams& P, int cap, int wmax, cudaStream_t s) {
   if (H.prec == ASP_PREC_C64) {
     switch (cap) {
-      case 64: return run<float, 128, 32, 2, 8>(H, P, wmax, s);
-      case 32: return run<float, 128, 32, 1, 16>(H, P, wmax, s);
-      case 16: return run<float, 128, 16, 1, 8>(H, P, wmax, s);
-      case 8: return run<float, 128, 8, 1, 4>(H, P, wmax, s);
-      case 4: return run<float, 128, 4, 1, 2>(H, P, wmax, s);
-      case 2: return run<float, 128, 2, 1, 1>(H, P, wmax, s);
-      case 1: return run<float, 64, 1, 1, 1>(H, P, wmax, s);
+      case 64: return run<float, 4, 8, 2>(H, P, wmax, s);
+      case 32: return run<float, 4, 8, 1>(H, P, wmax, s);
+      case 16: return run<float, 2, 8, 1>(H, P, wmax, s);
+      case 8: return run<float, 2, 4, 1>(H, P, wmax, s);
+      case 4: return run<float, 2, 2, 1>(H, P, wmax, s);
+      case 2: return run<float, 2, 1, 1>(H, P, wmax, s);
+      case 1: return run<float, 1, 1, 1>(H, P, wmax, s);
     }
   } else {
     switch (cap) {
-      case 16: return run<double, 128, 16, 1, 8>(H, P, wmax, s);
-      case 8: return run<double, 128, 8, 1, 4>(H, P, wmax, s);
-      case 4: return run<double, 128, 4, 1, 2>(H, P, wmax, s);
-      case 2: return run<double, 128, 2, 1, 1>(H, P, wmax, s);
-      case 1: return run<double, 64, 1, 1, 1>(H, P, wmax, s);
+      case 16: return run<double, 2, 8, 1>(H, P, wmax, s);
+      case 8: return run<double, 2, 4, 1>(H, P, wmax, s);
+      case 4: return run<double, 2, 2, 1>(H, P, wmax, s);
+      case 2: return run<double, 2, 1, 1>(H, P, wmax, s);
+      case 1: return run<double, 1, 1, 1>(H, P, wmax, s);
     }
   }
   return cudaErrorInvalidValue;

@@ -55,22 +55,42 @@ struct SweepCoef {
   double2 up, dn, dg;
 };
 
+template <typename R> struct CplxOf;
+template <> struct CplxOf<float> { using T = float2; };
+template <> struct CplxOf<double> { using T = double2; };
+
+// Coefficients of the layer operators in the factor precision R: the x1
+// stencil weights a_k, c_k, d_k per x1 node, omega^2/c^2 (natural order) and
+// the sweep-axis weights of every subproblem column (concatenated, SubDesc::prof).
+template <typename R> struct FactorCoefs {
+  using C = typename CplxOf<R>::T;
+  const C* ca = nullptr;
+  const C* cc = nullptr;
+  const C* cd = nullptr;
+  const R* k2 = nullptr;
+  const C* up = nullptr;
+  const C* dn = nullptr;
+  const C* dg = nullptr;
+};
+
 struct SolveParams {
   const SubDesc* subs;
   const Job* jobs;
   int njobs;
   int n;            // blocks per subproblem (= x1 nodes)
   int ldv;          // right-hand-side stride of the vectors (= nrhs of the call)
+  int ldacc;        // right-hand-side stride of the trace buffers (nrhs rounded up to even)
+  int ldT;          // row stride of the transfer maps (n rounded up to even)
   double inv_h2;
   const void* W;    // factor blocks W_k = S_k^-1
-  const double2* ca;  // a_k: coupling of block k to block k-1 (x1 stencil)
-  const double2* cc;  // c_k: coupling of block k to block k+1
+  const void* ca;   // a_k: coupling of block k to block k-1 (x1 stencil), factor precision
+  const void* cc;   // c_k: coupling of block k to block k+1, factor precision
   const void* in;   // EMBED / SUB input (factor precision, RHS-interleaved)
   void* outM;       // EMBED output restricted to X_q (factor precision)
   void* outR;       // FILL_R output
   void* outL;       // FILL_L output
-  void* accR;       // [m+1][n][ldv] right traces / accumulated right-going traces
-  void* accL;       // [m+1][n][ldv] left traces
+  void* accR;       // [m+1][n][ldacc] right traces / accumulated right-going traces
+  void* accL;       // [m+1][n][ldacc] left traces
   void* tmap;       // transfer maps base
   void* outSub;     // MODE_SUB output (complex128, [w][n][ldv])
   void* zscr;       // forward-pass scratch, one slot per resident CTA
@@ -79,11 +99,11 @@ struct SolveParams {
 };
 
 struct ChainParams {
-  int n, m, ldv, nrhs;
+  int n, m, ldacc, ldT, nrhs;
   const void* tmap;        // maps
   const long long* toffR;  // [m+1] element offset of T_p^R (p = 2..m-1)
   const long long* toffL;  // [m+1] element offset of T_p^L
-  void* accR;              // [m+1][n][ldv]
+  void* accR;              // [m+1][n][ldacc]
   void* accL;
   unsigned int* bar;       // two grid-barrier counters (R, L), zeroed before launch
   int* err;
@@ -127,6 +147,11 @@ struct Handle {
   double2* cc = nullptr;  // c_k = s_k s_{k+1/2} / h^2
   double2* cd = nullptr;  // d_k = -s_k (s_{k+1/2} + s_{k-1/2}) / h^2
 
+  // the same coefficients in the factor precision (owned device buffers)
+  FactorCoefs<float> fc32;
+  FactorCoefs<double> fc64;
+  std::vector<void*> coef_bufs;
+
   // subproblems
   std::vector<SubDesc> subs;
   SubDesc* d_subs = nullptr;
@@ -140,6 +165,7 @@ struct Handle {
   size_t W_elems = 0;
   void* tmap = nullptr;
   size_t tmap_elems = 0;
+  int ldT = 0;  // row stride of a transfer map (n rounded up to even)
   std::vector<long long> toffR, toffL;
   long long* d_toffR = nullptr;
   long long* d_toffL = nullptr;

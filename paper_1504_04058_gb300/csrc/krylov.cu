@@ -30,40 +30,49 @@ __device__ __forceinline__ double2 dmul(double2 a, double2 b) { return cmul(a, b
 // ------------------------------------------------------------------ matvec
 // (Au)_{i1,i2} = a_{i1} u_{i1-1} + c_{i1} u_{i1+1} + a_{i2} u_{i2-1} + c_{i2} u_{i2+1}
 //                + (d_{i1} + d_{i2} + omega^2/c^2) u,  zero outside the grid.
+// Grid: blockIdx.y = x2 row, blockIdx.x = chunk of the row's n*nrhs elements;
+// NRT is the number of right-hand sides when it is a compile-time constant
+// (0: runtime `nrhs`), so that the point index needs no runtime division.
+template <int NRT>
 __global__ void matvec_kernel(const double* __restrict__ k2, const double2* __restrict__ ca,
                               const double2* __restrict__ cc, const double2* __restrict__ cd, int n,
-                              int nrhs, const double2* __restrict__ x, double2* __restrict__ y) {
-  const long long total = (long long)n * n * nrhs;
-  const long long rowst = (long long)n * nrhs;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long pt = e / nrhs;
-    const int i1 = (int)(pt % n), i2 = (int)(pt / n);
-    const double2 u = x[e];
-    const double2 d1 = cd[i1], d2 = cd[i2];
-    double2 diag = make_double2(d1.x + d2.x + k2[pt], d1.y + d2.y);
-    double2 acc = dmul(diag, u);
-    if (i1 > 0) cfma(acc, ca[i1], x[e - nrhs]);
-    if (i1 < n - 1) cfma(acc, cc[i1], x[e + nrhs]);
-    if (i2 > 0) cfma(acc, ca[i2], x[e - rowst]);
-    if (i2 < n - 1) cfma(acc, cc[i2], x[e + rowst]);
-    y[e] = acc;
-  }
+                              int nrhs_rt, const double2* __restrict__ x, double2* __restrict__ y) {
+  const int nr = NRT > 0 ? NRT : nrhs_rt;
+  const int er = blockIdx.x * blockDim.x + threadIdx.x;  // element within the row
+  if (er >= n * nr) return;
+  const int i2 = blockIdx.y;
+  const int i1 = er / nr;
+  const long long rowst = (long long)n * nr;
+  const long long e = (long long)i2 * rowst + er;
+  const double2 u = x[e];
+  const double2 d1 = cd[i1], d2 = cd[i2];
+  const double2 diag = make_double2(d1.x + d2.x + k2[(long long)i2 * n + i1], d1.y + d2.y);
+  double2 acc = dmul(diag, u);
+  if (i1 > 0) cfma(acc, ca[i1], x[e - nr]);
+  if (i1 < n - 1) cfma(acc, cc[i1], x[e + nr]);
+  if (i2 > 0) cfma(acc, ca[i2], x[e - rowst]);
+  if (i2 < n - 1) cfma(acc, cc[i2], x[e + rowst]);
+  y[e] = acc;
 }
 
 struct VecList {
   const double2* v[kDotChunk];
 };
 
-// partial[b][j][r] = sum over this block's elements of conj(v_j) * w
-__global__ void multidot_kernel(VecList V, int J, const double2* __restrict__ w, long long count, int nrhs,
-                                double2* __restrict__ partial) {
+// Reductions over a vector of `count` = points*nrhs elements use blocks of
+// bt = nrhs*floor(256/nrhs) threads and a grid stride that is a multiple of
+// nrhs, so each thread always sees the same right-hand side r = tid % nrhs.
+//
+// partial[b][j][r] = this block's sum of conj(v_j) * w for j < J, and, when
+// want_norm, partial[b][kDotChunk][r] = its sum of |w|^2.
+__global__ void gs_dot_kernel(VecList V, int J, int want_norm, const double2* __restrict__ w, long long count,
+                              int nrhs, double2* __restrict__ partial) {
   __shared__ double2 red[kVecThreads];
-  const int bt = blockDim.x;  // a multiple of nrhs
+  const int bt = blockDim.x;
   const int t = threadIdx.x;
-  double2 acc[kDotChunk];
+  double2 acc[kDotChunk + 1];
 #pragma unroll
-  for (int j = 0; j < kDotChunk; ++j) acc[j] = make_double2(0, 0);
+  for (int j = 0; j <= kDotChunk; ++j) acc[j] = make_double2(0, 0);
   for (long long e = (long long)blockIdx.x * bt + t; e < count; e += (long long)gridDim.x * bt) {
     const double2 we = w[e];
 #pragma unroll
@@ -73,57 +82,85 @@ __global__ void multidot_kernel(VecList V, int J, const double2* __restrict__ w,
         acc[j].x = fma(v.x, we.x, fma(v.y, we.y, acc[j].x));
         acc[j].y = fma(v.x, we.y, fma(-v.y, we.x, acc[j].y));
       }
+    if (want_norm) acc[kDotChunk].x = fma(we.x, we.x, fma(we.y, we.y, acc[kDotChunk].x));
   }
-  for (int j = 0; j < J; ++j) {
-    red[t] = acc[j];
-    __syncthreads();
-    if (t < nrhs) {
-      double2 s = make_double2(0, 0);
-      for (int q = t; q < bt; q += nrhs) { s.x += red[q].x; s.y += red[q].y; }
-      partial[((long long)blockIdx.x * kDotChunk + j) * nrhs + t] = s;
+#pragma unroll
+  for (int j = 0; j <= kDotChunk; ++j) {
+    if (j < J || (j == kDotChunk && want_norm)) {
+      red[t] = acc[j];
+      __syncthreads();
+      if (t < nrhs) {
+        double2 s = make_double2(0, 0);
+        for (int q = t; q < bt; q += nrhs) { s.x += red[q].x; s.y += red[q].y; }
+        partial[((long long)blockIdx.x * (kDotChunk + 1) + j) * nrhs + t] = s;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
-// out[(j0 + j)][r] = sum_b partial[b][j][r]   (fixed block order)
+// out[j0 + j][r] = sum_b partial[b][j][r] for j < J, and nrm[r] = sum_b
+// partial[b][kDotChunk][r] when nrm != nullptr (fixed block order).
 __global__ void dot_finish_kernel(const double2* __restrict__ partial, int nblocks, int J, int nrhs, int j0,
-                                  double2* __restrict__ out) {
+                                  double2* __restrict__ out, double2* __restrict__ nrm) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= J * nrhs) return;
-  const int j = idx / nrhs, r = idx % nrhs;
+  const int slots = J + (nrm ? 1 : 0);
+  if (idx >= slots * nrhs) return;
+  const int jj = idx / nrhs, r = idx % nrhs;
+  const int j = jj < J ? jj : kDotChunk;
   double2 s = make_double2(0, 0);
   for (int b = 0; b < nblocks; ++b) {
-    const double2 v = partial[((long long)b * kDotChunk + j) * nrhs + r];
+    const double2 v = partial[((long long)b * (kDotChunk + 1) + j) * nrhs + r];
     s.x += v.x; s.y += v.y;
   }
-  out[(long long)(j0 + j) * nrhs + r] = s;
+  if (jj < J) out[(long long)(j0 + jj) * nrhs + r] = s;
+  else nrm[r] = s;
 }
 
-// w[e] += sgn * sum_j coef[(j0+j)][r] * v_j[e]
-__global__ void multiaxpy_kernel(VecList V, int J, const double2* __restrict__ coef, int j0, double sgn,
-                                 double2* __restrict__ w, long long count, int nrhs) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(e % nrhs);
+// w[e] += sgn * sum_j coef[(j0+j)][r] * v_j[e]; with want_norm also the block
+// sums of |w_new|^2 in partial[b][kDotChunk][r].
+__global__ void gs_axpy_kernel(VecList V, int J, const double2* __restrict__ coef, int j0, double sgn,
+                               double2* __restrict__ w, long long count, int nrhs, int want_norm,
+                               double2* __restrict__ partial) {
+  __shared__ double2 red[kVecThreads];
+  const int bt = blockDim.x;
+  const int t = threadIdx.x;
+  const int r = t % nrhs;
+  double2 c[kDotChunk];
+#pragma unroll
+  for (int j = 0; j < kDotChunk; ++j) {
+    c[j] = make_double2(0, 0);
+    if (j < J) {
+      const double2 cj = coef[(long long)(j0 + j) * nrhs + r];
+      c[j] = make_double2(sgn * cj.x, sgn * cj.y);
+    }
+  }
+  double nacc = 0.0;
+  for (long long e = (long long)blockIdx.x * bt + t; e < count; e += (long long)gridDim.x * bt) {
     double2 acc = w[e];
 #pragma unroll
     for (int j = 0; j < kDotChunk; ++j)
-      if (j < J) {
-        double2 c = coef[(long long)(j0 + j) * nrhs + r];
-        c.x *= sgn; c.y *= sgn;
-        cfma(acc, c, V.v[j][e]);
-      }
+      if (j < J) cfma(acc, c[j], V.v[j][e]);
     w[e] = acc;
+    if (want_norm) nacc = fma(acc.x, acc.x, fma(acc.y, acc.y, nacc));
+  }
+  if (want_norm) {
+    red[t] = make_double2(nacc, 0.0);
+    __syncthreads();
+    if (t < nrhs) {
+      double2 s = make_double2(0, 0);
+      for (int q = t; q < bt; q += nrhs) s.x += red[q].x;
+      partial[((long long)blockIdx.x * (kDotChunk + 1) + kDotChunk) * nrhs + t] = s;
+    }
   }
 }
 
-// dst[e] = src[e] * s[r]  (s real)
+// dst[e] = src[e] * s[r]  (s real); same thread layout as the reductions
 __global__ void scale_kernel(const double2* __restrict__ src, const double* __restrict__ sc,
                              double2* __restrict__ dst, long long count, int nrhs) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
-       e += (long long)gridDim.x * blockDim.x) {
-    const double s = sc[e % nrhs];
+  const int bt = blockDim.x;
+  const double s = sc[threadIdx.x % nrhs];
+  for (long long e = (long long)blockIdx.x * bt + threadIdx.x; e < count; e += (long long)gridDim.x * bt) {
     const double2 v = src[e];
     dst[e] = make_double2(v.x * s, v.y * s);
   }
@@ -143,7 +180,8 @@ __global__ void sub_kernel(const double2* __restrict__ a, const double2* __restr
 struct KState {
   double2* h1;    // [restart+1][nrhs]  first CGS pass
   double2* h2;    // [restart+1][nrhs]  second CGS pass
-  double2* hn2;   // [1][nrhs]  ||w||^2 (re)
+  double2* hn2;   // [1][nrhs]  ||w||^2 after orthogonalization (re)
+  double2* nrm0;  // [1][nrhs]  ||w||^2 before orthogonalization (re)
   double2* Rm;    // [restart][restart+1][nrhs]  rotated Hessenberg columns
   double* cs;     // [restart][nrhs]
   double2* sn;    // [restart][nrhs]
@@ -156,6 +194,7 @@ struct KState {
   int* kcur;      // [nrhs] columns in the current cycle
   int* its;       // [nrhs] iterations until done
   int* active;    // [1] number of right-hand sides still iterating
+  int* need;      // [1] number of right-hand sides that need a second Gram-Schmidt pass
 };
 
 // Start of a restart cycle: beta = ||r||, g = [beta, 0..], inv = 1/beta.
@@ -246,6 +285,18 @@ __global__ void arnoldi_update_kernel(KState K, int nrhs, int j, int restart, do
   K.inv[r] = (stop || hn == 0.0) ? 0.0 : 1.0 / hn;
 }
 
+// Second Gram-Schmidt pass needed where the first one removed more than half
+// of ||w||^2 (||w'|| < ||w|| / sqrt(2): the classical criterion of Daniel,
+// Gragg, Kaufman and Stewart for cancellation).
+__global__ void reorth_check_kernel(KState K, int nrhs) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int c = 0;
+    for (int r = 0; r < nrhs; ++r)
+      if (!K.done[r] && K.hn2[r].x < 0.5 * K.nrm0[r].x) ++c;
+    *K.need = c;
+  }
+}
+
 __global__ void count_active_kernel(KState K, int nrhs) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     int a = 0;
@@ -285,9 +336,17 @@ int grid_for(long long count, int threads, int sms) {
 }  // namespace
 
 cudaError_t launch_matvec(const Handle& H, const double2* x, double2* y, int nrhs, cudaStream_t s) {
-  const long long total = H.N * nrhs;
-  matvec_kernel<<<grid_for(total, kVecThreads, H.num_sms), kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n,
-                                                                                nrhs, x, y);
+  const long long per_row = (long long)H.n * nrhs;
+  dim3 grid((unsigned)((per_row + kVecThreads - 1) / kVecThreads), (unsigned)H.n);
+  switch (nrhs) {
+    case 1: matvec_kernel<1><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
+    case 2: matvec_kernel<2><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
+    case 4: matvec_kernel<4><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
+    case 8: matvec_kernel<8><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
+    case 16: matvec_kernel<16><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
+    case 32: matvec_kernel<32><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
+    default: matvec_kernel<0><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
+  }
   const_cast<Handle&>(H).launches += 1;
   return cudaGetLastError();
 }
@@ -300,40 +359,52 @@ struct Krylov {
   long long count;
   cudaStream_t s;
   KState K;
-  int dot_blocks, dot_threads;
+  int red_blocks, red_threads;
   double2* partial;
 
   double2* Vv(int i) const { return H.V + (long long)i * count; }
   double2* Zv(int i) const { return H.Z + (long long)i * count; }
 
-  // out[j0 + j][r] = conj(V_j)^T w for j < J (J arbitrary, processed in chunks)
-  cudaError_t dots(const double2* const* vs, int J, const double2* w, double2* out) {
-    for (int j0 = 0; j0 < J; j0 += kDotChunk) {
+  // out[j][r] = conj(V_j)^T w for j < J (chunks of kDotChunk); nrm[r] = ||w||^2
+  // when nrm != nullptr (computed with the first chunk, or alone when J == 0).
+  cudaError_t dots(const double2* const* vs, int J, const double2* w, double2* out, double2* nrm) {
+    for (int j0 = 0; j0 < J || (J == 0 && j0 == 0); j0 += kDotChunk) {
       VecList L{};
       const int Jc = std::min(kDotChunk, J - j0);
       for (int j = 0; j < Jc; ++j) L.v[j] = vs[j0 + j];
-      for (int j = Jc; j < kDotChunk; ++j) L.v[j] = vs[j0];
-      multidot_kernel<<<dot_blocks, dot_threads, 0, s>>>(L, Jc, w, count, nrhs, partial);
-      dot_finish_kernel<<<(Jc * nrhs + 127) / 128, 128, 0, s>>>(partial, dot_blocks, Jc, nrhs, j0, out);
+      for (int j = std::max(Jc, 0); j < kDotChunk; ++j) L.v[j] = w;
+      double2* nr = (j0 == 0) ? nrm : nullptr;
+      gs_dot_kernel<<<red_blocks, red_threads, 0, s>>>(L, std::max(Jc, 0), nr ? 1 : 0, w, count, nrhs, partial);
+      const int slots = std::max(Jc, 0) + (nr ? 1 : 0);
+      dot_finish_kernel<<<(slots * nrhs + 127) / 128, 128, 0, s>>>(partial, red_blocks, std::max(Jc, 0), nrhs, j0,
+                                                                    out, nr);
       H.launches += 2;
+      if (J == 0) break;
     }
     return cudaGetLastError();
   }
-  cudaError_t axpys(const double2* const* vs, int J, const double2* coef, double sgn, double2* w) {
+  // w += sgn * sum_j coef[j] V_j; nrm[r] = ||w_new||^2 when nrm != nullptr
+  cudaError_t axpys(const double2* const* vs, int J, const double2* coef, double sgn, double2* w, double2* nrm) {
     for (int j0 = 0; j0 < J; j0 += kDotChunk) {
       VecList L{};
       const int Jc = std::min(kDotChunk, J - j0);
       for (int j = 0; j < Jc; ++j) L.v[j] = vs[j0 + j];
       for (int j = Jc; j < kDotChunk; ++j) L.v[j] = vs[j0];
-      multiaxpy_kernel<<<grid_for(count, kVecThreads, H.num_sms), kVecThreads, 0, s>>>(L, Jc, coef, j0, sgn, w,
-                                                                                         count, nrhs);
+      const bool last = j0 + kDotChunk >= J;
+      const bool want = last && nrm;
+      gs_axpy_kernel<<<red_blocks, red_threads, 0, s>>>(L, Jc, coef, j0, sgn, w, count, nrhs, want ? 1 : 0, partial);
       H.launches += 1;
+      if (want) {
+        dot_finish_kernel<<<(nrhs + 127) / 128, 128, 0, s>>>(partial, red_blocks, 0, nrhs, 0, nullptr, nrm);
+        H.launches += 1;
+      }
     }
     return cudaGetLastError();
   }
-  cudaError_t norm2(const double2* w, double2* out) {
-    const double2* v[1] = {w};
-    return dots(v, 1, w, out);
+  cudaError_t scale(const double2* src, const double* sc, double2* dst) {
+    scale_kernel<<<red_blocks, red_threads, 0, s>>>(src, sc, dst, count, nrhs);
+    H.launches += 1;
+    return cudaGetLastError();
   }
 };
 
@@ -350,6 +421,7 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
     G.K.h1 = take2((long long)(R + 1) * nrhs);
     G.K.h2 = take2((long long)(R + 1) * nrhs);
     G.K.hn2 = take2(nrhs);
+    G.K.nrm0 = take2(nrhs);
     G.K.Rm = take2((long long)R * (R + 1) * nrhs);
     G.K.sn = take2((long long)R * nrhs);
     G.K.g = take2((long long)(R + 1) * nrhs);
@@ -363,10 +435,11 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
     G.K.done = pi; pi += nrhs;
     G.K.kcur = pi; pi += nrhs;
     G.K.its = pi; pi += nrhs;
-    G.K.active = pi;
+    G.K.active = pi; pi += 1;
+    G.K.need = pi;
   }
-  G.dot_threads = nrhs * std::max(1, kVecThreads / nrhs);
-  G.dot_blocks = H.num_sms * 2;
+  G.red_threads = nrhs * std::max(1, kVecThreads / nrhs);
+  G.red_blocks = H.num_sms * 2;
   G.partial = reinterpret_cast<double2*>(H.red);
   const long long count = G.count;
   const int gv = grid_for(count, kVecThreads, H.num_sms);
@@ -383,6 +456,7 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
   bool first = true;
   std::vector<const double2*> vl(restart + 1);
   int rc = ASP_OK;
+  int active = nrhs;
   while (true) {
     // r = f - A u (u = 0 on the first cycle, so r = f)
     const double2* rvec = f;
@@ -392,12 +466,11 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
       H.launches += 1;
       rvec = H.wv;
     }
-    CK(G.norm2(rvec, G.K.hn2));
+    CK(G.dots(nullptr, 0, rvec, nullptr, G.K.hn2));
     cycle_start_kernel<<<gr, 128, 0, s>>>(G.K, nrhs, first ? 1 : 0, tol);
-    scale_kernel<<<gv, kVecThreads, 0, s>>>(rvec, G.K.inv, G.Vv(0), count, nrhs);
-    H.launches += 2;
+    H.launches += 1;
+    CK(G.scale(rvec, G.K.inv, G.Vv(0)));
     first = false;
-    int active = nrhs;
     for (int j = 0; j < restart && its < maxit; ++j) {
       rc = apply_precond(H, G.Vv(j), G.Zv(j), nrhs, s);
       if (rc != ASP_OK) return rc;
@@ -407,17 +480,26 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
       phase_end(H, s);
       phase_begin(H, PH_KRYLOV, s);
       for (int i = 0; i <= j; ++i) vl[i] = G.Vv(i);
-      CK(G.dots(vl.data(), j + 1, w, G.K.h1));
-      CK(G.axpys(vl.data(), j + 1, G.K.h1, -1.0, w));
-      CK(G.dots(vl.data(), j + 1, w, G.K.h2));
-      CK(G.axpys(vl.data(), j + 1, G.K.h2, -1.0, w));
-      CK(G.norm2(w, G.K.hn2));
+      // classical Gram-Schmidt, a second pass only where cancellation demands it
+      CK(G.dots(vl.data(), j + 1, w, G.K.h1, G.K.nrm0));
+      CK(G.axpys(vl.data(), j + 1, G.K.h1, -1.0, w, G.K.hn2));
+      reorth_check_kernel<<<1, 32, 0, s>>>(G.K, nrhs);
+      H.launches += 1;
+      CK(cudaMemcpyAsync(H.h_flags + 1, G.K.need, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (H.h_flags[1] > 0) {
+        CK(G.dots(vl.data(), j + 1, w, G.K.h2, nullptr));
+        CK(G.axpys(vl.data(), j + 1, G.K.h2, -1.0, w, G.K.hn2));
+      } else {
+        CK(cudaMemsetAsync(G.K.h2, 0, sizeof(double2) * (j + 1) * nrhs, s));
+      }
       ++its;
       arnoldi_update_kernel<<<gr, 128, 0, s>>>(G.K, nrhs, j, H.prm.restart, tol, its);
-      scale_kernel<<<gv, kVecThreads, 0, s>>>(w, G.K.inv, w, count, nrhs);
+      H.launches += 1;
+      CK(G.scale(w, G.K.inv, w));
       count_active_kernel<<<1, 32, 0, s>>>(G.K, nrhs);
+      H.launches += 1;
       phase_end(H, s);
-      H.launches += 3;
       CK(cudaMemcpyAsync(H.h_flags, G.K.active, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       active = H.h_flags[0];
@@ -428,14 +510,14 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
     H.launches += 1;
     std::vector<const double2*> zl(restart);
     for (int i = 0; i < restart; ++i) zl[i] = G.Zv(i);
-    CK(G.axpys(zl.data(), restart, G.K.y, 1.0, u));
+    CK(G.axpys(zl.data(), restart, G.K.y, 1.0, u, nullptr));
     if (active == 0 || its >= maxit) break;
   }
   // true residual ||f - A u|| / ||f||
   CK(launch_matvec(H, u, H.wv, nrhs, s));
   sub_kernel<<<gv, kVecThreads, 0, s>>>(f, H.wv, H.wv, count);
   H.launches += 1;
-  CK(G.norm2(H.wv, G.K.hn2));
+  CK(G.dots(nullptr, 0, H.wv, nullptr, G.K.hn2));
   std::vector<double2> hn2(nrhs);
   std::vector<double> fn(nrhs), est(nrhs);
   std::vector<int> done(nrhs), itv(nrhs);
@@ -464,9 +546,9 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
 
 size_t krylov_state_bytes(int restart, int nrhs, size_t* n2, size_t* nd, size_t* ni) {
   const long long R = restart;
-  *n2 = (size_t)((R + 1) * nrhs * 2 + nrhs + R * (R + 1) * nrhs + R * nrhs + (R + 1) * nrhs + R * nrhs);
+  *n2 = (size_t)((R + 1) * nrhs * 2 + 2 * nrhs + R * (R + 1) * nrhs + R * nrhs + (R + 1) * nrhs + R * nrhs);
   *nd = (size_t)(R * nrhs + 3 * nrhs);
-  *ni = (size_t)(3 * nrhs + 1);
+  *ni = (size_t)(3 * nrhs + 2);
   return *n2 * sizeof(double2) + *nd * sizeof(double) + *ni * sizeof(int);
 }
 
