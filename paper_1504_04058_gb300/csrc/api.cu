@@ -171,7 +171,7 @@ Sizes sizes_for(const asp_params* p, int num_sms) {
   for (int q = 1; q <= P.m - 1; ++q) addsub(P.m_lo[q], P.beta[q], true);
   const int ldT = (n + 1) & ~1;
   Z.tmap_elems = P.m >= 3 ? (size_t)2 * (P.m - 2) * n * ldT : 0;
-  Z.zslots = std::max(1, 2 * num_sms);
+  Z.zslots = std::max(1, 4 * num_sms);
   Z.zslot = (size_t)n * Z.wmax * fmax_rhs_cap(p->factor_prec);
   const long long R = p->restart;
   const long long mr = p->max_rhs;

@@ -103,8 +103,8 @@ template <typename C, int TC, int PS> __device__ __forceinline__ void st_cols(C*
   }
 }
 
-template <typename R, int TC, int LC, int NCW>
-__global__ void __launch_bounds__(512) btsolve_kernel(SolveParams P, Geometry G) {
+template <typename R, int TC, int LC, int NCW, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geometry G) {
   using C = Cx<R>;
   using T = Tiling<R, TC, LC, NCW>;
   constexpr int TR = T::TR, WR = T::WR, WC = T::WC, NR = T::NR, E = T::E;
@@ -353,12 +353,14 @@ __global__ void __launch_bounds__(512) btsolve_kernel(SolveParams P, Geometry G)
     for (int s = 0; s < kStages; ++s) mbar_inval(&bar[s]);
 }
 
-template <typename R, int TC, int LC, int NCW>
+// MAXT / MINB: largest CTA the instance is compiled for and the number of
+// such CTAs per SM its register budget is sized for.
+template <typename R, int TC, int LC, int NCW, int MAXT = 512, int MINB = 1>
 cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
   using T = Tiling<R, TC, LC, NCW>;
   const int nrw = (wcap + T::WR - 1) / T::WR;
   const int nt = 32 * nrw * NCW;
-  if (nt > 512) return cudaErrorInvalidValue;
+  if (nt > MAXT) return cudaErrorInvalidValue;
   Geometry G;
   G.wcap = wcap;
   const int wpc = (sizeof(R) == 4) ? ((wcap + 1) & ~1) : wcap;
@@ -367,7 +369,7 @@ cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
   G.wstage = wcap * wpc + T::WR * nrw + 2;
   if (sizeof(R) == 4) G.wstage = (G.wstage + 1) & ~1;
   const size_t smem = T::total(G, nt);
-  auto kern = btsolve_kernel<R, TC, LC, NCW>;
+  auto kern = btsolve_kernel<R, TC, LC, NCW, MAXT, MINB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = P.njobs < H.zslots ? P.njobs : H.zslots;
@@ -396,8 +398,10 @@ int btsolve_rhs_capacity(int nrhs, int wmax, int prec, bool tmap) {
 cudaError_t launch_btsolve(Handle& H, const SolveParams& P, int cap, int wmax, cudaStream_t s) {
   if (H.prec == ASP_PREC_C64) {
     switch (cap) {
-      case 64: return run<float, 4, 8, 2>(H, P, wmax, s);
-      case 32: return run<float, 4, 8, 1>(H, P, wmax, s);
+      case 64:
+        if (wmax <= 24) return run<float, 4, 8, 2, 192, 3>(H, P, wmax, s);
+        return run<float, 4, 8, 2>(H, P, wmax, s);
+      case 32: return run<float, 2, 8, 2, 384, 2>(H, P, wmax, s);
       case 16: return run<float, 2, 8, 1>(H, P, wmax, s);
       case 8: return run<float, 2, 4, 1>(H, P, wmax, s);
       case 4: return run<float, 2, 2, 1>(H, P, wmax, s);

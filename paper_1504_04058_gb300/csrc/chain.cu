@@ -87,10 +87,13 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
       const int kn = min(KC, n - kc);
       C* dT = s_T + (size_t)b * kMaxRows * KC;
       C* dS = s_src + (size_t)b * KC * kRhs;
-      // T chunk, transposed so that a lane's 8 rows at one k are contiguous
-      for (int e = tid; e < rows * kn; e += kChainThreads) {
-        const int rr = e / kn, kk = e % kn;
-        cp_async<CB>(dT + kk * kMaxRows + rr, T + (long long)(row0 + rr) * ldT + kc + kk);
+      // T chunk, transposed so that a lane's 8 rows at one k are contiguous;
+      // consecutive threads take consecutive rows (contiguous shared stores)
+      {
+        const int rr = tid & (kMaxRows - 1);
+        if (rr < rows)
+          for (int kk = tid / kMaxRows; kk < kn; kk += kChainThreads / kMaxRows)
+            cp_async<CB>(dT + kk * kMaxRows + rr, T + (long long)(row0 + rr) * ldT + kc + kk);
       }
       if constexpr (CB == 16) {
         for (int e = tid; e < kn * nrhs; e += kChainThreads) {
