@@ -178,6 +178,30 @@ long long asp_take_launch_count(asp_handle* h);
 int asp_set_phase_timing(asp_handle* h, int enable);
 int asp_phase_times(asp_handle* h, double* ms, long long* launches, int nphases);
 
+/* ---- allocation-free residual check ------------------------------------
+ * asp_residual_norms_noalloc: rel_res[r] = ||f_r - A u_r|| / ||f_r|| (0 when
+ * f_r = 0) for r < nrhs, with A the operator of asp_matvec for the problem in
+ * `p` (dim, n, omega, pml, C are read; the other fields are ignored).  The
+ * paper has no counterpart of this call: it exists for callers that cannot
+ * allocate device memory -- code inside a CUDA-graph capture, processes whose
+ * device memory belongs to another allocator, serving loops that must not
+ * allocate -- and therefore takes no handle.
+ *   c        DEVICE, n*n doubles, the velocity in the natural ordering
+ *   f, u     DEVICE complex128 vectors, RHS-interleaved as everywhere
+ *   rel_res  DEVICE, nrhs doubles, written
+ * It allocates nothing: its temporaries live in one fixed device array inside
+ * the library (about 0.7 MB, held on every GPU that loads the library until the
+ * process exits), sized for n <= ASP_NOALLOC_MAX_N and nrhs <=
+ * ASP_NOALLOC_MAX_RHS; larger requests return ASP_ERR_INVALID.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress), so
+ * make the first call on each device before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race and may return wrong
+ * values, so order them (one stream, or events).  Enqueued on `stream`. */
+#define ASP_NOALLOC_MAX_N 4096
+#define ASP_NOALLOC_MAX_RHS 64
+int asp_residual_norms_noalloc(const asp_params* p, const double* c, const void* f, const void* u, int nrhs,
+                               double* rel_res, void* stream);
+
 /* Free everything the handle owns.  NULL is accepted; calling it twice on the
  * same pointer is undefined (the handle is gone after the first call). */
 void asp_destroy(asp_handle* h);

@@ -19,7 +19,8 @@ from . import _lib
 from ._lib import (ASP_PREC_C64, ASP_PREC_C128, KIND_L, KIND_M, KIND_R, AspError,  # noqa: F401
                    asp_params, asp_solve_info)
 
-__all__ = ["asp_setup", "asp_footprint_bytes", "AspHandle", "make_params", "AspError",
+__all__ = ["asp_setup", "asp_footprint_bytes", "asp_residual_norms_noalloc", "AspHandle", "make_params",
+           "AspError",
            "ASP_PREC_C64", "ASP_PREC_C128", "KIND_M", "KIND_R", "KIND_L"]
 
 
@@ -162,6 +163,29 @@ class AspHandle:
             self.destroy()
         except Exception:
             pass
+
+
+def asp_residual_norms_noalloc(params: asp_params, c, f, u, rel_res=None, stream=None):
+    """||f_r - A u_r|| / ||f_r|| per right-hand side without any device allocation
+    inside the library (for callers that cannot allocate: graph captures,
+    foreign allocators, allocation-free serving loops).  ``c`` is the float64
+    CUDA velocity (n, n); ``f``, ``u`` complex128 CUDA tensors (n, n, nrhs);
+    ``rel_res`` an optional float64 CUDA tensor of nrhs entries that receives
+    the result (allocated here, by torch, if omitted)."""
+    torch = _torch()
+    n = params.n
+    _dev_vec(f, n, "f")
+    _dev_vec(u, n, "u")
+    if not (c.is_cuda and c.dtype == torch.float64 and c.is_contiguous() and c.numel() == n * n):
+        raise ValueError("c must be a contiguous float64 CUDA tensor with n*n entries")
+    nrhs = f.shape[2]
+    if rel_res is None:
+        rel_res = torch.empty(nrhs, dtype=torch.float64, device=f.device)
+    _lib.check(_lib.load().asp_residual_norms_noalloc(
+        ctypes.byref(params), ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(f.data_ptr()),
+        ctypes.c_void_p(u.data_ptr()), nrhs, ctypes.c_void_p(rel_res.data_ptr()),
+        ctypes.c_void_p(_stream_ptr(stream))), "asp_residual_norms_noalloc")
+    return rel_res
 
 
 def asp_setup(c, params: asp_params) -> AspHandle:

@@ -32,8 +32,10 @@ EXPORTS = [
     "asp_setup", "asp_footprint_bytes", "asp_num_layers", "asp_layer_range", "asp_factor",
     "asp_apply_preconditioner", "asp_matvec", "asp_subproblem_width", "asp_subproblem_solve",
     "asp_gmres_solve", "asp_take_launch_count", "asp_set_phase_timing", "asp_phase_times",
-    "asp_destroy", "asp_error_string", "asp_last_error_detail",
+    "asp_destroy", "asp_error_string", "asp_last_error_detail", "asp_residual_norms_noalloc",
 ]
+NOALLOC_MAX_N = 4096
+NOALLOC_MAX_RHS = 64
 PHASES = ["factor", "tmap", "embed", "chain", "fill", "elementwise", "matvec", "krylov"]
 
 
@@ -95,6 +97,7 @@ def load() -> ctypes.CDLL:
         "asp_set_phase_timing": (I, [P, I]),
         "asp_phase_times": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), I]),
         "asp_destroy": (V, [P]),
+        "asp_residual_norms_noalloc": (I, [ctypes.POINTER(asp_params), P, P, P, I, P, P]),
         "asp_error_string": (ctypes.c_char_p, [I]),
         "asp_last_error_detail": (ctypes.c_char_p, []),
     }
