@@ -185,7 +185,7 @@ Sizes sizes_for(const asp_params* p, int num_sms) {
   bytes += (size_t)2 * (P.m + 1) * n * ((mr + 1) & ~1) * Z.esz;                   // accR, accL
   bytes += (size_t)Z.zslots * Z.zslot * Z.esz;                                   // forward scratch
   bytes += (size_t)(2 * R + 2) * Z.N * mr * sizeof(double2);                     // V, Z, work
-  bytes += (size_t)num_sms * 2 * 9 * mr * sizeof(double2);                       // dot partials
+  bytes += (size_t)num_sms * 4 * 9 * mr * sizeof(double2);                       // dot partials
   bytes += kst + 64;
   Z.bytes = bytes;
   return Z;
@@ -284,7 +284,10 @@ int get_embed_jobs(Handle& H, int nrhs, JobList** out) {
   if (it == c.embed.end()) {
     int wm = 0;
     for (int q = 1; q <= H.m; ++q) wm = std::max(wm, H.subs[H.subM[q]].w);
-    const int cap = btsolve_rhs_capacity(nrhs, wm, H.prec, false);
+    int cap = btsolve_rhs_capacity(nrhs, wm, H.prec, false);
+    // too few layers to give every SM two M-solve jobs: split the right-hand sides
+    while (cap > 8 && (long long)H.m * ((nrhs + cap - 1) / cap) < 3LL * H.num_sms)
+      cap = btsolve_rhs_capacity(cap / 2, wm, H.prec, false);
     std::vector<Job> jobs;
     for (int q = 1; q <= H.m; ++q)
       for (int r0 = 0; r0 < nrhs; r0 += cap) jobs.push_back({H.subM[q], MODE_EMBED, r0, std::min(cap, nrhs - r0)});
@@ -661,7 +664,7 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   dal((void**)&H.V, (size_t)(R + 1) * N * mr * sizeof(double2));
   dal((void**)&H.Z, (size_t)R * N * mr * sizeof(double2));
   dal((void**)&H.wv, (size_t)N * mr * sizeof(double2));
-  dal((void**)&H.red, (size_t)sms * 2 * 9 * mr * sizeof(double2));
+  dal((void**)&H.red, (size_t)sms * 4 * 9 * mr * sizeof(double2));
   size_t n2, nd, ni;
   krylov_state_bytes(R, mr, &n2, &nd, &ni);
   dal((void**)&H.hess, n2 * sizeof(double2));

@@ -14,9 +14,9 @@
 // kept as an explicit inverse, which turns every solve step into a dense
 // matrix product.
 //
-// One CTA of 128 threads factors one subproblem; the n block inversions are
-// sequential.  Thread t owns row i = t mod 64 and every other column
-// (j = t/64, t/64 + 2, ...) of the block, so no index arithmetic divides.
+// One CTA of 256 threads factors one subproblem; the n block inversions are
+// sequential.  Thread t owns row i = t mod 64 and every fourth column
+// (j = t/64, t/64 + 4, ...) of the block, so no index arithmetic divides.
 // Each inversion is Gauss-Jordan with partial pivoting inside the block, in
 // shared memory with implicit row exchanges and two ping-pong buffers: step c
 // picks the largest unused entry of column c as pivot (row r_c, found by every
@@ -32,7 +32,8 @@ namespace asp {
 
 namespace {
 
-constexpr int kFactorThreads = 128;
+constexpr int kFactorThreads = 256;
+constexpr int kColGroups = kFactorThreads / 64;  // threads sharing a row
 
 template <typename R>
 __global__ void __launch_bounds__(kFactorThreads)
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(kFactorThreads)
   __shared__ int col_of_row[64];
   const int tid = threadIdx.x, lane = tid & 31;
   const int i = tid & 63;        // my row
-  const int jh = tid >> 6;       // my column parity
+  const int jh = tid >> 6;       // my first column (then every kColGroups-th)
   const bool row_ok = i < w;
   const Cx<R>* up = F.up + S.prof;
   const Cx<R>* dn = F.dn + S.prof;
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(kFactorThreads)
     if (row_ok) {
       const C diag = cadd(cadd(dg[i], F.cd[k]), cmake<R>(F.k2[(long long)(S.lo - 1 + i) * n + k], R(0)));
       const int pr = (k > 0) ? piv_row[i] : 0;
-      for (int j = jh; j < w; j += 2) {
+      for (int j = jh; j < w; j += kColGroups) {
         C t = czero<R>();
         if (j == i) t = diag;
         else if (j == i + 1) t = up[i];
@@ -104,7 +105,8 @@ __global__ void __launch_bounds__(kFactorThreads)
       if (row_ok) {
         const C aic = src[i * ld + c];
         const C f = cmul(aic, inv);
-        for (int j = jh; j < w; j += 2) {
+#pragma unroll 2
+        for (int j = jh; j < w; j += kColGroups) {
           C v;
           if (i == r) {
             v = (j == c) ? inv : cmul(src[r * ld + j], inv);
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(kFactorThreads)
     if (row_ok) {
       C* Wk = Wsub + (long long)k * w * wp;
       const int pr = piv_row[i];
-      for (int j = jh; j < w; j += 2) Wk[j * wp + i] = src[pr * ld + col_of_row[j]];
+      for (int j = jh; j < w; j += kColGroups) Wk[j * wp + i] = src[pr * ld + col_of_row[j]];
     }
     prev = src;
     // the next formation reads prev and piv/col tables; the barrier after it

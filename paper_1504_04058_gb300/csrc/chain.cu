@@ -31,13 +31,14 @@ constexpr int kMaxRows = 16;  // rows of the product per CTA
 constexpr int kRhs = 32;      // right-hand sides per launch (two per lane, 16 lanes)
 
 template <typename R> struct ChainKC;
-template <> struct ChainKC<float> { static constexpr int v = 128; };
+template <> struct ChainKC<float> { static constexpr int v = 256; };
 template <> struct ChainKC<double> { static constexpr int v = 64; };
 
 template <typename R> __host__ __device__ constexpr size_t chain_smem() {
-  // s_T[2][KC][kMaxRows] + s_src[2][KC][kRhs] + red[kWarps][kMaxRows][kRhs]
-  return sizeof(Cx<R>) * ((size_t)2 * kMaxRows * ChainKC<R>::v + (size_t)2 * ChainKC<R>::v * kRhs +
-                          (size_t)kWarps * kMaxRows * kRhs);
+  // s_T[2][KC][kMaxRows] + s_src[2][KC][kRhs]; the cross-warp reduction buffer
+  // red[kWarps][kMaxRows][kRhs] reuses s_src once the last chunk is consumed
+  static_assert(2 * ChainKC<R>::v >= kWarps * kMaxRows, "reduction buffer must fit in the staging area");
+  return sizeof(Cx<R>) * ((size_t)2 * kMaxRows * ChainKC<R>::v + (size_t)2 * ChainKC<R>::v * kRhs);
 }
 
 __device__ __forceinline__ void pair_ld(const float2* p, float2& a, float2& b) {
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s_T = reinterpret_cast<C*>(smem_raw);                // [2][KC][kMaxRows] (rows fastest)
   C* s_src = s_T + (size_t)2 * kMaxRows * KC;             // [2][KC][kRhs]
-  C* red = s_src + (size_t)2 * KC * kRhs;                 // [kWarps][kMaxRows][kRhs]
+  C* red = s_src;                                         // [kWarps][kMaxRows][kRhs], after the chunks
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
           cfma(a[i][1], tv[i], s1);
         }
       }
-      __syncthreads();  // buffer (ch & 1) is refilled two chunks later
+      __syncthreads();  // buffer (ch & 1) is refilled two chunks later (and red reuses s_src)
     }
     // cross-warp reduction and accumulation into dst
 #pragma unroll

@@ -70,24 +70,45 @@ __global__ void gs_dot_kernel(VecList V, int J, int want_norm, const double2* __
   __shared__ double2 red[kVecThreads];
   const int bt = blockDim.x;
   const int t = threadIdx.x;
-  double2 acc[kDotChunk + 1];
+  // two independent accumulator sets (elements e and e + stride) keep two
+  // FP64 dependency chains in flight per thread
+  double2 acc[2][kDotChunk + 1];
 #pragma unroll
-  for (int j = 0; j <= kDotChunk; ++j) acc[j] = make_double2(0, 0);
-  for (long long e = (long long)blockIdx.x * bt + t; e < count; e += (long long)gridDim.x * bt) {
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int j = 0; j <= kDotChunk; ++j) acc[u][j] = make_double2(0, 0);
+  const long long stride = (long long)gridDim.x * bt;
+  long long e = (long long)blockIdx.x * bt + t;
+  for (; e + stride < count; e += 2 * stride) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const long long eu = e + u * stride;
+      const double2 we = w[eu];
+#pragma unroll
+      for (int j = 0; j < kDotChunk; ++j)
+        if (j < J) {
+          const double2 v = V.v[j][eu];
+          acc[u][j].x = fma(v.x, we.x, fma(v.y, we.y, acc[u][j].x));
+          acc[u][j].y = fma(v.x, we.y, fma(-v.y, we.x, acc[u][j].y));
+        }
+      if (want_norm) acc[u][kDotChunk].x = fma(we.x, we.x, fma(we.y, we.y, acc[u][kDotChunk].x));
+    }
+  }
+  if (e < count) {
     const double2 we = w[e];
 #pragma unroll
     for (int j = 0; j < kDotChunk; ++j)
       if (j < J) {
         const double2 v = V.v[j][e];
-        acc[j].x = fma(v.x, we.x, fma(v.y, we.y, acc[j].x));
-        acc[j].y = fma(v.x, we.y, fma(-v.y, we.x, acc[j].y));
+        acc[0][j].x = fma(v.x, we.x, fma(v.y, we.y, acc[0][j].x));
+        acc[0][j].y = fma(v.x, we.y, fma(-v.y, we.x, acc[0][j].y));
       }
-    if (want_norm) acc[kDotChunk].x = fma(we.x, we.x, fma(we.y, we.y, acc[kDotChunk].x));
+    if (want_norm) acc[0][kDotChunk].x = fma(we.x, we.x, fma(we.y, we.y, acc[0][kDotChunk].x));
   }
 #pragma unroll
   for (int j = 0; j <= kDotChunk; ++j) {
     if (j < J || (j == kDotChunk && want_norm)) {
-      red[t] = acc[j];
+      red[t] = make_double2(acc[0][j].x + acc[1][j].x, acc[0][j].y + acc[1][j].y);
       __syncthreads();
       if (t < nrhs) {
         double2 s = make_double2(0, 0);
@@ -136,11 +157,18 @@ __global__ void gs_axpy_kernel(VecList V, int J, const double2* __restrict__ coe
     }
   }
   double nacc = 0.0;
-  for (long long e = (long long)blockIdx.x * bt + t; e < count; e += (long long)gridDim.x * bt) {
-    double2 acc = w[e];
+  const long long stride = (long long)gridDim.x * bt;
+  for (long long e = (long long)blockIdx.x * bt + t; e < count; e += stride) {
+    // even and odd terms in separate chains, then w + (even + odd)
+    double2 a0 = make_double2(0, 0), a1 = make_double2(0, 0);
 #pragma unroll
-    for (int j = 0; j < kDotChunk; ++j)
-      if (j < J) cfma(acc, c[j], V.v[j][e]);
+    for (int j = 0; j < kDotChunk; j += 2) {
+      if (j < J) cfma(a0, c[j], V.v[j][e]);
+      if (j + 1 < J) cfma(a1, c[j + 1], V.v[j + 1][e]);
+    }
+    double2 acc = w[e];
+    acc.x += a0.x + a1.x;
+    acc.y += a0.y + a1.y;
     w[e] = acc;
     if (want_norm) nacc = fma(acc.x, acc.x, fma(acc.y, acc.y, nacc));
   }
@@ -439,7 +467,7 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
     G.K.need = pi;
   }
   G.red_threads = nrhs * std::max(1, kVecThreads / nrhs);
-  G.red_blocks = H.num_sms * 2;
+  G.red_blocks = H.num_sms * 4;
   G.partial = reinterpret_cast<double2*>(H.red);
   const long long count = G.count;
   const int gv = grid_for(count, kVecThreads, H.num_sms);
