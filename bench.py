@@ -139,7 +139,7 @@ def _traffic_from_profile(kernel_phase):
                 kv[k.strip()] = v.strip()
     except OSError:
         return None
-    src = os.path.join(ROOT, "paper_1504_04058_gb300", "csrc", "btsolve.cu")
+    src = os.path.join(ROOT, "paper_1504_04058_gb300", "csrc", "btsolve.cuh")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if kv.get("btsolve_sha256_16") != sha:
         return None

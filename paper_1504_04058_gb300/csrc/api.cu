@@ -19,6 +19,7 @@
 #include <string>
 #include <vector>
 
+#include "btsolve.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -31,6 +32,7 @@ size_t krylov_state_bytes(int restart, int nrhs, size_t* n2, size_t* nd, size_t*
 static thread_local std::string g_detail;
 
 static cudaEvent_t pool_event(Handle& H) {
+  std::lock_guard<std::mutex> lock(H.rec_mu);
   if (!H.evpool.empty()) {
     cudaEvent_t e = H.evpool.back();
     H.evpool.pop_back();
@@ -41,25 +43,27 @@ static cudaEvent_t pool_event(Handle& H) {
   return e;
 }
 
-void phase_begin(Handle& H, int phase, cudaStream_t s) {
-  if (!H.timing) return;
-  H.open_phase = phase;
-  H.open_ev = pool_event(H);
-  if (H.open_ev) cudaEventRecord(H.open_ev, s);
+PhaseTok phase_begin(Handle& H, int phase, cudaStream_t s) {
+  PhaseTok t;
+  if (!H.timing) return t;
+  t.phase = phase;
+  t.a = pool_event(H);
+  if (t.a) cudaEventRecord(t.a, s);
+  return t;
 }
 
-void phase_end(Handle& H, cudaStream_t s) {
-  if (!H.timing || H.open_phase < 0 || !H.open_ev) return;
+void phase_end(Handle& H, PhaseTok t, cudaStream_t s) {
+  if (!H.timing || t.phase < 0 || !t.a) return;
   cudaEvent_t b = pool_event(H);
+  std::lock_guard<std::mutex> lock(H.rec_mu);
   if (b) {
     cudaEventRecord(b, s);
-    H.recs.push_back({H.open_phase, H.open_ev, b});
+    H.recs.push_back({t.phase, t.a, b});
   } else {
-    H.evpool.push_back(H.open_ev);
+    H.evpool.push_back(t.a);
   }
-  H.open_phase = -1;
-  H.open_ev = nullptr;
 }
+
 void set_detail(const std::string& s) { g_detail = s; }
 int fail(int code, const std::string& detail) {
   g_detail = detail;
@@ -284,10 +288,7 @@ int get_embed_jobs(Handle& H, int nrhs, JobList** out) {
   if (it == c.embed.end()) {
     int wm = 0;
     for (int q = 1; q <= H.m; ++q) wm = std::max(wm, H.subs[H.subM[q]].w);
-    int cap = btsolve_rhs_capacity(nrhs, wm, H.prec, false);
-    // too few layers to give every SM two M-solve jobs: split the right-hand sides
-    while (cap > 8 && (long long)H.m * ((nrhs + cap - 1) / cap) < 3LL * H.num_sms)
-      cap = btsolve_rhs_capacity(cap / 2, wm, H.prec, false);
+    const int cap = btsolve_rhs_capacity(nrhs, wm, H.prec, false);
     std::vector<Job> jobs;
     for (int q = 1; q <= H.m; ++q)
       for (int r0 = 0; r0 < nrhs; r0 += cap) jobs.push_back({H.subM[q], MODE_EMBED, r0, std::min(cap, nrhs - r0)});
@@ -341,6 +342,7 @@ SolveParams base_params(Handle& H, int ldv) {
   P.tmap = H.tmap;
   P.zscr = H.zscr;
   P.zslot = H.zslot;
+  P.zslots = H.zslots;
   P.err = H.err;
   return P;
 }
@@ -365,9 +367,9 @@ int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_
   const long long count = H.N * nrhs;
   const void* in = r;
   if (H.prec == ASP_PREC_C64) {
-    phase_begin(H, PH_SUM, s);
+    PhaseTok tk = phase_begin(H, PH_SUM, s);
     if (launch_to_prec(r, H.r_lo, count, H.prec, s) != cudaSuccess) return fail(ASP_ERR_CUDA, "to_prec launch");
-    phase_end(H, s);
+    phase_end(H, tk, s);
     H.launches += 1;
     in = H.r_lo;
   }
@@ -381,9 +383,9 @@ int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_
   P.in = in;
   P.jobs = je->d;
   P.njobs = je->n;
-  phase_begin(H, PH_EMBED, s);
-  cudaError_t ce = launch_btsolve(H, P, je->cap, je->wmax, s);
-  phase_end(H, s);
+  PhaseTok tk = phase_begin(H, PH_EMBED, s);
+  cudaError_t ce = launch_btsolve_apply(H, P, CLS_EMBED, je->cap, je->wmax, s);
+  phase_end(H, tk, s);
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("M-solve launch: ") + cudaGetErrorString(ce));
   // 2. accumulated traces of both sweeps (Algorithm 2, second and third loops)
   const size_t esz = H.prec == ASP_PREC_C128 ? sizeof(double2) : sizeof(float2);
@@ -394,23 +396,23 @@ int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_
     C.accR = (char*)H.accR + r0 * esz;
     C.accL = (char*)H.accL + r0 * esz;
     C.bar = H.bar; C.err = H.err;
-    phase_begin(H, PH_CHAIN, s);
+    tk = phase_begin(H, PH_CHAIN, s);
     ce = launch_chain(H, C, s);
-    phase_end(H, s);
+    phase_end(H, tk, s);
     if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("sweep chain launch: ") + cudaGetErrorString(ce));
   }
   // 3. the right- and left-going layer fields from the accumulated traces
   P.jobs = jf->d;
   P.njobs = jf->n;
-  phase_begin(H, PH_FILL, s);
-  ce = launch_btsolve(H, P, jf->cap, jf->wmax, s);
-  phase_end(H, s);
+  tk = phase_begin(H, PH_FILL, s);
+  ce = launch_btsolve_apply(H, P, CLS_FILL, jf->cap, jf->wmax, s);
+  phase_end(H, tk, s);
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("fill launch: ") + cudaGetErrorString(ce));
   // 4. u~_p = u~_{p,1:p-1} + u~_{p,p} + u~_{p,p+1:m}
   const long long per_col = (long long)H.n * nrhs;
   const int r_from = H.x_hi[1];       // 0-based first column of X_2
   const int l_below = H.x_lo[H.m] - 1;  // 0-based first column of X_m
-  phase_begin(H, PH_SUM, s);
+  tk = phase_begin(H, PH_SUM, s);
   const dim3 sgrid((unsigned)((per_col + 255) / 256), (unsigned)H.n);
   if (H.prec == ASP_PREC_C64)
     sum3_kernel<float><<<sgrid, 256, 0, s>>>((float2*)H.uM, (float2*)H.uR, (float2*)H.uL, z, per_col, r_from,
@@ -418,7 +420,7 @@ int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_
   else
     sum3_kernel<double><<<sgrid, 256, 0, s>>>((double2*)H.uM, (double2*)H.uR, (double2*)H.uL, z, per_col, r_from,
                                               l_below);
-  phase_end(H, s);
+  phase_end(H, tk, s);
   H.launches += 1;
   ce = cudaGetLastError();
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("sum launch: ") + cudaGetErrorString(ce));
@@ -479,6 +481,7 @@ int asp_phase_times(asp_handle* hd, double* ms, long long* launches, int nphases
     if (ms) ms[i] = 0.0;
     if (launches) launches[i] = 0;
   }
+  std::lock_guard<std::mutex> lock(H.rec_mu);
   for (auto& r : H.recs) {
     float t = 0.f;
     if (r.phase < nphases && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
@@ -506,6 +509,9 @@ void asp_destroy(asp_handle* hd) {
   for (void* p : H.coef_bufs)
     if (p) cudaFree(p);
   if (H.h_flags) cudaFreeHost(H.h_flags);
+  if (H.ev_fork) cudaEventDestroy(H.ev_fork);
+  if (H.ev_join) cudaEventDestroy(H.ev_join);
+  if (H.aux) cudaStreamDestroy(H.aux);
   delete hd;
 }
 
@@ -672,6 +678,9 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   dal((void**)&H.kflags, ni * sizeof(int));
   dal((void**)&H.err, 2 * sizeof(int));
   if (ok && cudaMallocHost((void**)&H.h_flags, 64) != cudaSuccess) ok = false;
+  if (ok && cudaStreamCreateWithFlags(&H.aux, cudaStreamNonBlocking) != cudaSuccess) ok = false;
+  if (ok && cudaEventCreateWithFlags(&H.ev_fork, cudaEventDisableTiming) != cudaSuccess) ok = false;
+  if (ok && cudaEventCreateWithFlags(&H.ev_join, cudaEventDisableTiming) != cudaSuccess) ok = false;
   if (!ok) {
     asp_destroy(hd);
     cudaGetLastError();
@@ -742,9 +751,19 @@ int asp_factor(asp_handle* hd, void* stream) {
   if (!hd) return fail(ASP_ERR_INVALID, "null handle");
   Handle& H = hd->h;
   cudaStream_t s = (cudaStream_t)stream;
-  phase_begin(H, PH_FACTOR, s);
-  cudaError_t ce = launch_factor(H, s);
-  phase_end(H, s);
+  // The M-subproblems (indices [0, m)) factor on the internal stream while the
+  // R/L subproblems (indices [m, 3m-2)) factor on the caller's stream and their
+  // transfer maps are built; the M factors are latency-bound and overlap well.
+  const int m = H.m;
+  if (cudaEventRecord(H.ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(H.aux, H.ev_fork, 0) != cudaSuccess)
+    return fail(ASP_ERR_CUDA, "factor: stream fork");
+  PhaseTok ta = phase_begin(H, PH_FACTOR, H.aux);
+  cudaError_t ce = launch_factor(H, 0, m, H.aux);
+  phase_end(H, ta, H.aux);
+  if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString(ce));
+  PhaseTok tb = phase_begin(H, PH_FACTOR, s);
+  ce = launch_factor(H, m, (int)H.subs.size() - m, s);
+  phase_end(H, tb, s);
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString(ce));
   // transfer maps: columns of T_p^R and T_p^L in chunks of right-hand sides
   if (H.m >= 3) {
@@ -765,11 +784,13 @@ int asp_factor(asp_handle* hd, void* stream) {
     SolveParams P = base_params(H, 1);
     P.jobs = L.d;
     P.njobs = L.n;
-    phase_begin(H, PH_TMAP, s);
-    ce = launch_btsolve(H, P, cap, H.wmaxRL, s);
-    phase_end(H, s);
+    PhaseTok tk = phase_begin(H, PH_TMAP, s);
+    ce = launch_btsolve_aux(H, P, CLS_TMAP, cap, H.wmaxRL, s);
+    phase_end(H, tk, s);
     if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("transfer-map launch: ") + cudaGetErrorString(ce));
   }
+  if (cudaEventRecord(H.ev_join, H.aux) != cudaSuccess || cudaStreamWaitEvent(s, H.ev_join, 0) != cudaSuccess)
+    return fail(ASP_ERR_CUDA, "factor: stream join");
   int rc = check_err(H, s, "factor");
   if (rc != ASP_OK) return rc;
   H.factored = true;
@@ -789,9 +810,9 @@ int asp_matvec(asp_handle* hd, const void* x, void* y, int nrhs, void* stream) {
   Handle& H = hd->h;
   if (nrhs < 1 || nrhs > H.prm.max_rhs) return fail(ASP_ERR_INVALID, "nrhs out of range");
   if (x == y) return fail(ASP_ERR_INVALID, "x and y alias");
-  phase_begin(H, PH_MATVEC, (cudaStream_t)stream);
+  PhaseTok tk = phase_begin(H, PH_MATVEC, (cudaStream_t)stream);
   cudaError_t ce = launch_matvec(H, (const double2*)x, (double2*)y, nrhs, (cudaStream_t)stream);
-  phase_end(H, (cudaStream_t)stream);
+  phase_end(H, tk, (cudaStream_t)stream);
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("matvec launch: ") + cudaGetErrorString(ce));
   return ASP_OK;
 }
@@ -821,7 +842,7 @@ int asp_subproblem_solve(asp_handle* hd, int kind, int p, const void* g, void* v
       return fail(ASP_ERR_CUDA, "to_prec launch");
     in = H.r_lo;
   }
-  const int cap = btsolve_rhs_capacity(nrhs, w, H.prec, false);
+  const int cap = nrhs >= 4 ? 4 : 1;
   JobCache& jc = caches()[&H];
   const long long key = (long long)idx * 1024 + nrhs;
   auto it = jc.sub.find(key);
@@ -839,7 +860,7 @@ int asp_subproblem_solve(asp_handle* hd, int kind, int p, const void* g, void* v
   P.outSub = v;
   P.jobs = L.d;
   P.njobs = L.n;
-  cudaError_t ce = launch_btsolve(H, P, cap, w, s);
+  cudaError_t ce = launch_btsolve_aux(H, P, CLS_SUB, cap, w, s);
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("subproblem launch: ") + cudaGetErrorString(ce));
   return ASP_OK;
 }

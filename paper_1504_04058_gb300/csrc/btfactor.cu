@@ -37,11 +37,12 @@ constexpr int kColGroups = kFactorThreads / 64;  // threads sharing a row
 
 template <typename R>
 __global__ void __launch_bounds__(kFactorThreads)
-    btfactor_kernel(const SubDesc* __restrict__ subs, FactorCoefs<R> F, int n, Cx<R>* __restrict__ Wout,
-                    int* err) {
+    btfactor_kernel(const SubDesc* __restrict__ subs, int first, FactorCoefs<R> F, int n,
+                    Cx<R>* __restrict__ Wout, int* err) {
   using C = Cx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const SubDesc S = subs[blockIdx.x];
+  const int sub = first + blockIdx.x;
+  const SubDesc S = subs[sub];
   const int w = S.w, wp = S.wp;
   const int ld = w | 1;  // odd row stride: column accesses spread over the banks
   C* buf0 = reinterpret_cast<C*>(smem_raw);
@@ -133,25 +134,27 @@ __global__ void __launch_bounds__(kFactorThreads)
     // the next formation reads prev and piv/col tables; the barrier after it
     // orders those reads before the next Gauss-Jordan overwrites them
   }
-  if (bad && tid == 0) record_error(err, ASP_ERR_SMALL_PIVOT, blockIdx.x);
+  if (bad && tid == 0) record_error(err, ASP_ERR_SMALL_PIVOT, sub);
 }
 
 }  // namespace
 
-cudaError_t launch_factor(Handle& H, cudaStream_t s) {
-  const int nsub = (int)H.subs.size();
-  if (nsub == 0) return cudaSuccess;
+cudaError_t launch_factor(Handle& H, int first, int count, cudaStream_t s) {
+  const int nsub = count;
+  if (nsub <= 0) return cudaSuccess;
   const size_t esz = H.prec == ASP_PREC_C128 ? sizeof(double2) : sizeof(float2);
   const size_t smem = 2 * (size_t)H.wmax * (H.wmax | 1) * esz;
   cudaError_t e;
   if (H.prec == ASP_PREC_C128) {
     e = cudaFuncSetAttribute(btfactor_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    btfactor_kernel<double><<<nsub, kFactorThreads, smem, s>>>(H.d_subs, H.fc64, H.n, (double2*)H.W, H.err);
+    btfactor_kernel<double><<<nsub, kFactorThreads, smem, s>>>(H.d_subs, first, H.fc64, H.n, (double2*)H.W,
+                                                                H.err);
   } else {
     e = cudaFuncSetAttribute(btfactor_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    btfactor_kernel<float><<<nsub, kFactorThreads, smem, s>>>(H.d_subs, H.fc32, H.n, (float2*)H.W, H.err);
+    btfactor_kernel<float><<<nsub, kFactorThreads, smem, s>>>(H.d_subs, first, H.fc32, H.n, (float2*)H.W,
+                                                               H.err);
   }
   H.launches += 1;
   return cudaGetLastError();

@@ -1,6 +1,8 @@
-// btsolve.cu -- batched solves with the layer factors: the G~ operators of
+// btsolve.cuh -- batched solves with the layer factors: the G~ operators of
 // Section 3.1 ("Auxiliary Green's operators") for many subproblems and
-// right-hand sides in one launch.
+// right-hand sides in one launch.  Included by btsolve_apply.cu (M-solves and
+// sweep fills) and btsolve_aux.cu (transfer maps and single solves), which
+// instantiate it.
 //
 // A job is (subproblem, block of right-hand sides, mode).  For one job the CTA
 // runs the two passes of the block-tridiagonal solve with the factors of
@@ -9,12 +11,13 @@
 //     backward  x_{n-1} = z_{n-1},  x_k = z_k - c_k W_k x_{k+1},   k = n-2 .. 0
 // Each step multiplies the dense w x w block W_k by a w x NR panel of
 // right-hand sides.  Work split: every thread owns a 2-row x TC-column tile of
-// the panel (rows i0, i0+1; right-hand sides r0 .. r0+TC-1) for the whole job,
-// so the recurrences (z_{k-1} -> y_k, x_{k+1} -> x_k) stay in its registers;
-// a warp covers (32/LC)*2 rows x LC*TC right-hand sides, the CTA stacks warps
-// over rows (and, for 64 right-hand sides, over two column blocks).  The inner
-// product loads two rows of W_k (one 16-byte shared load for complex64) and TC
-// panel entries per column j and issues 8*TC FMAs.
+// the panel for the whole job, so the recurrences (z_{k-1} -> y_k,
+// x_{k+1} -> x_k) stay in its registers; a warp covers (32/LC)*2 rows x LC*TC
+// right-hand sides, the CTA stacks warps over rows (and NCW column blocks).
+// The inner product loads two rows of W_k (one 16-byte shared load for
+// complex64) and TC panel entries per column j and issues 8*TC FMAs.  A
+// thread's TC columns come in pairs 2*LC apart so that lanes sharing a row
+// touch one contiguous span (no shared-memory bank conflicts).
 //
 // Data movement: the W_k blocks stream from HBM through a 3-stage
 // shared-memory ring filled by 1D bulk (TMA) copies that complete on
@@ -22,22 +25,29 @@
 // the z_k saved by the forward pass in a per-CTA scratch slot) stream through
 // a per-thread cp.async ring.  One __syncthreads per step publishes the panel.
 //
-// Modes (what g_k is and what is written):
-//   EMBED   G~_q^M f_q: g = input on the rows of X_q;  writes x on X_q to outM,
-//           its first / last X_q column to the left / right trace buffers.
-//   FILL_R  G~_p^R w: g = -(1/h^2) accR[p-1] on local column 0; writes x on X_p to outR.
-//   FILL_L  G~_p^L w: g = -(1/h^2) accL[p+1] on local column w-1; writes outL.
-//   TMAP_R  columns r of the dense map w -> (G~_p^R w)^R: g = -(1/h^2) e_r on column 0;
-//           keeps the last column of X_p.  The forward pass starts at block k0 = first r
-//           of the job (earlier blocks are zero).
-//   TMAP_L  same for G~_p^L, g on column w-1, keeps the first column of X_p.
-//   SUB     v = H^-1 g on the whole padded grid (checking entry point).
+// Mode classes (compile time) and modes (per job):
+//   CLS_EMBED  EMBED   G~_q^M f_q: g = input on the rows of X_q; writes x on X_q
+//                      to outM and its first / last X_q column to the trace buffers.
+//   CLS_FILL   FILL_R  G~_p^R w: g = -(1/h^2) accR[p-1] on local column 0; x on X_p -> outR.
+//              FILL_L  G~_p^L w: g = -(1/h^2) accL[p+1] on local column w-1; -> outL.
+//   CLS_TMAP   TMAP_R  columns r of the dense map w -> (G~_p^R w)^R: g = -(1/h^2) e_r on
+//                      column 0; keeps the last column of X_p.  The forward pass starts
+//                      at block k0 = the job's first r (earlier blocks are zero).
+//              TMAP_L  same for G~_p^L: g on column w-1, keeps the first column of X_p.
+//   CLS_SUB    SUB     v = H^-1 g on the whole padded grid (checking entry point).
+// Per job every thread resolves, for its two rows, whether the row takes
+// input, where its input and outputs live, and the per-step strides, so the
+// step loop does only pointer increments.
+#pragma once
+
 #include "common.cuh"
 #include "internal.h"
 
 namespace asp {
 
-namespace {
+enum ModeClass : int { CLS_EMBED = 0, CLS_FILL = 1, CLS_TMAP = 2, CLS_SUB = 3 };
+
+namespace bts {
 
 constexpr int kStages = 3;  // W-block ring depth
 constexpr int kRing = 3;    // per-thread input ring depth
@@ -66,7 +76,6 @@ struct Tiling {
   }
 };
 
-// ---- vector shared-memory access of a complex pair / single
 template <typename C> struct Vec2;
 template <> struct Vec2<float2> {
   __device__ static void ld(const float2* p, float2& a, float2& b) {
@@ -83,9 +92,6 @@ template <> struct Vec2<double2> {
   __device__ static void st(double2* p, double2 a, double2 b) { p[0] = a; p[1] = b; }
 };
 
-// A thread's TC panel entries: for TC = 1 one column; for TC >= 2 pairs of
-// adjacent columns placed 2*LC apart, so that the LC lanes sharing a row read
-// and write one contiguous span per pair (no shared-memory bank conflicts).
 template <typename C, int TC, int PS> __device__ __forceinline__ void ld_cols(const C* p, C (&v)[TC]) {
   if constexpr (TC == 1) {
     v[0] = p[0];
@@ -103,12 +109,13 @@ template <typename C, int TC, int PS> __device__ __forceinline__ void st_cols(C*
   }
 }
 
-template <typename R, int TC, int LC, int NCW, int MAXT, int MINB>
+template <typename R, int TC, int LC, int NCW, int MAXT, int MINB, int CLS>
 __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geometry G) {
   using C = Cx<R>;
   using T = Tiling<R, TC, LC, NCW>;
   constexpr int TR = T::TR, WR = T::WR, WC = T::WC, NR = T::NR, E = T::E;
   constexpr int CB = (int)sizeof(C);
+  constexpr int PS = 2 * LC;  // column distance between a thread's pairs
   extern __shared__ __align__(128) unsigned char smem[];
   const int NT = blockDim.x;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -120,14 +127,15 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int wr = warp / NCW, wc = warp % NCW;
-  constexpr int PS = 2 * LC;                  // column distance between a thread's pairs
-  const int i0 = wr * WR + (lane / LC) * TR;  // first row of this thread's tile
-  const int r0 = wc * WC + (TC == 1 ? (lane % LC) : 2 * (lane % LC));  // its first column
+  const int i0 = wr * WR + (lane / LC) * TR;                            // first row of the tile
+  const int r0 = wc * WC + (TC == 1 ? (lane % LC) : 2 * (lane % LC));  // first column of the tile
   auto rhs_of = [&](int c) { return TC == 1 ? r0 : r0 + (c & 1) + (c >> 1) * PS; };
   const int n = P.n, ldv = P.ldv, lda = P.ldacc, ldT = P.ldT;
   const C* __restrict__ Wg = reinterpret_cast<const C*>(P.W);
   C* zslot = reinterpret_cast<C*>(P.zscr) + (long long)blockIdx.x * P.zslot;
   const C neg_ih2 = cmake<R>(R(-P.inv_h2), R(0));
+  const C* cap = reinterpret_cast<const C*>(P.ca);
+  const C* ccp = reinterpret_cast<const C*>(P.cc);
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
@@ -141,14 +149,65 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
     const Job J = P.jobs[job];
     const SubDesc S = P.subs[J.sub];
     const int w = S.w, wp = S.wp, xoff = S.xoff, xw = S.xw, lo = S.lo, p = S.p;
-    const int mode = J.mode, rhs0 = J.rhs0, nr = J.nr;
-    const bool tmap = (mode == MODE_TMAP_R || mode == MODE_TMAP_L);
-    const int k0 = tmap ? rhs0 : 0;
+    const int rhs0 = J.rhs0, nr = J.nr;
+    const bool right = (J.mode == MODE_FILL_R || J.mode == MODE_TMAP_R);
+    const int k0 = (CLS == CLS_TMAP) ? rhs0 : 0;
     const int nf = n - k0;
     const int L = nf + (n - 1);
     const uint32_t bbytes = (uint32_t)(w * wp * CB);
     const C* Wsub = Wg + S.woff;
     auto blk = [&](int q) { return q < nf ? k0 + q : n - 2 - (q - nf); };
+
+    // ---- per-job, per-row resolution of inputs and outputs
+    const int bnd = right ? 0 : w - 1;                 // boundary-data row (FILL, TMAP)
+    const int keep = right ? xoff + xw - 1 : xoff;     // kept column (TMAP)
+    bool row_ok[TR], has_in[TR], out_row[TR], trR[TR], trL[TR];
+    const C* in_base[TR];
+    C* out_base[TR];
+    long long in_step = 0, out_step = 0;
+#pragma unroll
+    for (int a = 0; a < TR; ++a) {
+      const int i = i0 + a;
+      row_ok[a] = i < w;
+      const bool inx = i >= xoff && i < xoff + xw;
+      has_in[a] = false; out_row[a] = false; trR[a] = false; trL[a] = false;
+      in_base[a] = nullptr; out_base[a] = nullptr;
+      if (CLS == CLS_EMBED) {
+        has_in[a] = row_ok[a] && inx;
+        in_base[a] = reinterpret_cast<const C*>(P.in) + (long long)(lo - 1 + i) * n * ldv + rhs0;
+        in_step = ldv;
+        out_row[a] = has_in[a];
+        out_base[a] = reinterpret_cast<C*>(P.outM) + (long long)(lo - 1 + i) * n * ldv + rhs0;
+        out_step = ldv;
+        trR[a] = row_ok[a] && i == xoff + xw - 1;
+        trL[a] = row_ok[a] && i == xoff;
+      } else if (CLS == CLS_FILL) {
+        has_in[a] = row_ok[a] && i == bnd;
+        in_base[a] = reinterpret_cast<const C*>(right ? P.accR : P.accL) +
+                     (long long)(right ? p - 1 : p + 1) * n * lda + rhs0;
+        in_step = lda;
+        out_row[a] = row_ok[a] && inx;
+        out_base[a] = reinterpret_cast<C*>(right ? P.outR : P.outL) + (long long)(lo - 1 + i) * n * ldv + rhs0;
+        out_step = ldv;
+      } else if (CLS == CLS_TMAP) {
+        has_in[a] = row_ok[a] && i == bnd;  // computed, not loaded
+        out_row[a] = row_ok[a] && i == keep;
+        out_base[a] = reinterpret_cast<C*>(P.tmap) + S.toff + rhs0;
+        out_step = ldT;
+      } else {  // CLS_SUB
+        has_in[a] = row_ok[a];
+        in_base[a] = reinterpret_cast<const C*>(P.in) + (long long)i * n * ldv + rhs0;
+        in_step = ldv;
+        out_row[a] = row_ok[a];
+        out_step = ldv;
+      }
+    }
+    C* zrow[TR];
+#pragma unroll
+    for (int a = 0; a < TR; ++a) zrow[a] = zslot + (long long)(i0 + a) * NR;
+    const long long zstep = (long long)w * NR;
+    C* accRp = reinterpret_cast<C*>(P.accR) + (long long)p * n * lda + rhs0;
+    C* accLp = reinterpret_cast<C*>(P.accL) + (long long)p * n * lda + rhs0;
 
     __syncthreads();  // the previous job's last reads of the W ring and panels are done
     if (tid == 0) {
@@ -159,43 +218,28 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
       }
     }
 
-    // which of this thread's entries take input in the forward pass
-    auto row_has_input = [&](int i) {
-      if (mode == MODE_EMBED) return i >= xoff && i < xoff + xw;
-      if (mode == MODE_FILL_R) return i == 0;
-      if (mode == MODE_FILL_L) return i == w - 1;
-      if (mode == MODE_SUB) return i < w;
-      return false;
-    };
-    const C* inM = reinterpret_cast<const C*>(P.in);
-    const C* accRp = reinterpret_cast<const C*>(P.accR);
-    const C* accLp = reinterpret_cast<const C*>(P.accL);
     auto load_step = [&](int q2) {
       if (q2 < L) {
         const int kk = blk(q2);
         C* slot = ring + (size_t)(q2 % kRing) * E * NT;
         if (q2 < nf) {
+          if (CLS != CLS_TMAP) {
 #pragma unroll
-          for (int a = 0; a < TR; ++a) {
-            const int i = i0 + a;
-            if (i >= w || !row_has_input(i)) continue;
-            const C* src;
-            if (mode == MODE_EMBED) src = inM + ((long long)(lo - 1 + i) * n + kk) * ldv + rhs0;
-            else if (mode == MODE_FILL_R) src = accRp + ((long long)(p - 1) * n + kk) * lda + rhs0;
-            else if (mode == MODE_FILL_L) src = accLp + ((long long)(p + 1) * n + kk) * lda + rhs0;
-            else src = inM + ((long long)i * n + kk) * ldv + rhs0;
+            for (int a = 0; a < TR; ++a) {
+              if (!has_in[a]) continue;
+              const C* src = in_base[a] + (long long)kk * in_step;
 #pragma unroll
-            for (int c = 0; c < TC; ++c)
-              if (rhs_of(c) < nr) cp_async<CB>(slot + (size_t)(a * TC + c) * NT + tid, src + rhs_of(c));
+              for (int c = 0; c < TC; ++c)
+                if (rhs_of(c) < nr) cp_async<CB>(slot + (size_t)(a * TC + c) * NT + tid, src + rhs_of(c));
+            }
           }
         } else if (kk >= k0 && kk <= n - 3) {
 #pragma unroll
           for (int a = 0; a < TR; ++a) {
-            const int i = i0 + a;
-            if (i >= w) continue;
+            if (!row_ok[a]) continue;
+            const C* src = zrow[a] + (long long)kk * zstep;
 #pragma unroll
-            for (int c = 0; c < TC; ++c)
-              cp_async<CB>(slot + (size_t)(a * TC + c) * NT + tid, zslot + ((long long)kk * w + i) * NR + rhs_of(c));
+            for (int c = 0; c < TC; ++c) cp_async<CB>(slot + (size_t)(a * TC + c) * NT + tid, src + rhs_of(c));
           }
         }
       }
@@ -210,8 +254,6 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
 #pragma unroll
       for (int c = 0; c < TC; ++c) carry[a][c] = zkeep[a][c] = czero<R>();
 
-    const C* cap = reinterpret_cast<const C*>(P.ca);
-    const C* ccp = reinterpret_cast<const C*>(P.cc);
     C ak_next = cap[blk(0)], ck_next = ccp[blk(0)];
     for (int q = 0; q < L; ++q) {
       const int k = blk(q);
@@ -231,22 +273,19 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
       // ---- this step's panel rows of the thread's tile
 #pragma unroll
       for (int a = 0; a < TR; ++a) {
-        const int i = i0 + a;
-        if (i >= w) continue;
+        if (!row_ok[a]) continue;
         C y[TC];
         if (fwd) {
-          const bool has = row_has_input(i);
 #pragma unroll
           for (int c = 0; c < TC; ++c) {
-            const int r = rhs_of(c);
             C g = czero<R>();
-            if (has && r < nr) {
-              g = slot[(size_t)(a * TC + c) * NT + tid];
-              if (mode == MODE_FILL_R || mode == MODE_FILL_L) g = cmul(neg_ih2, g);
-            } else if (mode == MODE_TMAP_R) {
-              if (i == 0 && r < nr && k == rhs0 + r) g = neg_ih2;
-            } else if (mode == MODE_TMAP_L) {
-              if (i == w - 1 && r < nr && k == rhs0 + r) g = neg_ih2;
+            if (has_in[a] && rhs_of(c) < nr) {
+              if (CLS == CLS_TMAP) {
+                if (k == rhs0 + rhs_of(c)) g = neg_ih2;
+              } else {
+                g = slot[(size_t)(a * TC + c) * NT + tid];
+                if (CLS == CLS_FILL) g = cmul(neg_ih2, g);
+              }
             }
             y[c] = g;
             cfms(y[c], a_k, carry[a][c]);
@@ -255,7 +294,7 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
 #pragma unroll
           for (int c = 0; c < TC; ++c) y[c] = carry[a][c];
         }
-        st_cols<C, TC, PS>(yb + (size_t)i * NR + r0, y);
+        st_cols<C, TC, PS>(yb + (size_t)(i0 + a) * NR + r0, y);
       }
       __syncthreads();
       if (s_abort) return;
@@ -278,37 +317,39 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
       for (int a = 0; a < TR; ++a)
 #pragma unroll
         for (int c = 0; c < TC; ++c) acc[a][c] = czero<R>();
-      if (i0 < w) {
+      if (row_ok[0]) {
+        const C* yj = yb + r0;
+        const C* wj = Wk + i0;
 #pragma unroll 2
         for (int j = 0; j < w; ++j) {
           C yv[TC];
-          ld_cols<C, TC, PS>(yb + (size_t)j * NR + r0, yv);
+          ld_cols<C, TC, PS>(yj, yv);
           C w0, w1;
-          Vec2<C>::ld(Wk + (size_t)j * wp + i0, w0, w1);
+          Vec2<C>::ld(wj, w0, w1);
 #pragma unroll
           for (int c = 0; c < TC; ++c) {
             cfma(acc[0][c], w0, yv[c]);
             cfma(acc[1][c], w1, yv[c]);
           }
+          yj += NR;
+          wj += wp;
         }
       }
 
       // ---- epilogue
 #pragma unroll
       for (int a = 0; a < TR; ++a) {
-        const int i = i0 + a;
-        if (i >= w) continue;
+        if (!row_ok[a]) continue;
         C x[TC];
-        bool have_x = false;
         if (fwd) {
-          if (k <= n - 3) st_cols<C, TC, PS>(zslot + ((long long)k * w + i) * NR + r0, acc[a]);
-          if (k == n - 1) {
+          if (k <= n - 3) st_cols<C, TC, PS>(zrow[a] + (long long)k * zstep + r0, acc[a]);
+          if (k != n - 1) {
 #pragma unroll
-            for (int c = 0; c < TC; ++c) { zkeep[a][c] = carry[a][c]; x[c] = acc[a][c]; }
-            have_x = true;
+            for (int c = 0; c < TC; ++c) carry[a][c] = acc[a][c];
+            continue;
           }
 #pragma unroll
-          for (int c = 0; c < TC; ++c) carry[a][c] = acc[a][c];
+          for (int c = 0; c < TC; ++c) { zkeep[a][c] = carry[a][c]; x[c] = acc[a][c]; }
         } else {
 #pragma unroll
           for (int c = 0; c < TC; ++c) {
@@ -317,30 +358,31 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
             x[c] = z;
             cfms(x[c], c_k, acc[a][c]);
           }
-          have_x = true;
         }
-        if (!have_x) continue;
 #pragma unroll
-        for (int c = 0; c < TC; ++c) {
-          carry[a][c] = x[c];
-          const int r = rhs_of(c);
-          if (r >= nr) continue;
-          const long long gi = ((long long)(lo - 1 + i) * n + k) * ldv + rhs0 + r;
-          if (mode == MODE_EMBED) {
-            if (i >= xoff && i < xoff + xw) reinterpret_cast<C*>(P.outM)[gi] = x[c];
-            if (i == xoff + xw - 1) reinterpret_cast<C*>(P.accR)[((long long)p * n + k) * lda + rhs0 + r] = x[c];
-            if (i == xoff) reinterpret_cast<C*>(P.accL)[((long long)p * n + k) * lda + rhs0 + r] = x[c];
-          } else if (mode == MODE_FILL_R) {
-            if (i >= xoff && i < xoff + xw) reinterpret_cast<C*>(P.outR)[gi] = x[c];
-          } else if (mode == MODE_FILL_L) {
-            if (i >= xoff && i < xoff + xw) reinterpret_cast<C*>(P.outL)[gi] = x[c];
-          } else if (mode == MODE_TMAP_R) {
-            if (i == xoff + xw - 1) reinterpret_cast<C*>(P.tmap)[S.toff + (long long)k * ldT + rhs0 + r] = x[c];
-          } else if (mode == MODE_TMAP_L) {
-            if (i == xoff) reinterpret_cast<C*>(P.tmap)[S.toff + (long long)k * ldT + rhs0 + r] = x[c];
-          } else {
-            reinterpret_cast<double2*>(P.outSub)[((long long)i * n + k) * ldv + rhs0 + r] =
-                make_double2((double)x[c].x, (double)x[c].y);
+        for (int c = 0; c < TC; ++c) carry[a][c] = x[c];
+        if (out_row[a]) {
+          C* o = out_base[a] + (long long)k * out_step;
+#pragma unroll
+          for (int c = 0; c < TC; ++c)
+            if (rhs_of(c) < nr) {
+              if (CLS == CLS_SUB)
+                reinterpret_cast<double2*>(P.outSub)[((long long)(i0 + a) * n + k) * ldv + rhs0 + rhs_of(c)] =
+                    make_double2((double)x[c].x, (double)x[c].y);
+              else
+                o[rhs_of(c)] = x[c];
+            }
+        }
+        if (CLS == CLS_EMBED) {
+          if (trR[a]) {
+#pragma unroll
+            for (int c = 0; c < TC; ++c)
+              if (rhs_of(c) < nr) accRp[(long long)k * lda + rhs_of(c)] = x[c];
+          }
+          if (trL[a]) {
+#pragma unroll
+            for (int c = 0; c < TC; ++c)
+              if (rhs_of(c) < nr) accLp[(long long)k * lda + rhs_of(c)] = x[c];
           }
         }
       }
@@ -355,7 +397,7 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
 
 // MAXT / MINB: largest CTA the instance is compiled for and the number of
 // such CTAs per SM its register budget is sized for.
-template <typename R, int TC, int LC, int NCW, int MAXT = 512, int MINB = 1>
+template <typename R, int TC, int LC, int NCW, int CLS, int MAXT = 512, int MINB = 1>
 cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
   using T = Tiling<R, TC, LC, NCW>;
   const int nrw = (wcap + T::WR - 1) / T::WR;
@@ -369,55 +411,16 @@ cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
   G.wstage = wcap * wpc + T::WR * nrw + 2;
   if (sizeof(R) == 4) G.wstage = (G.wstage + 1) & ~1;
   const size_t smem = T::total(G, nt);
-  auto kern = btsolve_kernel<R, TC, LC, NCW, MAXT, MINB>;
+  auto kern = btsolve_kernel<R, TC, LC, NCW, MAXT, MINB, CLS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int grid = P.njobs < H.zslots ? P.njobs : H.zslots;
+  int grid = P.njobs < P.zslots ? P.njobs : P.zslots;
   if (grid <= 0) return cudaSuccess;
   kern<<<grid, nt, smem, s>>>(P, G);
   H.launches += 1;
   return cudaGetLastError();
 }
 
-}  // namespace
-
-// Right-hand sides one CTA handles, for jobs with at most `nrhs` right-hand
-// sides (`tmap`: the transfer-map construction, whose n columns are the
-// right-hand sides).  Returns 0 if no instance fits (w > 64).
-int btsolve_rhs_capacity(int nrhs, int wmax, int prec, bool tmap) {
-  if (wmax > 64) return 0;
-  if (tmap) return prec == ASP_PREC_C64 ? 64 : 16;
-  if (nrhs >= 32) return prec == ASP_PREC_C64 ? 32 : 16;
-  if (nrhs >= 16) return 16;
-  if (nrhs >= 8) return 8;
-  if (nrhs >= 4) return 4;
-  if (nrhs >= 2) return 2;
-  return 1;
-}
-
-cudaError_t launch_btsolve(Handle& H, const SolveParams& P, int cap, int wmax, cudaStream_t s) {
-  if (H.prec == ASP_PREC_C64) {
-    switch (cap) {
-      case 64:
-        if (wmax <= 24) return run<float, 4, 8, 2, 192, 3>(H, P, wmax, s);
-        return run<float, 4, 8, 2>(H, P, wmax, s);
-      case 32: return run<float, 2, 8, 2, 384, 2>(H, P, wmax, s);
-      case 16: return run<float, 2, 8, 1>(H, P, wmax, s);
-      case 8: return run<float, 2, 4, 1>(H, P, wmax, s);
-      case 4: return run<float, 2, 2, 1>(H, P, wmax, s);
-      case 2: return run<float, 2, 1, 1>(H, P, wmax, s);
-      case 1: return run<float, 1, 1, 1>(H, P, wmax, s);
-    }
-  } else {
-    switch (cap) {
-      case 16: return run<double, 2, 8, 1>(H, P, wmax, s);
-      case 8: return run<double, 2, 4, 1>(H, P, wmax, s);
-      case 4: return run<double, 2, 2, 1>(H, P, wmax, s);
-      case 2: return run<double, 2, 1, 1>(H, P, wmax, s);
-      case 1: return run<double, 1, 1, 1>(H, P, wmax, s);
-    }
-  }
-  return cudaErrorInvalidValue;
-}
+}  // namespace bts
 
 }  // namespace asp

@@ -1,0 +1,51 @@
+// btsolve_apply.cu -- instances of the batched layer solve used by every
+// preconditioner apply: the M-solves (CLS_EMBED) and the sweep fills (CLS_FILL).
+#include "btsolve.cuh"
+
+namespace asp {
+
+cudaError_t launch_btsolve_apply(Handle& H, const SolveParams& P, int cls, int cap, int wmax, cudaStream_t s) {
+  using namespace bts;
+  if (H.prec == ASP_PREC_C64) {
+    if (cls == CLS_EMBED) {
+      switch (cap) {
+        case 32: return run<float, 2, 8, 2, CLS_EMBED, 384, 2>(H, P, wmax, s);
+        case 16: return run<float, 2, 8, 1, CLS_EMBED>(H, P, wmax, s);
+        case 8: return run<float, 2, 4, 1, CLS_EMBED>(H, P, wmax, s);
+        case 4: return run<float, 2, 2, 1, CLS_EMBED>(H, P, wmax, s);
+        case 2: return run<float, 2, 1, 1, CLS_EMBED>(H, P, wmax, s);
+        case 1: return run<float, 1, 1, 1, CLS_EMBED>(H, P, wmax, s);
+      }
+    } else {
+      switch (cap) {
+        case 32: return run<float, 2, 8, 2, CLS_FILL, 384, 2>(H, P, wmax, s);
+        case 16: return run<float, 2, 8, 1, CLS_FILL>(H, P, wmax, s);
+        case 8: return run<float, 2, 4, 1, CLS_FILL>(H, P, wmax, s);
+        case 4: return run<float, 2, 2, 1, CLS_FILL>(H, P, wmax, s);
+        case 2: return run<float, 2, 1, 1, CLS_FILL>(H, P, wmax, s);
+        case 1: return run<float, 1, 1, 1, CLS_FILL>(H, P, wmax, s);
+      }
+    }
+  } else {
+    if (cls == CLS_EMBED) {
+      switch (cap) {
+        case 16: return run<double, 2, 8, 1, CLS_EMBED>(H, P, wmax, s);
+        case 8: return run<double, 2, 4, 1, CLS_EMBED>(H, P, wmax, s);
+        case 4: return run<double, 2, 2, 1, CLS_EMBED>(H, P, wmax, s);
+        case 2: return run<double, 2, 1, 1, CLS_EMBED>(H, P, wmax, s);
+        case 1: return run<double, 1, 1, 1, CLS_EMBED>(H, P, wmax, s);
+      }
+    } else {
+      switch (cap) {
+        case 16: return run<double, 2, 8, 1, CLS_FILL>(H, P, wmax, s);
+        case 8: return run<double, 2, 4, 1, CLS_FILL>(H, P, wmax, s);
+        case 4: return run<double, 2, 2, 1, CLS_FILL>(H, P, wmax, s);
+        case 2: return run<double, 2, 1, 1, CLS_FILL>(H, P, wmax, s);
+        case 1: return run<double, 1, 1, 1, CLS_FILL>(H, P, wmax, s);
+      }
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace asp

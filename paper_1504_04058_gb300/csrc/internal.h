@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -95,6 +96,7 @@ struct SolveParams {
   void* outSub;     // MODE_SUB output (complex128, [w][n][ldv])
   void* zscr;       // forward-pass scratch, one slot per resident CTA
   long long zslot;  // elements per slot
+  int zslots;       // number of slots (upper bound on the grid)
   int* err;
 };
 
@@ -117,13 +119,18 @@ enum Phase : int {
 };
 
 // Records CUDA events around launches when phase timing is enabled.
-void phase_begin(Handle& H, int phase, cudaStream_t s);
-void phase_end(Handle& H, cudaStream_t s);
+struct PhaseTok {
+  int phase = -1;
+  cudaEvent_t a = nullptr;
+};
+PhaseTok phase_begin(Handle& H, int phase, cudaStream_t s);
+void phase_end(Handle& H, PhaseTok t, cudaStream_t s);
 
 // ---- launchers (one translation unit each) ----
 cudaError_t launch_matvec(const Handle& H, const double2* x, double2* y, int nrhs, cudaStream_t s);
-cudaError_t launch_factor(Handle& H, cudaStream_t s);
-cudaError_t launch_btsolve(Handle& H, const SolveParams& P, int rhs_per_job, int wmax, cudaStream_t s);
+cudaError_t launch_factor(Handle& H, int first, int count, cudaStream_t s);
+cudaError_t launch_btsolve_apply(Handle& H, const SolveParams& P, int cls, int cap, int wmax, cudaStream_t s);
+cudaError_t launch_btsolve_aux(Handle& H, const SolveParams& P, int cls, int cap, int wmax, cudaStream_t s);
 int btsolve_rhs_capacity(int nrhs, int wmax, int prec, bool tmap);
 cudaError_t launch_chain(Handle& H, const ChainParams& P, cudaStream_t s);
 cudaError_t launch_to_prec(const double2* in, void* out, long long count, int prec, cudaStream_t s);
@@ -205,8 +212,11 @@ struct Handle {
   struct Rec { int phase; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> evpool;
-  int open_phase = -1;
-  cudaEvent_t open_ev = nullptr;
+  std::mutex rec_mu;
+
+  // second stream for work that overlaps the caller's stream (factor time)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 void set_detail(const std::string& s);

@@ -70,45 +70,24 @@ __global__ void gs_dot_kernel(VecList V, int J, int want_norm, const double2* __
   __shared__ double2 red[kVecThreads];
   const int bt = blockDim.x;
   const int t = threadIdx.x;
-  // two independent accumulator sets (elements e and e + stride) keep two
-  // FP64 dependency chains in flight per thread
-  double2 acc[2][kDotChunk + 1];
+  double2 acc[kDotChunk + 1];
 #pragma unroll
-  for (int u = 0; u < 2; ++u)
-#pragma unroll
-    for (int j = 0; j <= kDotChunk; ++j) acc[u][j] = make_double2(0, 0);
-  const long long stride = (long long)gridDim.x * bt;
-  long long e = (long long)blockIdx.x * bt + t;
-  for (; e + stride < count; e += 2 * stride) {
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const long long eu = e + u * stride;
-      const double2 we = w[eu];
-#pragma unroll
-      for (int j = 0; j < kDotChunk; ++j)
-        if (j < J) {
-          const double2 v = V.v[j][eu];
-          acc[u][j].x = fma(v.x, we.x, fma(v.y, we.y, acc[u][j].x));
-          acc[u][j].y = fma(v.x, we.y, fma(-v.y, we.x, acc[u][j].y));
-        }
-      if (want_norm) acc[u][kDotChunk].x = fma(we.x, we.x, fma(we.y, we.y, acc[u][kDotChunk].x));
-    }
-  }
-  if (e < count) {
+  for (int j = 0; j <= kDotChunk; ++j) acc[j] = make_double2(0, 0);
+  for (long long e = (long long)blockIdx.x * bt + t; e < count; e += (long long)gridDim.x * bt) {
     const double2 we = w[e];
 #pragma unroll
     for (int j = 0; j < kDotChunk; ++j)
       if (j < J) {
         const double2 v = V.v[j][e];
-        acc[0][j].x = fma(v.x, we.x, fma(v.y, we.y, acc[0][j].x));
-        acc[0][j].y = fma(v.x, we.y, fma(-v.y, we.x, acc[0][j].y));
+        acc[j].x = fma(v.x, we.x, fma(v.y, we.y, acc[j].x));
+        acc[j].y = fma(v.x, we.y, fma(-v.y, we.x, acc[j].y));
       }
-    if (want_norm) acc[0][kDotChunk].x = fma(we.x, we.x, fma(we.y, we.y, acc[0][kDotChunk].x));
+    if (want_norm) acc[kDotChunk].x = fma(we.x, we.x, fma(we.y, we.y, acc[kDotChunk].x));
   }
 #pragma unroll
   for (int j = 0; j <= kDotChunk; ++j) {
     if (j < J || (j == kDotChunk && want_norm)) {
-      red[t] = make_double2(acc[0][j].x + acc[1][j].x, acc[0][j].y + acc[1][j].y);
+      red[t] = acc[j];
       __syncthreads();
       if (t < nrhs) {
         double2 s = make_double2(0, 0);
@@ -157,18 +136,11 @@ __global__ void gs_axpy_kernel(VecList V, int J, const double2* __restrict__ coe
     }
   }
   double nacc = 0.0;
-  const long long stride = (long long)gridDim.x * bt;
-  for (long long e = (long long)blockIdx.x * bt + t; e < count; e += stride) {
-    // even and odd terms in separate chains, then w + (even + odd)
-    double2 a0 = make_double2(0, 0), a1 = make_double2(0, 0);
-#pragma unroll
-    for (int j = 0; j < kDotChunk; j += 2) {
-      if (j < J) cfma(a0, c[j], V.v[j][e]);
-      if (j + 1 < J) cfma(a1, c[j + 1], V.v[j + 1][e]);
-    }
+  for (long long e = (long long)blockIdx.x * bt + t; e < count; e += (long long)gridDim.x * bt) {
     double2 acc = w[e];
-    acc.x += a0.x + a1.x;
-    acc.y += a0.y + a1.y;
+#pragma unroll
+    for (int j = 0; j < kDotChunk; ++j)
+      if (j < J) cfma(acc, c[j], V.v[j][e]);
     w[e] = acc;
     if (want_norm) nacc = fma(acc.x, acc.x, fma(acc.y, acc.y, nacc));
   }
@@ -467,7 +439,7 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
     G.K.need = pi;
   }
   G.red_threads = nrhs * std::max(1, kVecThreads / nrhs);
-  G.red_blocks = H.num_sms * 4;
+  G.red_blocks = H.num_sms * 2;
   G.partial = reinterpret_cast<double2*>(H.red);
   const long long count = G.count;
   const int gv = grid_for(count, kVecThreads, H.num_sms);
@@ -503,10 +475,10 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
       rc = apply_precond(H, G.Vv(j), G.Zv(j), nrhs, s);
       if (rc != ASP_OK) return rc;
       double2* w = G.Vv(j + 1);
-      phase_begin(H, PH_MATVEC, s);
+      PhaseTok tmv = phase_begin(H, PH_MATVEC, s);
       CK(launch_matvec(H, G.Zv(j), w, nrhs, s));
-      phase_end(H, s);
-      phase_begin(H, PH_KRYLOV, s);
+      phase_end(H, tmv, s);
+      PhaseTok tkr = phase_begin(H, PH_KRYLOV, s);
       for (int i = 0; i <= j; ++i) vl[i] = G.Vv(i);
       // classical Gram-Schmidt, a second pass only where cancellation demands it
       CK(G.dots(vl.data(), j + 1, w, G.K.h1, G.K.nrm0));
@@ -527,7 +499,7 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
       CK(G.scale(w, G.K.inv, w));
       count_active_kernel<<<1, 32, 0, s>>>(G.K, nrhs);
       H.launches += 1;
-      phase_end(H, s);
+      phase_end(H, tkr, s);
       CK(cudaMemcpyAsync(H.h_flags, G.K.active, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       active = H.h_flags[0];
