@@ -47,12 +47,14 @@ __global__ void matvec_kernel(const double* __restrict__ k2, const double2* __re
   const double2 u = x[e];
   const double2 d1 = cd[i1], d2 = cd[i2];
   const double2 diag = make_double2(d1.x + d2.x + k2[(long long)i2 * n + i1], d1.y + d2.y);
+  // two independent partial sums (x1 and x2 neighbours) shorten the FP64 chain
   double2 acc = dmul(diag, u);
+  double2 acc2 = make_double2(0.0, 0.0);
   if (i1 > 0) cfma(acc, ca[i1], x[e - nr]);
+  if (i2 > 0) cfma(acc2, ca[i2], x[e - rowst]);
   if (i1 < n - 1) cfma(acc, cc[i1], x[e + nr]);
-  if (i2 > 0) cfma(acc, ca[i2], x[e - rowst]);
-  if (i2 < n - 1) cfma(acc, cc[i2], x[e + rowst]);
-  y[e] = acc;
+  if (i2 < n - 1) cfma(acc2, cc[i2], x[e + rowst]);
+  y[e] = make_double2(acc.x + acc2.x, acc.y + acc2.y);
 }
 
 struct VecList {
@@ -65,34 +67,51 @@ struct VecList {
 //
 // partial[b][j][r] = this block's sum of conj(v_j) * w for j < J, and, when
 // want_norm, partial[b][kDotChunk][r] = its sum of |w|^2.
+// EU elements per thread and loop iteration: independent FP64 chains in flight
+// (GB300 issues FP64 at 1/58 of the FP32 rate with a long result latency, so
+// a single dependent chain per thread leaves the FP64 pipe idle).
+template <int EU>
 __global__ void gs_dot_kernel(VecList V, int J, int want_norm, const double2* __restrict__ w, long long count,
                               int nrhs, double2* __restrict__ partial) {
   __shared__ double2 red[kVecThreads];
   const int bt = blockDim.x;
   const int t = threadIdx.x;
-  double2 acc[kDotChunk + 1];
+  constexpr int JM = (EU >= 4) ? 2 : (EU == 2 ? 4 : kDotChunk);  // vectors handled per pass at this unroll
+  double2 acc[EU][JM + 1];
 #pragma unroll
-  for (int j = 0; j <= kDotChunk; ++j) acc[j] = make_double2(0, 0);
-  for (long long e = (long long)blockIdx.x * bt + t; e < count; e += (long long)gridDim.x * bt) {
-    const double2 we = w[e];
+  for (int u = 0; u < EU; ++u)
 #pragma unroll
-    for (int j = 0; j < kDotChunk; ++j)
-      if (j < J) {
-        const double2 v = V.v[j][e];
-        acc[j].x = fma(v.x, we.x, fma(v.y, we.y, acc[j].x));
-        acc[j].y = fma(v.x, we.y, fma(-v.y, we.x, acc[j].y));
+    for (int j = 0; j <= JM; ++j) acc[u][j] = make_double2(0, 0);
+  const long long stride = (long long)gridDim.x * bt;
+  for (long long e0 = (long long)blockIdx.x * bt + t; e0 < count; e0 += EU * stride) {
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      const long long e = e0 + u * stride;
+      if (e < count) {
+        const double2 we = w[e];
+#pragma unroll
+        for (int j = 0; j < JM; ++j)
+          if (j < J) {
+            const double2 v = V.v[j][e];
+            acc[u][j].x = fma(v.x, we.x, fma(v.y, we.y, acc[u][j].x));
+            acc[u][j].y = fma(v.x, we.y, fma(-v.y, we.x, acc[u][j].y));
+          }
+        if (want_norm) acc[u][JM].x = fma(we.x, we.x, fma(we.y, we.y, acc[u][JM].x));
       }
-    if (want_norm) acc[kDotChunk].x = fma(we.x, we.x, fma(we.y, we.y, acc[kDotChunk].x));
+    }
   }
 #pragma unroll
-  for (int j = 0; j <= kDotChunk; ++j) {
-    if (j < J || (j == kDotChunk && want_norm)) {
-      red[t] = acc[j];
+  for (int j = 0; j <= JM; ++j) {
+    if (j < J || (j == JM && want_norm)) {
+      double2 sum = acc[0][j];
+#pragma unroll
+      for (int u = 1; u < EU; ++u) { sum.x += acc[u][j].x; sum.y += acc[u][j].y; }
+      red[t] = sum;
       __syncthreads();
       if (t < nrhs) {
         double2 s = make_double2(0, 0);
         for (int q = t; q < bt; q += nrhs) { s.x += red[q].x; s.y += red[q].y; }
-        partial[((long long)blockIdx.x * (kDotChunk + 1) + j) * nrhs + t] = s;
+        partial[((long long)blockIdx.x * (kDotChunk + 1) + (j == JM ? kDotChunk : j)) * nrhs + t] = s;
       }
       __syncthreads();
     }
@@ -119,9 +138,12 @@ __global__ void dot_finish_kernel(const double2* __restrict__ partial, int nbloc
 
 // w[e] += sgn * sum_j coef[(j0+j)][r] * v_j[e]; with want_norm also the block
 // sums of |w_new|^2 in partial[b][kDotChunk][r].
+// four elements per thread and iteration, and the J terms of each element in
+// two independent partial sums, so several FP64 chains are in flight
 __global__ void gs_axpy_kernel(VecList V, int J, const double2* __restrict__ coef, int j0, double sgn,
                                double2* __restrict__ w, long long count, int nrhs, int want_norm,
                                double2* __restrict__ partial) {
+  constexpr int EU = 4;
   __shared__ double2 red[kVecThreads];
   const int bt = blockDim.x;
   const int t = threadIdx.x;
@@ -135,17 +157,40 @@ __global__ void gs_axpy_kernel(VecList V, int J, const double2* __restrict__ coe
       c[j] = make_double2(sgn * cj.x, sgn * cj.y);
     }
   }
-  double nacc = 0.0;
-  for (long long e = (long long)blockIdx.x * bt + t; e < count; e += (long long)gridDim.x * bt) {
-    double2 acc = w[e];
+  double nacc[EU] = {0.0};
+  const long long stride = (long long)gridDim.x * bt;
+  for (long long e0 = (long long)blockIdx.x * bt + t; e0 < count; e0 += EU * stride) {
+    double2 a0[EU], a1[EU];
 #pragma unroll
-    for (int j = 0; j < kDotChunk; ++j)
-      if (j < J) cfma(acc, c[j], V.v[j][e]);
-    w[e] = acc;
-    if (want_norm) nacc = fma(acc.x, acc.x, fma(acc.y, acc.y, nacc));
+    for (int u = 0; u < EU; ++u) { a0[u] = make_double2(0, 0); a1[u] = make_double2(0, 0); }
+#pragma unroll
+    for (int j = 0; j < kDotChunk; j += 2) {
+#pragma unroll
+      for (int u = 0; u < EU; ++u) {
+        const long long e = e0 + u * stride;
+        if (e < count) {
+          if (j < J) cfma(a0[u], c[j], V.v[j][e]);
+          if (j + 1 < J) cfma(a1[u], c[j + 1], V.v[j + 1][e]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      const long long e = e0 + u * stride;
+      if (e < count) {
+        double2 acc = w[e];
+        acc.x += a0[u].x + a1[u].x;
+        acc.y += a0[u].y + a1[u].y;
+        w[e] = acc;
+        if (want_norm) nacc[u] = fma(acc.x, acc.x, fma(acc.y, acc.y, nacc[u]));
+      }
+    }
   }
   if (want_norm) {
-    red[t] = make_double2(nacc, 0.0);
+    double nsum = 0.0;
+#pragma unroll
+    for (int u = 0; u < EU; ++u) nsum += nacc[u];
+    red[t] = make_double2(nsum, 0.0);
     __syncthreads();
     if (t < nrhs) {
       double2 s = make_double2(0, 0);
@@ -368,16 +413,19 @@ struct Krylov {
   // out[j][r] = conj(V_j)^T w for j < J (chunks of kDotChunk); nrm[r] = ||w||^2
   // when nrm != nullptr (computed with the first chunk, or alone when J == 0).
   cudaError_t dots(const double2* const* vs, int J, const double2* w, double2* out, double2* nrm) {
-    for (int j0 = 0; j0 < J || (J == 0 && j0 == 0); j0 += kDotChunk) {
+    // small J: more elements per thread; chunks of at most JM vectors per pass
+    const int JM = J <= 2 ? 2 : (J <= 4 ? 4 : kDotChunk);
+    for (int j0 = 0; j0 < J || (J == 0 && j0 == 0); j0 += JM) {
       VecList L{};
-      const int Jc = std::min(kDotChunk, J - j0);
+      const int Jc = std::max(0, std::min(JM, J - j0));
       for (int j = 0; j < Jc; ++j) L.v[j] = vs[j0 + j];
-      for (int j = std::max(Jc, 0); j < kDotChunk; ++j) L.v[j] = w;
+      for (int j = Jc; j < kDotChunk; ++j) L.v[j] = w;
       double2* nr = (j0 == 0) ? nrm : nullptr;
-      gs_dot_kernel<<<red_blocks, red_threads, 0, s>>>(L, std::max(Jc, 0), nr ? 1 : 0, w, count, nrhs, partial);
-      const int slots = std::max(Jc, 0) + (nr ? 1 : 0);
-      dot_finish_kernel<<<(slots * nrhs + 127) / 128, 128, 0, s>>>(partial, red_blocks, std::max(Jc, 0), nrhs, j0,
-                                                                    out, nr);
+      if (JM == 2) gs_dot_kernel<4><<<red_blocks, red_threads, 0, s>>>(L, Jc, nr ? 1 : 0, w, count, nrhs, partial);
+      else if (JM == 4) gs_dot_kernel<2><<<red_blocks, red_threads, 0, s>>>(L, Jc, nr ? 1 : 0, w, count, nrhs, partial);
+      else gs_dot_kernel<1><<<red_blocks, red_threads, 0, s>>>(L, Jc, nr ? 1 : 0, w, count, nrhs, partial);
+      const int slots = Jc + (nr ? 1 : 0);
+      dot_finish_kernel<<<(slots * nrhs + 127) / 128, 128, 0, s>>>(partial, red_blocks, Jc, nrhs, j0, out, nr);
       H.launches += 2;
       if (J == 0) break;
     }

@@ -103,10 +103,12 @@ __global__ void na_residual_kernel(const double* __restrict__ c, double omega, i
     const double k2 = omega * omega / (c[pt] * c[pt]);
     const double2 diag = make_double2(d1.x + d2.x + k2, d1.y + d2.y);
     double2 acc = cmul(diag, x);
+    double2 acc2 = make_double2(0.0, 0.0);
     if (i1 > 0) cfma(acc, S->ca[i1], u[e - nrhs]);
+    if (i2 > 0) cfma(acc2, S->ca[i2], u[e - rowst]);
     if (i1 < n - 1) cfma(acc, S->cc[i1], u[e + nrhs]);
-    if (i2 > 0) cfma(acc, S->ca[i2], u[e - rowst]);
-    if (i2 < n - 1) cfma(acc, S->cc[i2], u[e + rowst]);
+    if (i2 < n - 1) cfma(acc2, S->cc[i2], u[e + rowst]);
+    acc = make_double2(acc.x + acc2.x, acc.y + acc2.y);
     const double2 fe = f[e];
     const double2 r = make_double2(fe.x - acc.x, fe.y - acc.y);
     rr = fma(r.x, r.x, fma(r.y, r.y, rr));
