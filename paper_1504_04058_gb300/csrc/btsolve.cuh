@@ -12,10 +12,10 @@
 // Each step multiplies the dense w x w block W_k by a w x NR panel of
 // right-hand sides.  Work split: every thread owns a 2-row x TC-column tile of
 // the panel for the whole job, so the recurrences (z_{k-1} -> y_k,
-// x_{k+1} -> x_k) stay in its registers; a warp covers (32/LC)*2 rows x LC*TC
+// x_{k+1} -> x_k) stay in its registers; a warp covers (32/LC)*TR rows x LC*TC
 // right-hand sides, the CTA stacks warps over rows (and NCW column blocks).
-// The inner product loads two rows of W_k (one 16-byte shared load for
-// complex64) and TC panel entries per column j and issues 8*TC FMAs.  A
+// The inner product loads TR rows of W_k (16-byte shared loads of row pairs)
+// and TC panel entries per column j and issues 4*TR*TC FMAs.  A
 // thread's TC columns come in pairs 2*LC apart so that lanes sharing a row
 // touch one contiguous span (no shared-memory bank conflicts).
 //
@@ -59,10 +59,10 @@ struct Geometry {
 
 __host__ __device__ inline size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
 
-template <typename R, int TC, int LC, int NCW>
+template <typename R, int TR_, int TC, int LC, int NCW>
 struct Tiling {
   using C = Cx<R>;
-  static constexpr int TR = 2;                 // rows per thread
+  static constexpr int TR = TR_;               // rows per thread (2 or 4)
   static constexpr int WR = (32 / LC) * TR;    // rows per warp
   static constexpr int WC = LC * TC;           // right-hand sides per warp
   static constexpr int NR = WC * NCW;          // right-hand sides per CTA
@@ -109,10 +109,10 @@ template <typename C, int TC, int PS> __device__ __forceinline__ void st_cols(C*
   }
 }
 
-template <typename R, int TC, int LC, int NCW, int MAXT, int MINB, int CLS>
+template <typename R, int TRT, int TC, int LC, int NCW, int MAXT, int MINB, int CLS>
 __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geometry G) {
   using C = Cx<R>;
-  using T = Tiling<R, TC, LC, NCW>;
+  using T = Tiling<R, TRT, TC, LC, NCW>;
   constexpr int TR = T::TR, WR = T::WR, WC = T::WC, NR = T::NR, E = T::E;
   constexpr int CB = (int)sizeof(C);
   constexpr int PS = 2 * LC;  // column distance between a thread's pairs
@@ -324,13 +324,13 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
         for (int j = 0; j < w; ++j) {
           C yv[TC];
           ld_cols<C, TC, PS>(yj, yv);
-          C w0, w1;
-          Vec2<C>::ld(wj, w0, w1);
+          C wv[TR];
 #pragma unroll
-          for (int c = 0; c < TC; ++c) {
-            cfma(acc[0][c], w0, yv[c]);
-            cfma(acc[1][c], w1, yv[c]);
-          }
+          for (int a = 0; a < TR; a += 2) Vec2<C>::ld(wj + a, wv[a], wv[a + 1]);
+#pragma unroll
+          for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int c = 0; c < TC; ++c) cfma(acc[a][c], wv[a], yv[c]);
           yj += NR;
           wj += wp;
         }
@@ -395,11 +395,11 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
     for (int s = 0; s < kStages; ++s) mbar_inval(&bar[s]);
 }
 
-// MAXT / MINB: largest CTA the instance is compiled for and the number of
-// such CTAs per SM its register budget is sized for.
-template <typename R, int TC, int LC, int NCW, int CLS, int MAXT = 512, int MINB = 1>
+// TRT: rows per thread.  MAXT / MINB: largest CTA the instance is compiled for
+// and the number of such CTAs per SM its register budget is sized for.
+template <typename R, int TRT, int TC, int LC, int NCW, int CLS, int MAXT = 512, int MINB = 1>
 cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
-  using T = Tiling<R, TC, LC, NCW>;
+  using T = Tiling<R, TRT, TC, LC, NCW>;
   const int nrw = (wcap + T::WR - 1) / T::WR;
   const int nt = 32 * nrw * NCW;
   if (nt > MAXT) return cudaErrorInvalidValue;
@@ -411,7 +411,7 @@ cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
   G.wstage = wcap * wpc + T::WR * nrw + 2;
   if (sizeof(R) == 4) G.wstage = (G.wstage + 1) & ~1;
   const size_t smem = T::total(G, nt);
-  auto kern = btsolve_kernel<R, TC, LC, NCW, MAXT, MINB, CLS>;
+  auto kern = btsolve_kernel<R, TRT, TC, LC, NCW, MAXT, MINB, CLS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = P.njobs < P.zslots ? P.njobs : P.zslots;

@@ -9,18 +9,18 @@ cudaError_t launch_btsolve_aux(Handle& H, const SolveParams& P, int cls, int cap
   using namespace bts;
   if (H.prec == ASP_PREC_C64) {
     if (cls == CLS_TMAP) {
-      if (cap == 64 && wmax <= 24) return run<float, 4, 8, 2, CLS_TMAP, 192, 3>(H, P, wmax, s);
-      if (cap == 64) return run<float, 4, 8, 2, CLS_TMAP>(H, P, wmax, s);
+      if (cap == 64 && wmax <= 24) return run<float, 2, 4, 8, 2, CLS_TMAP, 192, 3>(H, P, wmax, s);
+      if (cap == 64) return run<float, 2, 4, 8, 2, CLS_TMAP>(H, P, wmax, s);
     } else {
-      if (cap == 4) return run<float, 2, 2, 1, CLS_SUB>(H, P, wmax, s);
-      if (cap == 1) return run<float, 1, 1, 1, CLS_SUB>(H, P, wmax, s);
+      if (cap == 4) return run<float, 2, 2, 2, 1, CLS_SUB>(H, P, wmax, s);
+      if (cap == 1) return run<float, 2, 1, 1, 1, CLS_SUB>(H, P, wmax, s);
     }
   } else {
     if (cls == CLS_TMAP) {
-      if (cap == 16) return run<double, 2, 8, 1, CLS_TMAP>(H, P, wmax, s);
+      if (cap == 16) return run<double, 2, 2, 8, 1, CLS_TMAP>(H, P, wmax, s);
     } else {
-      if (cap == 4) return run<double, 2, 2, 1, CLS_SUB>(H, P, wmax, s);
-      if (cap == 1) return run<double, 1, 1, 1, CLS_SUB>(H, P, wmax, s);
+      if (cap == 4) return run<double, 2, 2, 2, 1, CLS_SUB>(H, P, wmax, s);
+      if (cap == 1) return run<double, 2, 1, 1, 1, CLS_SUB>(H, P, wmax, s);
     }
   }
   return cudaErrorInvalidValue;
