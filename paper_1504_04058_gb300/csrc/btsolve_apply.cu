@@ -18,7 +18,7 @@ cudaError_t launch_btsolve_apply(Handle& H, const SolveParams& P, int cls, int c
       }
     } else {
       switch (cap) {
-        case 32: return run<float, 4, 2, 8, 2, CLS_FILL, 256, 2>(H, P, wmax, s);
+        case 32: return run<float, 2, 2, 8, 2, CLS_FILL, 384, 2>(H, P, wmax, s);
         case 16: return run<float, 2, 2, 8, 1, CLS_FILL>(H, P, wmax, s);
         case 8: return run<float, 2, 2, 4, 1, CLS_FILL>(H, P, wmax, s);
         case 4: return run<float, 2, 2, 2, 1, CLS_FILL>(H, P, wmax, s);

@@ -13,7 +13,7 @@
 // accR[p] holds (u~_{p,p})^R on entry and (u~_{p,1:p})^R on exit; accL likewise.
 // One cooperative launch runs both sweeps: the first half of the CTAs the R
 // chain, the second half the L chain, each with its own grid barrier between
-// layers.  Per layer a CTA owns RC <= 16 rows of the product; its 8 warps split
+// layers.  Per layer a CTA owns RC <= 16 rows of the product; its 16 warps split
 // the k-range (each chunk of KC columns is staged in shared memory by cp.async,
 // double-buffered), each lane holds an 8-row x 2-right-hand-side tile, and the
 // warps' partial sums are reduced through shared memory.  Barrier waits are
@@ -25,14 +25,14 @@ namespace asp {
 
 namespace {
 
-constexpr int kChainThreads = 256;
+constexpr int kChainThreads = 512;
 constexpr int kWarps = kChainThreads / 32;
 constexpr int kMaxRows = 16;  // rows of the product per CTA
 constexpr int kRhs = 32;      // right-hand sides per launch (two per lane, 16 lanes)
 
 template <typename R> struct ChainKC;
 template <> struct ChainKC<float> { static constexpr int v = 256; };
-template <> struct ChainKC<double> { static constexpr int v = 64; };
+template <> struct ChainKC<double> { static constexpr int v = 128; };
 
 template <typename R> __host__ __device__ constexpr size_t chain_smem() {
   // s_T[2][KC][kMaxRows] + s_src[2][KC][kRhs]; the cross-warp reduction buffer
