@@ -261,9 +261,19 @@ struct JobCache {
   }
 };
 
+// Job lists per handle.  Handles may be used from different host threads at
+// the same time (one thread per handle), so the map itself is guarded.
+std::mutex& caches_mu() {
+  static std::mutex mu;
+  return mu;
+}
 std::map<const Handle*, JobCache>& caches() {
   static std::map<const Handle*, JobCache> c;
   return c;
+}
+JobCache& cache_of(const Handle* h) {
+  std::lock_guard<std::mutex> lock(caches_mu());
+  return caches()[h];
 }
 
 int upload_jobs(Handle& H, const std::vector<Job>& jobs, int cap, int wmax, JobList* out) {
@@ -277,13 +287,13 @@ int upload_jobs(Handle& H, const std::vector<Job>& jobs, int cap, int wmax, JobL
     cudaFree(d);
     return fail(ASP_ERR_CUDA, "job list upload");
   }
-  caches()[&H].owned.push_back(d);
+  cache_of(&H).owned.push_back(d);
   out->d = (Job*)d;
   return ASP_OK;
 }
 
 int get_embed_jobs(Handle& H, int nrhs, JobList** out) {
-  JobCache& c = caches()[&H];
+  JobCache& c = cache_of(&H);
   auto it = c.embed.find(nrhs);
   if (it == c.embed.end()) {
     int wm = 0;
@@ -302,7 +312,7 @@ int get_embed_jobs(Handle& H, int nrhs, JobList** out) {
 }
 
 int get_fill_jobs(Handle& H, int nrhs, JobList** out) {
-  JobCache& c = caches()[&H];
+  JobCache& c = cache_of(&H);
   auto it = c.fill.find(nrhs);
   if (it == c.fill.end()) {
     const int wm = std::max(1, H.wmaxRL);
@@ -500,7 +510,10 @@ void asp_destroy(asp_handle* hd) {
   Handle& H = hd->h;
   for (auto& r : H.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : H.evpool) cudaEventDestroy(e);
-  caches().erase(&H);
+  {
+    std::lock_guard<std::mutex> lock(caches_mu());
+    caches().erase(&H);
+  }
   void* ptrs[] = {H.k2, H.ca, H.cc, H.cd, H.d_subs, H.d_coef, H.W, H.tmap, H.d_toffR, H.d_toffL, H.r_lo,
                   H.uM, H.uR, H.uL, H.accR, H.accL, H.zscr, H.bar, H.V, H.Z, H.wv, H.red, H.hess, H.kstate,
                   H.kflags, H.err};
@@ -768,7 +781,7 @@ int asp_factor(asp_handle* hd, void* stream) {
   // transfer maps: columns of T_p^R and T_p^L in chunks of right-hand sides
   if (H.m >= 3) {
     const int cap = btsolve_rhs_capacity(H.n, H.wmaxRL, H.prec, true);
-    JobCache& jc = caches()[&H];
+    JobCache& jc = cache_of(&H);
     if (!jc.have_tmap) {
       std::vector<Job> jobs;
       for (int r0 = 0; r0 < H.n; r0 += cap)
@@ -843,7 +856,7 @@ int asp_subproblem_solve(asp_handle* hd, int kind, int p, const void* g, void* v
     in = H.r_lo;
   }
   const int cap = nrhs >= 4 ? 4 : 1;
-  JobCache& jc = caches()[&H];
+  JobCache& jc = cache_of(&H);
   const long long key = (long long)idx * 1024 + nrhs;
   auto it = jc.sub.find(key);
   if (it == jc.sub.end()) {

@@ -1,0 +1,71 @@
+"""The serving loop on the GPU: a request's solution does not depend on which
+requests it was batched with or which other solves ran beside it on another
+stream, factors are cached and evicted within the memory budget, and every
+solution meets the tolerance by the oracle's own residual."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import operator
+
+pytestmark = pytest.mark.gpu
+
+N, OMEGA, GAMMA, B = 47, 5 * math.pi, 5, 4
+KEYS = 3
+
+
+def requests(serving):
+    out = []
+    rid = 0
+    for rnd in range(3):
+        for v in range(KEYS):
+            P = W.small_problem(2, N, OMEGA, GAMMA, B, "layered", nrhs=1 + (rid % 2), seed=100 + rid)
+            c = W.layered_velocity(N, 40 + v, dim=2)
+            out.append(serving.Request(("layered", v), c, OMEGA, GAMMA, B, P.f, tol=1e-6, precision="c128",
+                                       rid=rid))
+            rid += 1
+    return out
+
+
+def run(serving, reqs, **kw):
+    srv = serving.Server(start=False, **kw)
+    futs = [srv.submit(r) for r in reqs]
+    srv.start()
+    res = [f.result(timeout=300) for f in futs]
+    stats, used, budget = dict(srv.stats), srv.used_bytes, srv.memory_budget
+    srv.close()
+    return res, stats, used, budget
+
+
+def test_batched_concurrent_solutions_match_alone():
+    from paper_1504_04058_gb300 import asp_footprint_bytes, serving
+    reqs = requests(serving)
+    alone, st_a, _, _ = run(serving, reqs, memory_budget=1 << 34, workers=1, max_rhs=8, batching=False)
+    assert st_a["solves"] == len(reqs) and st_a["factorizations"] == KEYS
+    assert all(r.batched_with == rq.nrhs for r, rq in zip(alone, reqs))
+
+    probe = serving.Server(1 << 34, workers=1, max_rhs=8, start=False)
+    fp = asp_footprint_bytes(probe._params(reqs[0]))
+    probe.close()
+    mixed, st_m, used, budget = run(serving, reqs, memory_budget=int(2.5 * fp), workers=2, max_rhs=8)
+    # one batch per key, two keys resident at a time: the third evicts one
+    assert st_m["solves"] == KEYS and st_m["factorizations"] == KEYS
+    assert st_m["evictions"] >= 1 and used <= budget
+    assert all(r.batched_with == sum(q.nrhs for q in reqs if q.key() == rq.key())
+               for r, rq in zip(mixed, reqs))
+
+    for rq, a, m in zip(reqs, alone, mixed):
+        assert a.rid == m.rid == rq.rid
+        assert a.iterations == m.iterations, (rq.rid, a.iterations, m.iterations)
+        err = np.linalg.norm(m.u - a.u) / np.linalg.norm(a.u)
+        assert err <= 1e-9, (rq.rid, err)
+        r = rq.f - operator.apply_A(2, N, OMEGA, rq.c, GAMMA, 20.0, m.u)
+        for k in range(rq.nrhs):
+            rel = np.linalg.norm(r[..., k]) / np.linalg.norm(rq.f[..., k])
+            assert rel <= rq.tol, (rq.rid, k, rel)
+            assert m.rel_res_true[k] <= rq.tol
+
+    lat = serving.percentiles([m.latency_s for m in mixed])
+    assert 0 < lat["p50"] <= lat["p99"] < 300
