@@ -35,12 +35,14 @@ def _stream_ptr(stream=None) -> int:
     return int(s.cuda_stream)
 
 
-def _dev_vec(t, n: int, name: str):
+def _dev_vec(t, n: int, name: str, dim: int = 2):
+    """Checks a grid-function batch: contiguous complex128 CUDA tensor of shape
+    (n,)*dim + (nrhs,), sweep axis first, x1 next to the right-hand sides."""
     torch = _torch()
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128):
         raise TypeError(f"{name} must be a complex128 CUDA tensor")
-    if t.dim() != 3 or t.shape[0] != n or t.shape[1] != n or not t.is_contiguous():
-        raise ValueError(f"{name} must be contiguous with shape (n, n, nrhs) = ({n}, {n}, nrhs)")
+    if t.dim() != dim + 1 or any(int(x) != n for x in t.shape[:dim]) or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with shape {(n,) * dim + ('nrhs',)}")
     return t
 
 
@@ -61,6 +63,7 @@ class AspHandle:
         self._ptr = ctypes.c_void_p(ptr)
         self.params = params
         self.n = params.n
+        self.dim = params.dim
 
     # -------------------------------------------------------------- info
     @property
@@ -99,37 +102,39 @@ class AspHandle:
 
     def apply_preconditioner(self, r, z=None, stream=None):
         torch = _torch()
-        _dev_vec(r, self.n, "r")
+        _dev_vec(r, self.n, "r", self.dim)
         if z is None:
             z = torch.empty_like(r)
-        _dev_vec(z, self.n, "z")
+        _dev_vec(z, self.n, "z", self.dim)
         _lib.check(_lib.load().asp_apply_preconditioner(
-            self._ptr, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()), r.shape[2],
+            self._ptr, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()), r.shape[-1],
             ctypes.c_void_p(_stream_ptr(stream))), "asp_apply_preconditioner")
         return z
 
     def matvec(self, x, y=None, stream=None):
         torch = _torch()
-        _dev_vec(x, self.n, "x")
+        _dev_vec(x, self.n, "x", self.dim)
         if y is None:
             y = torch.empty_like(x)
-        _dev_vec(y, self.n, "y")
+        _dev_vec(y, self.n, "y", self.dim)
         _lib.check(_lib.load().asp_matvec(self._ptr, ctypes.c_void_p(x.data_ptr()),
-                                          ctypes.c_void_p(y.data_ptr()), x.shape[2],
+                                          ctypes.c_void_p(y.data_ptr()), x.shape[-1],
                                           ctypes.c_void_p(_stream_ptr(stream))), "asp_matvec")
         return y
 
     def subproblem_solve(self, kind: int, p: int, g, v=None, stream=None):
-        """v = H^-1 g for one subproblem; g, v complex128 of shape (w, n, nrhs)."""
+        """v = H^-1 g for one subproblem; g, v complex128 of shape (w, n, nrhs)
+        in 2D and (w, n, n, nrhs) in 3D (sweep axis first)."""
         torch = _torch()
         w = self.subproblem_width(kind, p)
-        if not (g.is_cuda and g.dtype == torch.complex128 and tuple(g.shape[:2]) == (w, self.n)
-                and g.is_contiguous()):
-            raise ValueError(f"g must be a contiguous complex128 CUDA tensor of shape ({w}, {self.n}, nrhs)")
+        want = (w,) + (self.n,) * (self.dim - 1)
+        if not (g.is_cuda and g.dtype == torch.complex128 and tuple(g.shape[:-1]) == want
+                and g.dim() == self.dim + 1 and g.is_contiguous()):
+            raise ValueError(f"g must be a contiguous complex128 CUDA tensor of shape {want + ('nrhs',)}")
         if v is None:
             v = torch.empty_like(g)
         _lib.check(_lib.load().asp_subproblem_solve(
-            self._ptr, kind, p, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(v.data_ptr()), g.shape[2],
+            self._ptr, kind, p, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(v.data_ptr()), g.shape[-1],
             ctypes.c_void_p(_stream_ptr(stream))), "asp_subproblem_solve")
         return v
 
@@ -137,11 +142,11 @@ class AspHandle:
                     stream=None, raise_on_nonconvergence: bool = True):
         """FGMRES; returns (u, info) with info a list of dicts per right-hand side."""
         torch = _torch()
-        _dev_vec(f, self.n, "f")
+        _dev_vec(f, self.n, "f", self.dim)
         if u is None:
             u = torch.empty_like(f)
-        _dev_vec(u, self.n, "u")
-        nrhs = f.shape[2]
+        _dev_vec(u, self.n, "u", self.dim)
+        nrhs = f.shape[-1]
         info = (asp_solve_info * nrhs)()
         rs = self.params.restart if restart is None else restart
         code = _lib.load().asp_gmres_solve(self._ptr, ctypes.c_void_p(f.data_ptr()),

@@ -104,6 +104,8 @@ double2 hadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); 
 struct Sizes {
   int m = 0, wmax = 0, wmaxRL = 0, nsub = 0;
   size_t W_elems = 0, tmap_elems = 0, coef = 0;
+  size_t A_elems = 0, piv_elems = 0, z3_elems = 0;  // 3D
+  int nbmaxM = 0, nbmaxRL = 0;                       // 3D
   size_t esz = 0;
   long long N = 0;
   size_t zslot = 0;
@@ -113,8 +115,9 @@ struct Sizes {
 
 bool valid(const asp_params* p, std::string* why) {
   if (!p) { *why = "null params"; return false; }
-  if (p->dim != 2) { *why = p->dim == 3 ? "3D is not implemented in this build" : "dim must be 2"; return false; }
-  if (p->n < 3 || p->n > 16383) { *why = "n out of range [3, 16383]"; return false; }
+  if (p->dim != 2 && p->dim != 3) { *why = "dim must be 2 or 3"; return false; }
+  if (p->dim == 2 && (p->n < 3 || p->n > 16383)) { *why = "n out of range [3, 16383]"; return false; }
+  if (p->dim == 3 && (p->n < 3 || p->n > 1023)) { *why = "n out of range [3, 1023] in 3D"; return false; }
   if (!(p->omega > 0) || !isfinite(p->omega)) { *why = "omega must be positive and finite"; return false; }
   if (p->pml < 2) { *why = "pml (gamma) must be >= 2"; return false; }
   if (p->pml_aux < 0) { *why = "pml_aux must be >= 0"; return false; }
@@ -152,9 +155,71 @@ Part partition(int n, int gamma, int ga, int b) {
   return P;
 }
 
+// Largest 3D block size (n * padded width) the slab kernels take.
+constexpr int kMaxNb3 = 3072;
+
+// Valid problems that this build does not handle: 2D padded layers wider than
+// 64 columns, 3D blocks larger than kMaxNb3.
+bool supported(const asp_params* p, std::string* why) {
+  const int ga = p->pml_aux ? p->pml_aux : p->pml;
+  Part P = partition(p->n, p->pml, ga, p->b);
+  int wmax = 0;
+  for (int q = 1; q <= P.m; ++q) wmax = std::max(wmax, P.m_hi[q] - P.m_lo[q] + 1);
+  if (p->dim == 2 && wmax > 64) {
+    *why = "padded layer width 2*gamma_a + b - 2 (+ remainder) exceeds 64 columns";
+    return false;
+  }
+  if (p->dim == 3 && (long long)p->n * wmax > kMaxNb3) {
+    *why = "3D block size n * (padded slab width) exceeds " + std::to_string(kMaxNb3);
+    return false;
+  }
+  return true;
+}
+
 int fmax_rhs_cap(int prec) { return prec == ASP_PREC_C64 ? 64 : 16; }
 
+Sizes sizes_for3(const asp_params* p, int num_sms) {
+  Sizes Z;
+  const int n = p->n, gamma = p->pml, ga = p->pml_aux ? p->pml_aux : p->pml, b = p->b;
+  Part P = partition(n, gamma, ga, b);
+  Z.m = P.m;
+  Z.esz = p->factor_prec == ASP_PREC_C128 ? 16 : 8;
+  Z.N = (long long)n * n * n;
+  const long long mr = p->max_rhs;
+  auto addslab = [&](int lo, int hi, bool rl) {
+    const int w = hi - lo + 1;
+    const int nb = n * w, ld = (nb + 3) & ~3;
+    Z.W_elems += (size_t)n * nb * ld;
+    Z.A_elems += (size_t)2 * nb * ld;
+    Z.piv_elems += (size_t)3 * nb;
+    Z.z3_elems += (size_t)n * nb * mr;
+    Z.coef += w;
+    Z.wmax = std::max(Z.wmax, w);
+    if (rl) Z.nbmaxRL = std::max(Z.nbmaxRL, nb);
+    else Z.nbmaxM = std::max(Z.nbmaxM, nb);
+    Z.nsub++;
+  };
+  for (int q = 1; q <= P.m; ++q) addslab(P.m_lo[q], P.m_hi[q], false);
+  for (int q = 2; q <= P.m; ++q) addslab(P.alpha[q], P.m_hi[q], true);
+  for (int q = 1; q <= P.m - 1; ++q) addslab(P.m_lo[q], P.beta[q], true);
+  const long long R = p->restart;
+  size_t n2, nd, ni;
+  const size_t kst = krylov_state_bytes(p->restart, p->max_rhs, &n2, &nd, &ni);
+  const size_t rsz = Z.esz / 2;  // real type of the factor precision
+  size_t bytes = 0;
+  bytes += Z.N * (sizeof(double) + rsz) + 3 * (size_t)n * (sizeof(double2) + Z.esz);  // k2, ca, cc, cd (both)
+  bytes += Z.coef * (sizeof(SweepCoef) + 3 * Z.esz) + Z.nsub * sizeof(Slab) + Z.nsub * sizeof(int);
+  bytes += (Z.W_elems + Z.A_elems + Z.z3_elems) * Z.esz + Z.piv_elems * sizeof(int);
+  bytes += (size_t)Z.N * mr * Z.esz * (3 + (Z.esz == 8 ? 1 : 0));                 // uM uR uL (+ r_lo)
+  bytes += (size_t)(2 * R + 2) * Z.N * mr * sizeof(double2);                        // V, Z, work
+  bytes += (size_t)num_sms * 4 * 9 * mr * sizeof(double2);                          // dot partials
+  bytes += kst + 64;
+  Z.bytes = bytes;
+  return Z;
+}
+
 Sizes sizes_for(const asp_params* p, int num_sms) {
+  if (p->dim == 3) return sizes_for3(p, num_sms);
   Sizes Z;
   const int n = p->n, gamma = p->pml, ga = p->pml_aux ? p->pml_aux : p->pml, b = p->b;
   Part P = partition(n, gamma, ga, b);
@@ -211,7 +276,8 @@ __global__ void to_prec_kernel(const double2* __restrict__ in, Cx<R>* __restrict
 }
 
 // z = uM + uR (except on X_1, where there is no right-going part) + uL (except
-// on X_m).  Grid: blockIdx.y = x2 column, blockIdx.x = chunk of its n*nrhs elements.
+// on X_m).  Grid: blockIdx.y = sweep-axis index (x2 column in 2D, x3 plane in
+// 3D), blockIdx.x = chunk of its per_col elements.
 template <typename R>
 __global__ void sum3_kernel(const Cx<R>* __restrict__ a, const Cx<R>* __restrict__ b, const Cx<R>* __restrict__ c,
                             double2* __restrict__ z, long long per_col, int r_from, int l_below) {
@@ -239,6 +305,18 @@ cudaError_t launch_to_prec(const double2* in, void* out, long long count, int pr
     to_prec_kernel<float><<<vec_grid(count, 152), 256, 0, s>>>(in, (float2*)out, count);
   else
     to_prec_kernel<double><<<vec_grid(count, 152), 256, 0, s>>>(in, (double2*)out, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum3(const void* a, const void* b, const void* c, double2* z, long long per_col, int ncols,
+                        int r_from, int l_below, int prec, cudaStream_t s) {
+  const dim3 sgrid((unsigned)((per_col + 255) / 256), (unsigned)ncols);
+  if (prec == ASP_PREC_C64)
+    sum3_kernel<float><<<sgrid, 256, 0, s>>>((const float2*)a, (const float2*)b, (const float2*)c, z, per_col, r_from,
+                                             l_below);
+  else
+    sum3_kernel<double><<<sgrid, 256, 0, s>>>((const double2*)a, (const double2*)b, (const double2*)c, z, per_col,
+                                              r_from, l_below);
   return cudaGetLastError();
 }
 
@@ -373,6 +451,7 @@ int check_err(Handle& H, cudaStream_t s, const char* what) {
 }  // namespace
 
 int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_t s) {
+  if (H.dim == 3) return apply3d(H, r, z, nrhs, s);
   if (!H.factored) return fail(ASP_ERR_STATE, "apply before factor");
   const long long count = H.N * nrhs;
   const void* in = r;
@@ -419,20 +498,10 @@ int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_
   phase_end(H, tk, s);
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("fill launch: ") + cudaGetErrorString(ce));
   // 4. u~_p = u~_{p,1:p-1} + u~_{p,p} + u~_{p,p+1:m}
-  const long long per_col = (long long)H.n * nrhs;
-  const int r_from = H.x_hi[1];       // 0-based first column of X_2
-  const int l_below = H.x_lo[H.m] - 1;  // 0-based first column of X_m
   tk = phase_begin(H, PH_SUM, s);
-  const dim3 sgrid((unsigned)((per_col + 255) / 256), (unsigned)H.n);
-  if (H.prec == ASP_PREC_C64)
-    sum3_kernel<float><<<sgrid, 256, 0, s>>>((float2*)H.uM, (float2*)H.uR, (float2*)H.uL, z, per_col, r_from,
-                                             l_below);
-  else
-    sum3_kernel<double><<<sgrid, 256, 0, s>>>((double2*)H.uM, (double2*)H.uR, (double2*)H.uL, z, per_col, r_from,
-                                              l_below);
+  ce = launch_sum3(H.uM, H.uR, H.uL, z, (long long)H.n * nrhs, H.n, H.x_hi[1], H.x_lo[H.m] - 1, H.prec, s);
   phase_end(H, tk, s);
   H.launches += 1;
-  ce = cudaGetLastError();
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("sum launch: ") + cudaGetErrorString(ce));
   return ASP_OK;
 }
@@ -462,7 +531,7 @@ const char* asp_last_error_detail(void) { return g_detail.c_str(); }
 
 size_t asp_footprint_bytes(const asp_params* p) {
   std::string why;
-  if (!valid(p, &why)) return 0;
+  if (!valid(p, &why) || !supported(p, &why)) return 0;
   int sms = device_sms();
   if (sms <= 0) sms = 152;
   return sizes_for(p, sms).bytes;
@@ -514,9 +583,10 @@ void asp_destroy(asp_handle* hd) {
     std::lock_guard<std::mutex> lock(caches_mu());
     caches().erase(&H);
   }
+  release_jobs3(&H);
   void* ptrs[] = {H.k2, H.ca, H.cc, H.cd, H.d_subs, H.d_coef, H.W, H.tmap, H.d_toffR, H.d_toffL, H.r_lo,
                   H.uM, H.uR, H.uL, H.accR, H.accL, H.zscr, H.bar, H.V, H.Z, H.wv, H.red, H.hess, H.kstate,
-                  H.kflags, H.err};
+                  H.kflags, H.err, H.d_slabs, H.d_slab_lists, H.A3, H.piv3, H.z3};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : H.coef_bufs)
@@ -532,10 +602,11 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   std::string why;
   if (!out) return fail(ASP_ERR_INVALID, "out is null");
   *out = nullptr;
-  if (!valid(p, &why)) return fail(p && p->dim == 3 ? ASP_ERR_UNSUPPORTED : ASP_ERR_INVALID, why);
+  if (!valid(p, &why)) return fail(ASP_ERR_INVALID, why);
+  if (!supported(p, &why)) return fail(ASP_ERR_UNSUPPORTED, why);
   if (!c) return fail(ASP_ERR_INVALID, "velocity pointer is null");
   const int n = p->n;
-  const long long N = (long long)n * n;
+  const long long N = p->dim == 3 ? (long long)n * n * n : (long long)n * n;
   std::vector<double> ch(N);
   if (c_is_device) {
     if (cudaMemcpy(ch.data(), c, N * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -551,6 +622,7 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   asp_handle* hd = new asp_handle();
   Handle& H = hd->h;
   H.prm = *p;
+  H.dim = p->dim;
   H.n = n;
   H.N = N;
   H.prec = p->factor_prec;
@@ -585,20 +657,12 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   std::vector<double> k2(N);
   for (long long i = 0; i < N; ++i) k2[i] = omega * omega / (ch[i] * ch[i]);
 
-  // ---- subproblems and their sweep-axis profiles
+  // ---- subproblems (2D: strips of columns; 3D: slabs of planes) and their
+  // sweep-axis profiles
   H.subM.assign(m + 1, -1); H.subR.assign(m + 1, -1); H.subL.assign(m + 1, -1);
-  long long woff = 0;
-  auto add = [&](int kind, int q, int lo, int hi, const Profile& pr) {
-    SubDesc S{};
-    S.kind = kind; S.p = q; S.lo = lo; S.w = hi - lo + 1;
-    S.wp = (H.prec == ASP_PREC_C64) ? ((S.w + 1) & ~1) : S.w;
-    S.xoff = H.x_lo[q] - lo;
-    S.xw = H.x_hi[q] - H.x_lo[q] + 1;
-    S.prof = (int)H.coef.size();
-    S.woff = woff;
-    S.toff = -1;
-    woff += (long long)n * S.w * S.wp;
-    for (int j = 0; j < S.w; ++j) {
+  auto push_coef = [&](int lo, int w, const Profile& pr) {
+    const int prof = (int)H.coef.size();
+    for (int j = 0; j < w; ++j) {
       const double x = (lo + j) * h;
       const double2 sj = pr.s(x, omega), sm = pr.s(x - 0.5 * h, omega), sp = pr.s(x + 0.5 * h, omega);
       SweepCoef cf;
@@ -607,9 +671,44 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
       cf.dg = hscale(hadd(cf.up, cf.dn), -1.0);
       H.coef.push_back(cf);
     }
+    return prof;
+  };
+  long long woff = 0, aoff = 0, poff = 0, zoff = 0;
+  auto add = [&](int kind, int q, int lo, int hi, const Profile& pr) {
+    const int w = hi - lo + 1;
+    H.wmax = std::max(H.wmax, w);
+    if (kind != KIND_M) H.wmaxRL = std::max(H.wmaxRL, w);
+    if (H.dim == 3) {
+      Slab S{};
+      S.kind = kind; S.p = q; S.lo = lo; S.w = w;
+      S.xoff = H.x_lo[q] - lo;
+      S.xw = H.x_hi[q] - H.x_lo[q] + 1;
+      S.prof = push_coef(lo, w, pr);
+      S.nb = n * w;
+      S.ld = (S.nb + 3) & ~3;
+      S.src_plane = 0;
+      S.src_sweep = 0;
+      if (kind == KIND_R) { S.src_plane = H.x_hi[q - 1] - 1; S.src_sweep = (q - 1 >= 2) ? 1 : 0; }
+      if (kind == KIND_L) { S.src_plane = H.x_lo[q + 1] - 1; S.src_sweep = (q + 1 <= m - 1) ? 1 : 0; }
+      S.woff = woff; woff += (long long)n * S.nb * S.ld;
+      S.aoff = aoff; aoff += 2LL * S.nb * S.ld;
+      S.poff = poff; poff += 3LL * S.nb;
+      S.zoff = zoff; zoff += (long long)n * S.nb * p->max_rhs;
+      if (kind == KIND_M) H.nbmaxM = std::max(H.nbmaxM, S.nb);
+      else H.nbmaxRL = std::max(H.nbmaxRL, S.nb);
+      H.slabs.push_back(S);
+      return (int)H.slabs.size() - 1;
+    }
+    SubDesc S{};
+    S.kind = kind; S.p = q; S.lo = lo; S.w = w;
+    S.wp = (H.prec == ASP_PREC_C64) ? ((S.w + 1) & ~1) : S.w;
+    S.xoff = H.x_lo[q] - lo;
+    S.xw = H.x_hi[q] - H.x_lo[q] + 1;
+    S.prof = push_coef(lo, w, pr);
+    S.woff = woff;
+    S.toff = -1;
+    woff += (long long)n * S.w * S.wp;
     H.subs.push_back(S);
-    H.wmax = std::max(H.wmax, S.w);
-    if (kind != KIND_M) H.wmaxRL = std::max(H.wmaxRL, S.w);
     return (int)H.subs.size() - 1;
   };
   const double eta = H.gamma * h, eta_a = H.gamma_a * h;
@@ -636,17 +735,15 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
     H.subL[q] = add(KIND_L, q, P.m_lo[q], H.beta[q], pr);
   }
   H.W_elems = (size_t)woff;
-  if (H.wmax > 64) {
-    asp_destroy(hd);
-    return fail(ASP_ERR_UNSUPPORTED, "padded layer width 2*gamma_a + b - 2 (+ remainder) exceeds 64 columns");
-  }
-  // transfer maps T_p^R, T_p^L for p = 2..m-1
+  // transfer maps T_p^R, T_p^L for p = 2..m-1 (2D only)
   H.toffR.assign(m + 1, 0); H.toffL.assign(m + 1, 0);
   H.ldT = (n + 1) & ~1;
   long long toff = 0;
-  for (int q = 2; q <= m - 1; ++q) {
-    H.toffR[q] = toff; H.subs[H.subR[q]].toff = toff; toff += (long long)n * H.ldT;
-    H.toffL[q] = toff; H.subs[H.subL[q]].toff = toff; toff += (long long)n * H.ldT;
+  if (H.dim == 2) {
+    for (int q = 2; q <= m - 1; ++q) {
+      H.toffR[q] = toff; H.subs[H.subR[q]].toff = toff; toff += (long long)n * H.ldT;
+      H.toffL[q] = toff; H.subs[H.subL[q]].toff = toff; toff += (long long)n * H.ldT;
+    }
   }
   H.tmap_elems = (size_t)toff;
 
@@ -663,21 +760,29 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   dal((void**)&H.ca, n * sizeof(double2));
   dal((void**)&H.cc, n * sizeof(double2));
   dal((void**)&H.cd, n * sizeof(double2));
-  dal((void**)&H.d_subs, H.subs.size() * sizeof(SubDesc));
   dal((void**)&H.d_coef, H.coef.size() * sizeof(SweepCoef));
   dal(&H.W, H.W_elems * esz);
-  dal(&H.tmap, H.tmap_elems * esz);
-  dal((void**)&H.d_toffR, (m + 1) * sizeof(long long));
-  dal((void**)&H.d_toffL, (m + 1) * sizeof(long long));
+  if (H.dim == 2) {
+    dal((void**)&H.d_subs, H.subs.size() * sizeof(SubDesc));
+    dal(&H.tmap, H.tmap_elems * esz);
+    dal((void**)&H.d_toffR, (m + 1) * sizeof(long long));
+    dal((void**)&H.d_toffL, (m + 1) * sizeof(long long));
+    dal(&H.accR, (size_t)(m + 1) * n * ((mr + 1) & ~1) * esz);
+    dal(&H.accL, (size_t)(m + 1) * n * ((mr + 1) & ~1) * esz);
+    H.zslots = Z.zslots;
+    H.zslot = (long long)Z.zslot;
+    dal(&H.zscr, (size_t)Z.zslots * Z.zslot * esz);
+  } else {
+    dal((void**)&H.d_slabs, H.slabs.size() * sizeof(Slab));
+    dal((void**)&H.d_slab_lists, H.slabs.size() * sizeof(int));
+    dal(&H.A3, (size_t)aoff * esz);
+    dal((void**)&H.piv3, (size_t)poff * sizeof(int));
+    dal(&H.z3, (size_t)zoff * esz);
+  }
   if (H.prec == ASP_PREC_C64) dal(&H.r_lo, (size_t)N * mr * esz);
   dal(&H.uM, (size_t)N * mr * esz);
   dal(&H.uR, (size_t)N * mr * esz);
   dal(&H.uL, (size_t)N * mr * esz);
-  dal(&H.accR, (size_t)(m + 1) * n * ((mr + 1) & ~1) * esz);
-  dal(&H.accL, (size_t)(m + 1) * n * ((mr + 1) & ~1) * esz);
-  H.zslots = Z.zslots;
-  H.zslot = (long long)Z.zslot;
-  dal(&H.zscr, (size_t)Z.zslots * Z.zslot * esz);
   dal((void**)&H.bar, 64);
   const int R = p->restart;
   dal((void**)&H.V, (size_t)(R + 1) * N * mr * sizeof(double2));
@@ -707,10 +812,17 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   cp(H.ca, ca.data(), n * sizeof(double2));
   cp(H.cc, cc.data(), n * sizeof(double2));
   cp(H.cd, cd.data(), n * sizeof(double2));
-  cp(H.d_subs, H.subs.data(), H.subs.size() * sizeof(SubDesc));
   cp(H.d_coef, H.coef.data(), H.coef.size() * sizeof(SweepCoef));
-  cp(H.d_toffR, H.toffR.data(), (m + 1) * sizeof(long long));
-  cp(H.d_toffL, H.toffL.data(), (m + 1) * sizeof(long long));
+  if (H.dim == 2) {
+    cp(H.d_subs, H.subs.data(), H.subs.size() * sizeof(SubDesc));
+    cp(H.d_toffR, H.toffR.data(), (m + 1) * sizeof(long long));
+    cp(H.d_toffL, H.toffL.data(), (m + 1) * sizeof(long long));
+  } else {
+    std::vector<int> lists(H.slabs.size());
+    for (size_t i = 0; i < lists.size(); ++i) lists[i] = (int)i;  // [M slabs | R slabs, L slabs]
+    cp(H.d_slabs, H.slabs.data(), H.slabs.size() * sizeof(Slab));
+    cp(H.d_slab_lists, lists.data(), lists.size() * sizeof(int));
+  }
   // factor-precision copies of the layer coefficients
   {
     const size_t nc = H.coef.size();
@@ -749,7 +861,8 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
       H.fc32.dg = (const float2*)put(dgf.data(), nc * sizeof(float2));
     }
   }
-  if (up && cudaMemset(H.W, 0, H.W_elems * esz) != cudaSuccess) up = false;
+  if (up && cudaMemset(H.W, 0, H.W_elems * esz) != cudaSuccess) up = false;  // 3D: row padding stays zero
+  if (up && H.piv3 && cudaMemset(H.piv3, 0, (size_t)poff * sizeof(int)) != cudaSuccess) up = false;
   if (up && cudaMemset(H.err, 0, 2 * sizeof(int)) != cudaSuccess) up = false;
   if (up && cudaDeviceSynchronize() != cudaSuccess) up = false;
   if (!up) {
@@ -764,6 +877,14 @@ int asp_factor(asp_handle* hd, void* stream) {
   if (!hd) return fail(ASP_ERR_INVALID, "null handle");
   Handle& H = hd->h;
   cudaStream_t s = (cudaStream_t)stream;
+  if (H.dim == 3) {
+    int rc3 = factor3d(H, s);
+    if (rc3 != ASP_OK) return rc3;
+    rc3 = check_err(H, s, "factor");
+    if (rc3 != ASP_OK) return rc3;
+    H.factored = true;
+    return ASP_OK;
+  }
   // The M-subproblems (indices [0, m)) factor on the internal stream while the
   // R/L subproblems (indices [m, 3m-2)) factor on the caller's stream and their
   // transfer maps are built; the M factors are latency-bound and overlap well.
@@ -836,7 +957,7 @@ int asp_subproblem_width(const asp_handle* hd, int kind, int p) {
   if (p < 1 || p > H.m) return ASP_ERR_INVALID;
   int idx = kind == KIND_M ? H.subM[p] : kind == KIND_R ? H.subR[p] : kind == KIND_L ? H.subL[p] : -1;
   if (idx < 0) return ASP_ERR_INVALID;
-  return H.subs[idx].w;
+  return H.dim == 3 ? H.slabs[idx].w : H.subs[idx].w;
 }
 
 int asp_subproblem_solve(asp_handle* hd, int kind, int p, const void* g, void* v, int nrhs, void* stream) {
@@ -848,6 +969,7 @@ int asp_subproblem_solve(asp_handle* hd, int kind, int p, const void* g, void* v
   int idx = kind == KIND_M ? H.subM[p] : kind == KIND_R ? H.subR[p] : kind == KIND_L ? H.subL[p] : -1;
   if (idx < 0) return fail(ASP_ERR_INVALID, "no such subproblem (H^R needs p >= 2, H^L needs p <= m-1)");
   cudaStream_t s = (cudaStream_t)stream;
+  if (H.dim == 3) return subsolve3d(H, idx, (const double2*)g, (double2*)v, nrhs, s);
   const int w = H.subs[idx].w;
   const void* in = g;
   if (H.prec == ASP_PREC_C64) {

@@ -1,0 +1,444 @@
+// factor3d.cu -- Algorithm 1 for the 3D slab subproblems (Section 4: the
+// layers are slabs of planes and the auxiliary problems H_q^M, H_p^R, H_p^L
+// are the quasi-2D problems of each slab).
+//
+// Ordered with x2 as the block index (local index j = i3l*n + i1 inside a
+// block), a slab of padded width w is block tridiagonal with n dense blocks of
+// size nb = n*w coupled by the x2 stencil weights times the identity, so block
+// elimination needs only the inverses of the Schur complements:
+//     S_0 = T_0,   S_k = T_k - a_k c_{k-1} W_{k-1},   W_k = S_k^-1,
+// the solver then runs z_k = W_k (g_k - a_k z_{k-1}) and x_k = z_k - c_k W_k x_{k+1}.
+// W_k is dense; each inversion is blocked Gauss-Jordan with partial pivoting
+// inside the block, done for every slab of a group at once:
+//   * form/store: W_{k-1} is un-permuted out of the work matrix into the
+//     factor storage, and S_k = T_k - beta_k W_{k-1} is written into the other
+//     work matrix;
+//   * per panel of kPW columns:
+//       panel  -- Gauss-Jordan steps restricted to the panel columns, all rows;
+//                 the panel is split over a thread-block cluster (rows across
+//                 CTAs, in shared memory); the pivot search and the pivot row
+//                 travel through distributed shared memory;
+//       update -- every column outside the panel: A[:, j] <- A[:, j] (rows of
+//                 this panel's pivots cleared) + A[:, panel] * A_old[R, j],
+//                 a rank-kPW complex product (R = the panel's pivot rows);
+//       rrows  -- the pivot rows themselves, A[R, j] = A[R, panel] * A_old[R, j].
+// After the last panel the work matrix holds the inverse with rows and columns
+// permuted: W[i][j] = B[piv_row[i]][col_of_row[j]], with piv_row[c] the pivot row
+// of column c and col_of_row its inverse.  Zero or non-finite pivots record
+// ASP_ERR_SMALL_PIVOT with the slab index.
+#include <cooperative_groups.h>
+#include <limits.h>
+
+#include <algorithm>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace asp {
+
+namespace {
+
+constexpr int kPW = 32;    // panel width
+constexpr int kLDP = kPW + 1;
+constexpr int kPanelThreads = 512;
+constexpr int kPanelWarps = kPanelThreads / 32;
+constexpr int kBM = 128, kBN = 64;  // update tile: 16 x 16 threads, 8 x 4 complex each (strided by 16)
+constexpr int kUpdThreads = 256;
+
+template <typename R> __device__ __forceinline__ Cx<R>* work(const Slab3Params& P, const Slab& S, int buf) {
+  return reinterpret_cast<Cx<R>*>(P.A) + S.aoff + (long long)buf * S.nb * S.ld;
+}
+
+// ------------------------------------------------------------ form / store
+// Row i = blockIdx.x of slab list[blockIdx.y].
+template <typename R>
+__global__ void __launch_bounds__(256) form_store_kernel(Slab3Params P, FactorCoefs<R> F, int k, int src_buf,
+                                                         int store, int form) {
+  using C = Cx<R>;
+  const Slab S = P.slabs[P.list[blockIdx.y]];
+  const int i = blockIdx.x;
+  if (i >= S.nb) return;
+  const int nb = S.nb, ld = S.ld, n = P.n;
+  const C* src = work<R>(P, S, src_buf);
+  C* dst = work<R>(P, S, src_buf ^ 1);
+  int* piv_row = P.piv + S.poff;
+  const int* col_of_row = piv_row + nb;
+  int* row_step = piv_row + 2 * nb;
+  C* Wk = reinterpret_cast<C*>(P.W) + S.woff + (long long)(k - 1) * nb * ld;
+  // the pivot tables are complete unless a pivot search failed (recorded as
+  // ASP_ERR_SMALL_PIVOT); clamping keeps every access inside the block anyway
+  const int pr = store ? min(max(piv_row[i], 0), nb - 1) : 0;
+  const int i3l = i / n, i1 = i - i3l * n;
+  C diag = czero<R>(), beta = czero<R>(), xm = czero<R>(), xp = czero<R>(), zm = czero<R>(), zp = czero<R>();
+  if (form) {
+    diag = cadd(cadd(F.dg[S.prof + i3l], F.cd[i1]), F.cd[k]);
+    diag.x += F.k2[((long long)(S.lo - 1 + i3l) * n + k) * n + i1];
+    if (k > 0) beta = cmul(F.ca[k], F.cc[k - 1]);
+    if (i1 > 0) xm = F.ca[i1];
+    if (i1 < n - 1) xp = F.cc[i1];
+    zm = F.dn[S.prof + i3l];
+    zp = F.up[S.prof + i3l];
+  }
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    C wv = czero<R>();
+    if (store) {
+      wv = src[(long long)pr * ld + min(max(col_of_row[j], 0), nb - 1)];
+      Wk[(long long)i * ld + j] = wv;
+    }
+    if (form) {
+      C t = czero<R>();
+      if (j == i) t = diag;
+      else if (j == i - 1) t = xm;
+      else if (j == i + 1) t = xp;
+      else if (j == i - n) t = zm;
+      else if (j == i + n) t = zp;
+      if (store) cfms(t, beta, wv);
+      dst[(long long)i * ld + j] = t;
+    }
+  }
+  if (form && threadIdx.x == 0) row_step[i] = -1;
+}
+
+// ------------------------------------------------------------------- panel
+// Grid (CL, nlist) with clusters of CL CTAs along x: CTA rank q holds rows
+// [q*rpc, (q+1)*rpc) of the panel in shared memory.
+template <typename R>
+__global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, int c0, int buf) {
+  using C = Cx<R>;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank();
+  const int CL = (int)cluster.num_blocks();
+  const int sidx = P.list[blockIdx.y];
+  const Slab S = P.slabs[sidx];
+  const int nb = S.nb, ld = S.ld;
+  if (c0 >= nb) return;  // the whole cluster leaves together
+  const int pw = min(kPW, nb - c0);
+  const int rpc = (nb + CL - 1) / CL;
+  const int row0 = q * rpc;
+  const int nrows = max(0, min(nb, row0 + rpc) - row0);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Ps = reinterpret_cast<C*>(smem_raw);                    // [rpc][kLDP]
+  int* rstep = reinterpret_cast<int*>(Ps + (size_t)rpc * kLDP);  // [rpc]
+  __shared__ C prow[kPW];
+  __shared__ R candv[2];
+  __shared__ int candr[2];
+  __shared__ R wbest[kPanelWarps];
+  __shared__ int wrow[kPanelWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  C* A = work<R>(P, S, buf);
+  int* piv_row = P.piv + S.poff;
+  int* col_of_row = piv_row + nb;
+  int* row_step = piv_row + 2 * nb;
+
+  for (int e = tid; e < nrows * kPW; e += kPanelThreads) {
+    const int l = e / kPW, t = e - l * kPW;
+    Ps[l * kLDP + t] = (t < pw) ? A[(long long)(row0 + l) * ld + c0 + t] : czero<R>();
+  }
+  for (int l = tid; l < nrows; l += kPanelThreads) rstep[l] = row_step[row0 + l];
+  __syncthreads();
+
+  bool bad = false;
+  for (int t = 0; t < pw; ++t) {
+    const int c = c0 + t;
+    // ---- pivot candidate of this CTA: largest |A[i][c]| over rows not yet pivots
+    R best = R(-1);
+    int bi = INT_MAX;
+    for (int l = tid; l < nrows; l += kPanelThreads) {
+      if (rstep[l] < 0) {
+        const C v = Ps[l * kLDP + t];
+        const R a = v.x * v.x + v.y * v.y;
+        if (a > best) { best = a; bi = row0 + l; }  // rows ascend with l: ties keep the first
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const R ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { wbest[warp] = best; wrow[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < kPanelWarps ? wbest[lane] : R(-1);
+      bi = lane < kPanelWarps ? wrow[lane] : INT_MAX;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const R ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { candv[t & 1] = best; candr[t & 1] = bi; }
+    }
+    cluster.sync();
+    // ---- the cluster's pivot (every thread computes the same choice)
+    R gb = R(-1);
+    int gr = INT_MAX;
+    for (int r = 0; r < CL; ++r) {
+      const R a = *cluster.map_shared_rank(&candv[t & 1], r);
+      const int ri = *cluster.map_shared_rank(&candr[t & 1], r);
+      if (a > gb || (a == gb && ri < gr)) { gb = a; gr = ri; }
+    }
+    const bool okp = gr >= 0 && gr < nb;
+    if (!(gb > R(0)) || !isfinite(gb)) bad = true;
+    const int owner = okp ? gr / rpc : 0;
+    const int lr = okp ? gr - owner * rpc : 0;
+    if (tid < kPW) {
+      C v = czero<R>();
+      if (okp && tid < pw) v = cluster.map_shared_rank(Ps, owner)[lr * kLDP + tid];
+      prow[tid] = v;
+    }
+    cluster.sync();  // every CTA holds the pivot row before its owner rewrites it
+    if (okp) {
+      const C inv = crecip(prow[t]);
+      const C pl = prow[lane];
+      for (int l = warp; l < nrows; l += kPanelWarps) {
+        C* rowp = Ps + l * kLDP;
+        C v;
+        if (row0 + l == gr) {
+          v = (lane == t) ? inv : cmul(pl, inv);
+        } else {
+          const C f = cmul(rowp[t], inv);
+          v = rowp[lane];
+          if (lane == t) {
+            v = f;
+            v.x = -v.x;
+            v.y = -v.y;
+          } else {
+            cfms(v, f, pl);
+          }
+        }
+        __syncwarp();
+        if (lane < pw) rowp[lane] = v;
+      }
+      if (tid == 0 && q == owner) rstep[lr] = c;
+      if (tid == 0 && q == 0) {
+        piv_row[c] = gr;
+        col_of_row[gr] = c;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nrows * pw; e += kPanelThreads) {
+    const int l = e / pw, t = e - l * pw;
+    A[(long long)(row0 + l) * ld + c0 + t] = Ps[l * kLDP + t];
+  }
+  for (int l = tid; l < nrows; l += kPanelThreads) row_step[row0 + l] = rstep[l];
+  if (bad && tid == 0 && q == 0) record_error(P.err, ASP_ERR_SMALL_PIVOT, sidx);
+}
+
+// ------------------------------------------------------------------ update
+// Columns outside the panel, rows that are not this panel's pivots:
+//     A[i][j] += sum_t A[i][c0+t] * A[r_t][j].
+// Grid (column tiles, row tiles, nlist).
+template <typename R>
+__global__ void __launch_bounds__(kUpdThreads) update_kernel(Slab3Params P, int c0, int buf) {
+  using C = Cx<R>;
+  const Slab S = P.slabs[P.list[blockIdx.z]];
+  const int nb = S.nb, ld = S.ld;
+  if (c0 >= nb) return;
+  const int pw = min(kPW, nb - c0);
+  const int j0 = blockIdx.x * kBN, i0 = blockIdx.y * kBM;
+  if (j0 >= nb || i0 >= nb) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* As = reinterpret_cast<C*>(smem_raw);  // [kBM][kLDP]   panel rows
+  C* Bs = As + kBM * kLDP;                 // [kPW][kBN]    old pivot rows
+  __shared__ int prs[kPW];
+  C* A = work<R>(P, S, buf);
+  const int* piv_row = P.piv + S.poff;
+  const int* row_step = piv_row + 2 * nb;
+  const int tid = threadIdx.x;
+  if (tid < kPW) prs[tid] = tid < pw ? min(max(piv_row[c0 + tid], 0), nb - 1) : 0;
+  for (int e = tid; e < kBM * kPW; e += kUpdThreads) {
+    const int ii = e / kPW, t = e - ii * kPW;
+    const int i = i0 + ii;
+    As[ii * kLDP + t] = (t < pw && i < nb) ? A[(long long)i * ld + c0 + t] : czero<R>();
+  }
+  __syncthreads();
+  for (int e = tid; e < kPW * kBN; e += kUpdThreads) {
+    const int t = e / kBN, jj = e - t * kBN;
+    const int j = j0 + jj;
+    Bs[t * kBN + jj] = (t < pw && j < nb) ? A[(long long)prs[t] * ld + j] : czero<R>();
+  }
+  __syncthreads();
+  const int ty = tid >> 4, tx = tid & 15;
+  C acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = czero<R>();
+  for (int t = 0; t < pw; ++t) {
+    C av[8], bv[4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) av[a] = As[(ty + 16 * a) * kLDP + t];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = Bs[t * kBN + tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int i = i0 + ty + 16 * a;
+    if (i >= nb) continue;
+    const int st = row_step[i];
+    if (st >= c0 && st < c0 + pw) continue;  // a pivot row of this panel
+    C* rowp = A + (long long)i * ld;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + tx + 16 * b;
+      if (j >= nb || (j >= c0 && j < c0 + pw)) continue;
+      rowp[j] = cadd(rowp[j], acc[a][b]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------- rrows
+// The panel's pivot rows outside the panel: A[r_t][j] = sum_u A[r_t][c0+u] A_old[r_u][j].
+// Grid (column tiles of RC, nlist); 8 * RC threads.
+template <typename R> struct RrowsCols { static constexpr int v = sizeof(R) == 4 ? 64 : 32; };
+
+template <typename R>
+__global__ void __launch_bounds__(8 * RrowsCols<R>::v) rrows_kernel(Slab3Params P, int c0, int buf) {
+  using C = Cx<R>;
+  constexpr int RC = RrowsCols<R>::v;
+  constexpr int NT = 8 * RC;
+  const Slab S = P.slabs[P.list[blockIdx.y]];
+  const int nb = S.nb, ld = S.ld;
+  if (c0 >= nb) return;
+  const int pw = min(kPW, nb - c0);
+  const int j0 = blockIdx.x * RC;
+  if (j0 >= nb) return;
+  __shared__ C Zs[kPW][RC];
+  __shared__ C PR[kPW][kLDP];
+  __shared__ int prs[kPW];
+  C* A = work<R>(P, S, buf);
+  const int* piv_row = P.piv + S.poff;
+  const int tid = threadIdx.x;
+  if (tid < kPW) prs[tid] = tid < pw ? min(max(piv_row[c0 + tid], 0), nb - 1) : 0;
+  __syncthreads();
+  for (int e = tid; e < kPW * RC; e += NT) {
+    const int t = e / RC, jj = e - t * RC;
+    const int j = j0 + jj;
+    Zs[t][jj] = (t < pw && j < nb) ? A[(long long)prs[t] * ld + j] : czero<R>();
+  }
+  for (int e = tid; e < kPW * kPW; e += NT) {
+    const int t = e / kPW, u = e - t * kPW;
+    PR[t][u] = (t < pw && u < pw) ? A[(long long)prs[t] * ld + c0 + u] : czero<R>();
+  }
+  __syncthreads();
+  const int jj = tid % RC, tg = tid / RC;  // 8 groups of 4 pivot rows
+  const int j = j0 + jj;
+  if (j >= nb || (j >= c0 && j < c0 + pw)) return;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int t = tg * 4 + a;
+    if (t >= pw) break;
+    C v = czero<R>();
+    for (int u = 0; u < pw; ++u) cfma(v, PR[t][u], Zs[u][jj]);
+    A[(long long)prs[t] * ld + j] = v;
+  }
+}
+
+// ------------------------------------------------------------------ driver
+template <typename R> struct Factor3Kernels {
+  static cudaError_t run_group(Handle& H, const FactorCoefs<R>& F, const int* d_list, int nlist, int nbmax,
+                               cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    Slab3Params P{};
+    P.slabs = H.d_slabs;
+    P.list = d_list;
+    P.nlist = nlist;
+    P.n = H.n;
+    P.W = H.W;
+    P.A = H.A3;
+    P.piv = H.piv3;
+    P.err = H.err;
+    const size_t esz = sizeof(Cx<R>);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t static_bytes = 4096;
+    const int rows_cap = (int)(((size_t)optin - static_bytes) / (kLDP * esz + sizeof(int)));
+    int CL = (nbmax + rows_cap - 1) / rows_cap;
+    if (CL < 1) CL = 1;
+    if (CL > 8) return cudaErrorInvalidValue;
+    const int rpc = (nbmax + CL - 1) / CL;
+    const size_t psmem = (size_t)rpc * (kLDP * esz + sizeof(int));
+    cudaError_t e = cudaFuncSetAttribute(panel_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    if (e != cudaSuccess) return e;
+    if (CL > 1) {
+      e = cudaFuncSetAttribute(panel_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
+      if (e != cudaSuccess) return e;
+    }
+    const size_t usmem = (size_t)(kBM * kLDP + kPW * kBN) * esz;
+    e = cudaFuncSetAttribute(update_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t pc{};
+    cudaLaunchAttribute pattr[1];
+    pattr[0].id = cudaLaunchAttributeClusterDimension;
+    pattr[0].val.clusterDim.x = CL;
+    pattr[0].val.clusterDim.y = 1;
+    pattr[0].val.clusterDim.z = 1;
+    pc.gridDim = dim3(CL, nlist);
+    pc.blockDim = dim3(kPanelThreads);
+    pc.dynamicSmemBytes = psmem;
+    pc.stream = s;
+    pc.attrs = pattr;
+    pc.numAttrs = 1;
+    const dim3 ugrid((nbmax + kBN - 1) / kBN, (nbmax + kBM - 1) / kBM, nlist);
+    const dim3 rgrid((nbmax + RrowsCols<R>::v - 1) / RrowsCols<R>::v, nlist);
+    const int n = H.n;
+    for (int k = 0; k <= n; ++k) {
+      const int store = k > 0, form = k < n;
+      form_store_kernel<R><<<dim3(nbmax, nlist), 256, 0, s>>>(P, F, k, (k + 1) & 1, store, form);
+      H.launches += 1;
+      if (!form) break;
+      const int buf = k & 1;
+      for (int c0 = 0; c0 < nbmax; c0 += kPW) {
+        e = cudaLaunchKernelEx(&pc, panel_kernel<R>, P, c0, buf);
+        if (e != cudaSuccess) return e;
+        update_kernel<R><<<ugrid, kUpdThreads, usmem, s>>>(P, c0, buf);
+        rrows_kernel<R><<<rgrid, 8 * RrowsCols<R>::v, 0, s>>>(P, c0, buf);
+        H.launches += 3;
+      }
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace
+
+// Factors every slab: the M group on the handle's internal stream, the R and L
+// group on the caller's stream, then joins the two.
+int factor3d(Handle& H, cudaStream_t s) {
+  const int m = H.m;
+  const int nM = m, nRL = (int)H.slabs.size() - m;
+  if (cudaEventRecord(H.ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(H.aux, H.ev_fork, 0) != cudaSuccess)
+    return fail(ASP_ERR_CUDA, "factor: stream fork");
+  cudaError_t ea, eb;
+  PhaseTok ta = phase_begin(H, PH_FACTOR, H.aux);
+  if (H.prec == ASP_PREC_C128)
+    ea = Factor3Kernels<double>::run_group(H, H.fc64, H.d_slab_lists, nM, H.nbmaxM, H.aux);
+  else
+    ea = Factor3Kernels<float>::run_group(H, H.fc32, H.d_slab_lists, nM, H.nbmaxM, H.aux);
+  phase_end(H, ta, H.aux);
+  PhaseTok tb = phase_begin(H, PH_FACTOR, s);
+  if (H.prec == ASP_PREC_C128)
+    eb = Factor3Kernels<double>::run_group(H, H.fc64, H.d_slab_lists + nM, nRL, H.nbmaxRL, s);
+  else
+    eb = Factor3Kernels<float>::run_group(H, H.fc32, H.d_slab_lists + nM, nRL, H.nbmaxRL, s);
+  phase_end(H, tb, s);
+  if (cudaEventRecord(H.ev_join, H.aux) != cudaSuccess || cudaStreamWaitEvent(s, H.ev_join, 0) != cudaSuccess)
+    return fail(ASP_ERR_CUDA, "factor: stream join");
+  if (ea != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("3D factor (M) launch: ") + cudaGetErrorString(ea));
+  if (eb != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("3D factor (R/L) launch: ") + cudaGetErrorString(eb));
+  return ASP_OK;
+}
+
+}  // namespace asp

@@ -111,6 +111,63 @@ struct ChainParams {
   int* err;
 };
 
+// ---- 3D (Section 4): slab subproblems
+// A slab is a subproblem on the padded sweep range [lo, lo+w-1] along x3 with
+// the full x1 and x2 ranges.  With x2 as the block index and the local index
+// j = i3l*n + i1 inside a block (x1 fastest), it is block tridiagonal: n dense
+// diagonal blocks T_k of size nb = n*w (the x1/x3 stencil of plane x2 = k),
+// coupled to the neighbouring planes by the x2 weights times the identity.
+struct Slab {
+  int kind, p;
+  int lo, w;          // padded sweep range (global 1-based x3)
+  int xoff, xw;       // X_p = local planes [xoff, xoff + xw)
+  int prof;           // offset of its sweep-axis coefficients (SweepCoef table)
+  int nb;             // block size n*w
+  int ld;             // row stride of a stored block (nb rounded up to 4)
+  int src_plane;      // FILL modes: 0-based global x3 plane of the incoming trace
+  int src_sweep;      // FILL modes: 1 if the trace includes the sweep field there
+  long long woff;     // element offset of block 0 of its factor (n blocks of nb x ld)
+  long long aoff;     // element offset of its two factor-time work matrices
+  long long poff;     // int offset of its pivot tables (3 * nb)
+  long long zoff;     // element offset of its solve scratch (n * nb * max_rhs)
+};
+
+struct Slab3Params {
+  const Slab* slabs;
+  const int* list;    // slab indices of this launch
+  int nlist;
+  int n;
+  void* W;            // factors
+  void* A;            // work matrices
+  int* piv;           // pivot tables: piv_row[nb], col_of_row[nb], row_step[nb]
+  int* err;
+};
+
+struct Solve3Job {
+  int slab, mode, rhs0, nr;
+  int item0;          // first work item of this job (prefix over the launch)
+};
+
+struct Solve3Params {
+  const Slab* slabs;
+  const Solve3Job* jobs;
+  int njobs;
+  int nitems;         // total work items (row chunks) per block step
+  int n, ldv;
+  double inv_h2;
+  const void* W;
+  const void* ca;     // x2 weights a_k (block k -> k-1), factor precision
+  const void* cc;     // x2 weights c_k (block k -> k+1)
+  const void* in;
+  void* outM;
+  void* outR;
+  void* outL;
+  void* outSub;       // MODE_SUB output (complex128, [w][n][n][ldv])
+  void* z;            // per-slab scratch base
+  unsigned int* bar;
+  int* err;
+};
+
 struct Handle;
 
 enum Phase : int {
@@ -134,15 +191,22 @@ cudaError_t launch_btsolve_aux(Handle& H, const SolveParams& P, int cls, int cap
 int btsolve_rhs_capacity(int nrhs, int wmax, int prec, bool tmap);
 cudaError_t launch_chain(Handle& H, const ChainParams& P, cudaStream_t s);
 cudaError_t launch_to_prec(const double2* in, void* out, long long count, int prec, cudaStream_t s);
-cudaError_t launch_sum3(const void* a, const void* b, const void* c, double2* z, long long count, int prec,
-                        cudaStream_t s);
+// z = a + b (planes >= r_from) + c (planes < l_below), planes of per_col elements
+cudaError_t launch_sum3(const void* a, const void* b, const void* c, double2* z, long long per_col, int ncols,
+                        int r_from, int l_below, int prec, cudaStream_t s);
+cudaError_t launch_matvec3d(const Handle& H, const double2* x, double2* y, int nrhs, cudaStream_t s);
+int factor3d(Handle& H, cudaStream_t s);
+int apply3d(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_t s);
+int subsolve3d(Handle& H, int slab, const double2* g, double2* v, int nrhs, cudaStream_t s);
+void release_jobs3(const Handle* H);
 
 // ---- handle ----
 struct Handle {
   asp_params prm{};
+  int dim = 2;
   int n = 0, m = 0, prec = 0, gamma = 0, gamma_a = 0, b = 0;
   double h = 0, inv_h2 = 0;
-  long long N = 0;  // n^2 grid points
+  long long N = 0;  // n^dim grid points
 
   // partition (host), 1-based arrays sized m+1
   std::vector<int> x_lo, x_hi, alpha, beta;
@@ -213,6 +277,15 @@ struct Handle {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> evpool;
   std::mutex rec_mu;
+
+  // 3D slabs (subM/subR/subL index into slabs when dim == 3)
+  std::vector<Slab> slabs;
+  Slab* d_slabs = nullptr;
+  int* d_slab_lists = nullptr;  // [M slabs | R and L slabs]
+  int nbmaxM = 0, nbmaxRL = 0;
+  void* A3 = nullptr;           // factor-time work matrices
+  int* piv3 = nullptr;
+  void* z3 = nullptr;           // solve scratch
 
   // second stream for work that overlaps the caller's stream (factor time)
   cudaStream_t aux = nullptr;

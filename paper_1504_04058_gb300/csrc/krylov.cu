@@ -396,6 +396,7 @@ int grid_for(long long count, int threads, int sms) {
 }  // namespace
 
 cudaError_t launch_matvec(const Handle& H, const double2* x, double2* y, int nrhs, cudaStream_t s) {
+  if (H.dim == 3) return launch_matvec3d(H, x, y, nrhs, s);
   const long long per_row = (long long)H.n * nrhs;
   dim3 grid((unsigned)((per_row + kVecThreads - 1) / kVecThreads), (unsigned)H.n);
   switch (nrhs) {

@@ -67,14 +67,41 @@ def test_invalid_parameters_rejected_on_host(lib):
         assert lib.asp_last_error_detail()
 
 
-def test_3d_request_reports_unsupported(lib):
+def test_dimension_checks(lib):
+    """dim must be 2 or 3; a 3D slab block larger than the kernels take is
+    reported as unsupported before any device work."""
     import numpy as np
     from paper_1504_04058_gb300 import _lib, make_params
-    p = make_params(31, 50.0, 4, 4, dim=3)
     out = ctypes.c_void_p()
+    p = make_params(31, 50.0, 4, 4, dim=4)
     c = np.ones(31 ** 3)
     assert lib.asp_setup(ctypes.byref(p), c.ctypes.data_as(ctypes.c_void_p), 0,
+                         ctypes.byref(out)) == _lib.ASP_ERR_INVALID
+    p = make_params(255, 50.0, 12, 4, dim=3)  # blocks of 255 * 26 unknowns
+    c = np.ones(255 ** 3)
+    assert lib.asp_setup(ctypes.byref(p), c.ctypes.data_as(ctypes.c_void_p), 0,
                          ctypes.byref(out)) == _lib.ASP_ERR_UNSUPPORTED
+    assert lib.asp_footprint_bytes(ctypes.byref(p)) == 0
+
+
+def test_3d_footprint_counts_every_slab_factor(lib):
+    """3D factors: n dense blocks of (n w) x (n w) per slab (rows padded to a
+    multiple of 4), for every M, R and L slab."""
+    from paper_1504_04058_gb300 import make_params
+    n, gamma, b = 95, 8, 4
+    p = make_params(n, 48 * 3.141592653589793, gamma, b, precision="c64", max_rhs=1, dim=3)
+    m = (n + 2 - 2 * gamma) // b
+    alpha = [gamma + (q - 1) * b for q in range(1, m + 1)]
+    beta = [gamma + q * b - 1 if q < m else n + 1 - gamma for q in range(1, m + 1)]
+    mlo = [1 if q == 1 else alpha[q - 1] - gamma + 1 for q in range(1, m + 1)]
+    mhi = [n if q == m else beta[q - 1] + gamma - 1 for q in range(1, m + 1)]
+    widths = [mhi[q] - mlo[q] + 1 for q in range(m)]
+    widths += [mhi[q] - alpha[q] + 1 for q in range(1, m)]
+    widths += [beta[q] - mlo[q] + 1 for q in range(m - 1)]
+    factor_bytes = sum(n * (n * w) * ((n * w + 3) // 4 * 4) * 8 for w in widths)
+    fp = lib.asp_footprint_bytes(ctypes.byref(p))
+    assert factor_bytes < fp < 1.2 * factor_bytes
+    assert 70e9 < factor_bytes < 80e9
 
 
 def test_nonpositive_velocity_rejected(lib):
