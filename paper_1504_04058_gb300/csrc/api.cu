@@ -190,7 +190,7 @@ Sizes sizes_for3(const asp_params* p, int num_sms) {
     const int w = hi - lo + 1;
     const int nb = n * w, ld = (nb + 3) & ~3;
     Z.W_elems += (size_t)n * nb * ld;
-    Z.A_elems += (size_t)2 * nb * ld;
+    Z.A_elems += (size_t)slab_work_elems(nb, ld);
     Z.piv_elems += (size_t)3 * nb;
     Z.z3_elems += (size_t)n * nb * mr;
     Z.coef += w;
@@ -691,7 +691,7 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
       if (kind == KIND_R) { S.src_plane = H.x_hi[q - 1] - 1; S.src_sweep = (q - 1 >= 2) ? 1 : 0; }
       if (kind == KIND_L) { S.src_plane = H.x_lo[q + 1] - 1; S.src_sweep = (q + 1 <= m - 1) ? 1 : 0; }
       S.woff = woff; woff += (long long)n * S.nb * S.ld;
-      S.aoff = aoff; aoff += 2LL * S.nb * S.ld;
+      S.aoff = aoff; aoff += slab_work_elems(S.nb, S.ld);
       S.poff = poff; poff += 3LL * S.nb;
       S.zoff = zoff; zoff += (long long)n * S.nb * p->max_rhs;
       if (kind == KIND_M) H.nbmaxM = std::max(H.nbmaxM, S.nb);

@@ -13,18 +13,25 @@
 //   * form/store: W_{k-1} is un-permuted out of the work matrix into the
 //     factor storage, and S_k = T_k - beta_k W_{k-1} is written into the other
 //     work matrix;
-//   * per panel of kPW columns:
+//   * per outer block of kSlabOuter columns, per inner panel of kSlabPanel
+//     columns inside it:
 //       panel  -- Gauss-Jordan steps restricted to the panel columns, all rows;
 //                 the panel is split over a thread-block cluster (rows across
 //                 CTAs, in shared memory); the pivot search and the pivot row
-//                 travel through distributed shared memory;
-//       update -- every column outside the panel: A[:, j] <- A[:, j] (rows of
-//                 this panel's pivots cleared) + A[:, panel] * A_old[R, j],
-//                 a rank-kPW complex product (R = the panel's pivot rows);
-//       rrows  -- the pivot rows themselves, A[R, j] = A[R, panel] * A_old[R, j].
-// After the last panel the work matrix holds the inverse with rows and columns
-// permuted: W[i][j] = B[piv_row[i]][col_of_row[j]], with piv_row[c] the pivot row
-// of column c and col_of_row its inverse.  Zero or non-finite pivots record
+//                 travel through distributed shared memory; at the end the
+//                 panel's pivot rows inside the outer block are copied aside;
+//       inner update -- the other columns of the outer block take the panel's
+//                 steps (a rank-kSlabPanel product);
+//   * then every column outside the outer block takes all of its steps at
+//     once: with R the block's pivot rows and P the block's columns after its
+//     panels, A[:, j] <- A[:, j] (rows R cleared) + P * A_old[R, j]; the rows
+//     R are copied aside first (gather), so one complex rank-kSlabOuter
+//     product updates pivot and non-pivot rows alike (big update).
+// Composing Gauss-Jordan steps this way is exact: a column outside a block of
+// steps changes only through the block's pivot rows.  After the last block the
+// work matrix holds the inverse with rows and columns permuted:
+// W[i][j] = B[piv_row[i]][col_of_row[j]], with piv_row[c] the pivot row of
+// column c and col_of_row its inverse.  Zero or non-finite pivots record
 // ASP_ERR_SMALL_PIVOT with the slab index.
 #include <cooperative_groups.h>
 #include <limits.h>
@@ -41,7 +48,8 @@ namespace asp {
 
 namespace {
 
-constexpr int kPW = 32;    // panel width
+constexpr int kPW = kSlabPanel;  // panel width
+constexpr int kKO = kSlabOuter;  // outer block width
 constexpr int kLDP = kPW + 1;
 constexpr int kPanelThreads = 512;
 constexpr int kPanelWarps = kPanelThreads / 32;
@@ -50,6 +58,14 @@ constexpr int kUpdThreads = 256;
 
 template <typename R> __device__ __forceinline__ Cx<R>* work(const Slab3Params& P, const Slab& S, int buf) {
   return reinterpret_cast<Cx<R>*>(P.A) + S.aoff + (long long)buf * S.nb * S.ld;
+}
+// outer block's pivot rows, kKO x ld
+template <typename R> __device__ __forceinline__ Cx<R>* zbig(const Slab3Params& P, const Slab& S) {
+  return reinterpret_cast<Cx<R>*>(P.A) + S.aoff + 2LL * S.nb * S.ld;
+}
+// inner panel's pivot rows inside the outer block, kPW x kKO
+template <typename R> __device__ __forceinline__ Cx<R>* zpan(const Slab3Params& P, const Slab& S) {
+  return reinterpret_cast<Cx<R>*>(P.A) + S.aoff + 2LL * S.nb * S.ld + (long long)kKO * S.ld;
 }
 
 // ------------------------------------------------------------ form / store
@@ -106,7 +122,7 @@ __global__ void __launch_bounds__(256) form_store_kernel(Slab3Params P, FactorCo
 // Grid (CL, nlist) with clusters of CL CTAs along x: CTA rank q holds rows
 // [q*rpc, (q+1)*rpc) of the panel in shared memory.
 template <typename R>
-__global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, int c0, int buf) {
+__global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, int c0, int C0, int buf) {
   using C = Cx<R>;
   cg::cluster_group cluster = cg::this_cluster();
   const int q = (int)cluster.block_rank();
@@ -127,6 +143,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
   __shared__ int candr[2];
   __shared__ R wbest[kPanelWarps];
   __shared__ int wrow[kPanelWarps];
+  __shared__ int pivs[kPW];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   C* A = work<R>(P, S, buf);
   int* piv_row = P.piv + S.poff;
@@ -219,6 +236,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
         col_of_row[gr] = c;
       }
     }
+    if (tid == 0) pivs[t] = okp ? gr : 0;
     __syncthreads();
   }
   for (int e = tid; e < nrows * pw; e += kPanelThreads) {
@@ -226,120 +244,109 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
     A[(long long)(row0 + l) * ld + c0 + t] = Ps[l * kLDP + t];
   }
   for (int l = tid; l < nrows; l += kPanelThreads) row_step[row0 + l] = rstep[l];
+  // pivot rows inside the outer block, outside the panel (untouched here), for
+  // the inner update; rows t = q, q + CL, ... on this CTA
+  {
+    const int C1 = min(C0 + kKO, nb);
+    Cx<R>* zp = zpan<R>(P, S);
+    for (int t = q; t < pw; t += CL) {
+      const Cx<R>* src = A + (long long)pivs[t] * ld;
+      for (int j = C0 + tid; j < C1; j += kPanelThreads)
+        zp[t * kKO + (j - C0)] = (j >= c0 && j < c0 + pw) ? czero<R>() : src[j];
+    }
+  }
   if (bad && tid == 0 && q == 0) record_error(P.err, ASP_ERR_SMALL_PIVOT, sidx);
 }
 
-// ------------------------------------------------------------------ update
-// Columns outside the panel, rows that are not this panel's pivots:
-//     A[i][j] += sum_t A[i][c0+t] * A[r_t][j].
-// Grid (column tiles, row tiles, nlist).
+// ------------------------------------------------------------------ gather
+// zbig[t][j] = A[piv_row[C0 + t]][j] for the outer block's pivots.  Grid
+// (row t, nlist).
 template <typename R>
-__global__ void __launch_bounds__(kUpdThreads) update_kernel(Slab3Params P, int c0, int buf) {
+__global__ void __launch_bounds__(256) gather_kernel(Slab3Params P, int C0, int buf) {
+  const Slab S = P.slabs[P.list[blockIdx.y]];
+  const int nb = S.nb, ld = S.ld;
+  const int t = blockIdx.x;
+  if (C0 >= nb || t >= min(kKO, nb - C0)) return;
+  const int* piv_row = P.piv + S.poff;
+  const int r = min(max(piv_row[C0 + t], 0), nb - 1);
+  const Cx<R>* src = work<R>(P, S, buf) + (long long)r * ld;
+  Cx<R>* dst = zbig<R>(P, S) + (long long)t * ld;
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) dst[j] = src[j];
+}
+
+// ------------------------------------------------------------------ update
+// For every row i and every column j in the update range outside [a0, a0+K):
+//     A[i][j] = (i a pivot of columns [a0, a0+K) ? 0 : A[i][j]) + sum_u A[i][a0+u] Z[u][j]
+// inner (big == 0): a0 = c0, K = the panel width, columns [C0, C0 + kKO), Z = zpan;
+// big   (big == 1): a0 = C0, K = the outer block width, all columns, Z = zbig.
+// Grid (column tiles, row tiles, nlist); K is consumed in chunks of kPW.
+template <typename R>
+__global__ void __launch_bounds__(kUpdThreads) update_kernel(Slab3Params P, int C0, int c0, int buf, int big) {
   using C = Cx<R>;
   const Slab S = P.slabs[P.list[blockIdx.z]];
   const int nb = S.nb, ld = S.ld;
-  if (c0 >= nb) return;
-  const int pw = min(kPW, nb - c0);
-  const int j0 = blockIdx.x * kBN, i0 = blockIdx.y * kBM;
-  if (j0 >= nb || i0 >= nb) return;
+  const int a0 = big ? C0 : c0;
+  if (a0 >= nb) return;
+  const int K = big ? min(kKO, nb - C0) : min(kPW, nb - c0);
+  const int jlo = big ? 0 : C0;
+  const int jhi = big ? nb : min(C0 + kKO, nb);
+  const int j0 = jlo + blockIdx.x * kBN, i0 = blockIdx.y * kBM;
+  if (j0 >= jhi || i0 >= nb) return;
+  if (j0 >= a0 && j0 + kBN <= a0 + K) return;  // the tile lies inside the eliminated columns
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* As = reinterpret_cast<C*>(smem_raw);  // [kBM][kLDP]   panel rows
-  C* Bs = As + kBM * kLDP;                 // [kPW][kBN]    old pivot rows
-  __shared__ int prs[kPW];
+  C* As = reinterpret_cast<C*>(smem_raw);  // [kBM][kLDP]   eliminated columns, chunk
+  C* Bs = As + kBM * kLDP;                 // [kPW][kBN]    old pivot rows, chunk
   C* A = work<R>(P, S, buf);
-  const int* piv_row = P.piv + S.poff;
-  const int* row_step = piv_row + 2 * nb;
+  const C* Z = big ? zbig<R>(P, S) : zpan<R>(P, S);
+  const long long ldz = big ? ld : kKO;
+  const int zc0 = big ? 0 : C0;
+  const int* row_step = P.piv + S.poff + 2 * nb;
   const int tid = threadIdx.x;
-  if (tid < kPW) prs[tid] = tid < pw ? min(max(piv_row[c0 + tid], 0), nb - 1) : 0;
-  for (int e = tid; e < kBM * kPW; e += kUpdThreads) {
-    const int ii = e / kPW, t = e - ii * kPW;
-    const int i = i0 + ii;
-    As[ii * kLDP + t] = (t < pw && i < nb) ? A[(long long)i * ld + c0 + t] : czero<R>();
-  }
-  __syncthreads();
-  for (int e = tid; e < kPW * kBN; e += kUpdThreads) {
-    const int t = e / kBN, jj = e - t * kBN;
-    const int j = j0 + jj;
-    Bs[t * kBN + jj] = (t < pw && j < nb) ? A[(long long)prs[t] * ld + j] : czero<R>();
-  }
-  __syncthreads();
   const int ty = tid >> 4, tx = tid & 15;
   C acc[8][4];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = czero<R>();
-  for (int t = 0; t < pw; ++t) {
-    C av[8], bv[4];
+  for (int kc = 0; kc < K; kc += kPW) {
+    const int kw = min(kPW, K - kc);
+    __syncthreads();
+    for (int e = tid; e < kBM * kPW; e += kUpdThreads) {
+      const int ii = e / kPW, t = e - ii * kPW;
+      const int i = i0 + ii;
+      As[ii * kLDP + t] = (t < kw && i < nb) ? A[(long long)i * ld + a0 + kc + t] : czero<R>();
+    }
+    for (int e = tid; e < kPW * kBN; e += kUpdThreads) {
+      const int t = e / kBN, jj = e - t * kBN;
+      const int j = j0 + jj;
+      Bs[t * kBN + jj] = (t < kw && j < jhi) ? Z[(long long)(kc + t) * ldz + (j - zc0)] : czero<R>();
+    }
+    __syncthreads();
+    for (int t = 0; t < kw; ++t) {
+      C av[8], bv[4];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) av[a] = As[(ty + 16 * a) * kLDP + t];
+      for (int a = 0; a < 8; ++a) av[a] = As[(ty + 16 * a) * kLDP + t];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) bv[b] = Bs[t * kBN + tx + 16 * b];
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[t * kBN + tx + 16 * b];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+      for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
+        for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
+    }
   }
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     const int i = i0 + ty + 16 * a;
     if (i >= nb) continue;
     const int st = row_step[i];
-    if (st >= c0 && st < c0 + pw) continue;  // a pivot row of this panel
+    const bool piv = st >= a0 && st < a0 + K;  // this row's old value leaves through Z
     C* rowp = A + (long long)i * ld;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int j = j0 + tx + 16 * b;
-      if (j >= nb || (j >= c0 && j < c0 + pw)) continue;
-      rowp[j] = cadd(rowp[j], acc[a][b]);
+      if (j >= jhi || (j >= a0 && j < a0 + K)) continue;
+      rowp[j] = piv ? acc[a][b] : cadd(rowp[j], acc[a][b]);
     }
-  }
-}
-
-// ------------------------------------------------------------------- rrows
-// The panel's pivot rows outside the panel: A[r_t][j] = sum_u A[r_t][c0+u] A_old[r_u][j].
-// Grid (column tiles of RC, nlist); 8 * RC threads.
-template <typename R> struct RrowsCols { static constexpr int v = sizeof(R) == 4 ? 64 : 32; };
-
-template <typename R>
-__global__ void __launch_bounds__(8 * RrowsCols<R>::v) rrows_kernel(Slab3Params P, int c0, int buf) {
-  using C = Cx<R>;
-  constexpr int RC = RrowsCols<R>::v;
-  constexpr int NT = 8 * RC;
-  const Slab S = P.slabs[P.list[blockIdx.y]];
-  const int nb = S.nb, ld = S.ld;
-  if (c0 >= nb) return;
-  const int pw = min(kPW, nb - c0);
-  const int j0 = blockIdx.x * RC;
-  if (j0 >= nb) return;
-  __shared__ C Zs[kPW][RC];
-  __shared__ C PR[kPW][kLDP];
-  __shared__ int prs[kPW];
-  C* A = work<R>(P, S, buf);
-  const int* piv_row = P.piv + S.poff;
-  const int tid = threadIdx.x;
-  if (tid < kPW) prs[tid] = tid < pw ? min(max(piv_row[c0 + tid], 0), nb - 1) : 0;
-  __syncthreads();
-  for (int e = tid; e < kPW * RC; e += NT) {
-    const int t = e / RC, jj = e - t * RC;
-    const int j = j0 + jj;
-    Zs[t][jj] = (t < pw && j < nb) ? A[(long long)prs[t] * ld + j] : czero<R>();
-  }
-  for (int e = tid; e < kPW * kPW; e += NT) {
-    const int t = e / kPW, u = e - t * kPW;
-    PR[t][u] = (t < pw && u < pw) ? A[(long long)prs[t] * ld + c0 + u] : czero<R>();
-  }
-  __syncthreads();
-  const int jj = tid % RC, tg = tid / RC;  // 8 groups of 4 pivot rows
-  const int j = j0 + jj;
-  if (j >= nb || (j >= c0 && j < c0 + pw)) return;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int t = tg * 4 + a;
-    if (t >= pw) break;
-    C v = czero<R>();
-    for (int u = 0; u < pw; ++u) cfma(v, PR[t][u], Zs[u][jj]);
-    A[(long long)prs[t] * ld + j] = v;
   }
 }
 
@@ -389,8 +396,8 @@ template <typename R> struct Factor3Kernels {
     pc.stream = s;
     pc.attrs = pattr;
     pc.numAttrs = 1;
-    const dim3 ugrid((nbmax + kBN - 1) / kBN, (nbmax + kBM - 1) / kBM, nlist);
-    const dim3 rgrid((nbmax + RrowsCols<R>::v - 1) / RrowsCols<R>::v, nlist);
+    const dim3 igrid(kKO / kBN, (nbmax + kBM - 1) / kBM, nlist);
+    const dim3 bgrid((nbmax + kBN - 1) / kBN, (nbmax + kBM - 1) / kBM, nlist);
     const int n = H.n;
     for (int k = 0; k <= n; ++k) {
       const int store = k > 0, form = k < n;
@@ -398,12 +405,16 @@ template <typename R> struct Factor3Kernels {
       H.launches += 1;
       if (!form) break;
       const int buf = k & 1;
-      for (int c0 = 0; c0 < nbmax; c0 += kPW) {
-        e = cudaLaunchKernelEx(&pc, panel_kernel<R>, P, c0, buf);
-        if (e != cudaSuccess) return e;
-        update_kernel<R><<<ugrid, kUpdThreads, usmem, s>>>(P, c0, buf);
-        rrows_kernel<R><<<rgrid, 8 * RrowsCols<R>::v, 0, s>>>(P, c0, buf);
-        H.launches += 3;
+      for (int C0 = 0; C0 < nbmax; C0 += kKO) {
+        for (int c0 = C0; c0 < std::min(C0 + kKO, nbmax); c0 += kPW) {
+          e = cudaLaunchKernelEx(&pc, panel_kernel<R>, P, c0, C0, buf);
+          if (e != cudaSuccess) return e;
+          update_kernel<R><<<igrid, kUpdThreads, usmem, s>>>(P, C0, c0, buf, 0);
+          H.launches += 2;
+        }
+        gather_kernel<R><<<dim3(kKO, nlist), 256, 0, s>>>(P, C0, buf);
+        update_kernel<R><<<bgrid, kUpdThreads, usmem, s>>>(P, C0, 0, buf, 1);
+        H.launches += 2;
       }
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;

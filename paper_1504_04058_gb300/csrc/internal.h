@@ -127,10 +127,21 @@ struct Slab {
   int src_plane;      // FILL modes: 0-based global x3 plane of the incoming trace
   int src_sweep;      // FILL modes: 1 if the trace includes the sweep field there
   long long woff;     // element offset of block 0 of its factor (n blocks of nb x ld)
-  long long aoff;     // element offset of its two factor-time work matrices
+  long long aoff;     // element offset of its factor-time work area (slab_work_elems)
   long long poff;     // int offset of its pivot tables (3 * nb)
   long long zoff;     // element offset of its solve scratch (n * nb * max_rhs)
 };
+
+// Blocked Gauss-Jordan of the 3D factor: inner panels of kSlabPanel columns
+// inside outer blocks of kSlabOuter columns.  Per slab the factor-time work
+// area holds two nb x ld matrices, the outer block's pivot rows (kSlabOuter x
+// ld) and the inner panel's pivot rows inside the outer block (kSlabPanel x
+// kSlabOuter).
+constexpr int kSlabPanel = 32;
+constexpr int kSlabOuter = 256;
+inline long long slab_work_elems(int nb, int ld) {
+  return 2LL * nb * ld + (long long)kSlabOuter * ld + (long long)kSlabPanel * kSlabOuter;
+}
 
 struct Slab3Params {
   const Slab* slabs;
