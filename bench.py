@@ -39,6 +39,23 @@ WORKLOAD = {"workload": "2d_helmholtz_n1023_layered_omega128pi_pml20_b4_32rhs", 
             "factor_precision": "complex64", "krylov": "FGMRES(40) FP64", "tol": 1e-6,
             "l2": "no flush needed: factors 11.5 GB + transfer maps 4.1 GB exceed the 129 MB L2"}
 PHASES = ["factor", "tmap", "embed", "chain", "fill", "elementwise", "matvec", "krylov"]
+METRIC_3D = "solves/s (3D n=95, omega=48pi, 1 RHS, to 1e-6 FP64 residual)"
+WORKLOAD_3D = {"workload": "3d_helmholtz_n95_bump_omega48pi_pml8_b4_1rhs", "n": 95, "omega": "48*pi", "pml": 8,
+               "b": 4, "nrhs": 1, "velocity": "1 + 0.3 Gaussian bump at the centre",
+               "factor_precision": "complex64", "krylov": "FGMRES(40) FP64", "tol": 1e-6,
+               "l2": "no flush needed: slab factors 76 GB exceed the 129 MB L2"}
+
+
+def algorithmic3d(n, gamma, b):
+    """Algorithmic work of the 3D slab factor: every slab has n dense blocks of
+    size nb = n*w, each inverted by Gauss-Jordan (nb^3 complex multiply-adds =
+    8 nb^3 real flops); an apply reads every stored block twice (forward and
+    backward substitution) in complex64."""
+    m, wM, wR, wL, _ = _layer_widths(n, gamma, b)
+    nbs = [n * w for w in wM + wR + wL]
+    flops = 8.0 * n * sum(nb ** 3 for nb in nbs)
+    w_bytes = 8.0 * n * sum(nb * ((nb + 3) // 4 * 4) for nb in nbs)
+    return {"factor_flops": flops, "factor_bytes": w_bytes, "apply_bytes": 2 * w_bytes}
 
 
 def _peaks():
@@ -159,10 +176,13 @@ def run_asp(args, rank, world):
     restart = 40
     if args.workload == "n1023":
         P = W.problem_2d_n1023_layered(nrhs=32, seed=1504 + rank)
+    elif args.workload == "n95_3d":
+        P = W.problem_3d_n95_bump()
     else:  # smaller case of the same kernels, for profiler captures
         P = W.small_problem(2, 511, 64 * math.pi, 16, 4, "layered", nrhs=32, seed=1504 + rank)
         restart = 16
-    prm = asp.make_params(P.n, P.omega, P.pml, P.b, C=P.C, precision="c64", max_rhs=P.nrhs, restart=restart)
+    prm = asp.make_params(P.n, P.omega, P.pml, P.b, C=P.C, precision="c64", max_rhs=P.nrhs, restart=restart,
+                          dim=P.dim)
     h = asp.asp_setup(P.c, prm)
     f_host = torch.from_numpy(P.f).pin_memory()
     f = f_host.to(dev)
@@ -215,6 +235,15 @@ def run_asp(args, rank, world):
     torch.cuda.synchronize()
     solve_ms = s0.elapsed_time(s1)
 
+    # ---- factor alone (both internal streams joined on the caller's stream)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    h.factor()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    factor_ms = g0.elapsed_time(g1)
+
     # ---- end to end through the public API with host buffers
     u_host = torch.empty_like(f_host).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
@@ -237,36 +266,54 @@ def run_asp(args, rank, world):
 
     # ---- roofline of the dominant kernel (live CUDA-event phase times)
     peaks, peak_kind = _peaks()
-    alg = algorithmic(P.n, P.pml, P.b, P.nrhs, 8)
-    dom = max((p for p in PHASES if p in alg), key=lambda p: phases[p][0])
-    tot_ms, nl = phases[dom]
-    avg_ms = tot_ms / max(nl, 1)
-    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # TFLOP/s at max clock
-    if dom in ("embed", "fill", "tmap", "factor"):
-        ach = alg[dom]["flops"] / (avg_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "kernel": f"btsolve/btfactor ({dom})",
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived, see DESIGN.md)"}
-    else:
-        ach = alg[dom]["bytes"] / (avg_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "kernel": dom, "peak_source": f"hbm_gbs ({peak_kind})"}
-    roof["traffic"] = _traffic_from_profile(dom)
-    roof["avg_launch_ms"] = avg_ms
-    roof["hbm_view"] = {"algorithmic_bytes": alg[dom]["bytes"],
-                        "GBps": alg[dom]["bytes"] / (avg_ms * 1e-3) / 1e9,
-                        "frac_of_measured_hbm": alg[dom]["bytes"] / (avg_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
     phase_ms = {p: round(phases[p][0] / args.steps, 3) for p in PHASES}
     value = world * P.nrhs / (ms * 1e-3)
+    if P.dim == 3:
+        alg3 = algorithmic3d(P.n, P.pml, P.b)
+        ach = alg3["factor_flops"] / (factor_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                "kernel": "3D slab factor (blocked Gauss-Jordan: panel + complex rank-256 update), whole factor",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived, see DESIGN.md)",
+                "traffic": None, "avg_launch_ms": factor_ms,
+                "algorithmic_flops": alg3["factor_flops"]}
+        apply_ms = (phases["embed"][0] + phases["fill"][0]) / max(phases["embed"][1], 1)
+        roof["hbm_view"] = {"kernel": "3D slab solves of one apply", "algorithmic_bytes": alg3["apply_bytes"],
+                            "ms_per_apply": apply_ms,
+                            "GBps": alg3["apply_bytes"] / (apply_ms * 1e-3) / 1e9,
+                            "frac_of_measured_hbm": alg3["apply_bytes"] / (apply_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+        config = dict(WORKLOAD_3D, parallelism=f"replicas x{world}")
+        metric = METRIC_3D
+    else:
+        alg = algorithmic(P.n, P.pml, P.b, P.nrhs, 8)
+        dom = max((p for p in PHASES if p in alg), key=lambda p: phases[p][0])
+        tot_ms, nl = phases[dom]
+        avg_ms = tot_ms / max(nl, 1)
+        if dom in ("embed", "fill", "tmap", "factor"):
+            ach = alg[dom]["flops"] / (avg_ms * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp32_peak, "kernel": f"btsolve/btfactor ({dom})",
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived, see DESIGN.md)"}
+        else:
+            ach = alg[dom]["bytes"] / (avg_ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "kernel": dom, "peak_source": f"hbm_gbs ({peak_kind})"}
+        roof["traffic"] = _traffic_from_profile(dom)
+        roof["avg_launch_ms"] = avg_ms
+        roof["hbm_view"] = {"algorithmic_bytes": alg[dom]["bytes"],
+                            "GBps": alg[dom]["bytes"] / (avg_ms * 1e-3) / 1e9,
+                            "frac_of_measured_hbm": alg[dom]["bytes"] / (avg_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+        config = (dict(WORKLOAD, parallelism=f"replicas x{world}") if args.workload == "n1023" else
+                  {"workload": "2d_helmholtz_n511_layered_omega64pi_pml16_b4_32rhs (profiling case)"})
+        metric = METRIC
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64 factors / f64 krylov", "data": "synthetic",
-        "config": dict(WORKLOAD, parallelism=f"replicas x{world}") if args.workload == "n1023" else
-        {"workload": "2d_helmholtz_n511_layered_omega64pi_pml16_b4_32rhs (profiling case)"},
+        "config": config,
         "iterations_max": max(its), "converged": conv, "worst_rel_res_true": worst_res,
         "solve_only_solves_per_s": world * P.nrhs / (solve_ms * 1e-3),
+        "factor_ms": factor_ms,
         "phase_ms_per_step": phase_ms,
         "e2e": {"value": world * P.nrhs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms},
@@ -365,8 +412,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["asp", "reference"], default="asp")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["n1023", "n511x32"], default="n1023",
-                    help="n511x32: the same kernels on a 2D n=511 problem with 32 RHS (profiling)")
+    ap.add_argument("--workload", choices=["n1023", "n511x32", "n95_3d"], default="n1023",
+                    help="n511x32: the same kernels on a 2D n=511 problem with 32 RHS (profiling); "
+                         "n95_3d: the 3D slab path on the n=95 bump problem (1 RHS)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -384,7 +432,11 @@ def main():
         torch.distributed.barrier()
     line = run_asp(args, rank, world)
     if rank == 0:
-        if not args.no_cpu_baseline:
+        if args.workload == "n95_3d":
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "not run: one banded LU of a single 95^3 slab subproblem "
+                                              "(162450 rows, half-bandwidth 1710) is minutes of CPU work"}
+        elif not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample(line["iterations_max"])
         print(json.dumps(line), flush=True)
     if world > 1:

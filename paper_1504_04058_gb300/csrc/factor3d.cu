@@ -120,7 +120,15 @@ __global__ void __launch_bounds__(256) form_store_kernel(Slab3Params P, FactorCo
 
 // ------------------------------------------------------------------- panel
 // Grid (CL, nlist) with clusters of CL CTAs along x: CTA rank q holds rows
-// [q*rpc, (q+1)*rpc) of the panel in shared memory.
+// [q*rpc, (q+1)*rpc) of the panel in shared memory; warp w owns the local rows
+// w, w + kPanelWarps, ... for both the pivot search and the updates, so within a
+// step only the CTA-wide candidate reduction needs a block barrier.  Per step
+// every CTA pushes its pivot candidate (|value|^2, row, and the row's kPW
+// entries) into a slot of every CTA of the cluster (distributed shared memory,
+// slots double-buffered by step parity); after one cluster barrier each CTA
+// picks the same winner from its own slots and applies the step to its rows.
+constexpr int kMaxCluster = 8;
+
 template <typename R>
 __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, int c0, int C0, int buf) {
   using C = Cx<R>;
@@ -136,11 +144,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
   const int row0 = q * rpc;
   const int nrows = max(0, min(nb, row0 + rpc) - row0);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* Ps = reinterpret_cast<C*>(smem_raw);                    // [rpc][kLDP]
+  C* Ps = reinterpret_cast<C*>(smem_raw);                        // [rpc][kLDP]
   int* rstep = reinterpret_cast<int*>(Ps + (size_t)rpc * kLDP);  // [rpc]
-  __shared__ C prow[kPW];
-  __shared__ R candv[2];
-  __shared__ int candr[2];
+  __shared__ C slot_row[2][kMaxCluster][kPW];
+  __shared__ R slot_val[2][kMaxCluster];
+  __shared__ int slot_idx[2][kMaxCluster];
   __shared__ R wbest[kPanelWarps];
   __shared__ int wrow[kPanelWarps];
   __shared__ int pivs[kPW];
@@ -160,14 +168,15 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
   bool bad = false;
   for (int t = 0; t < pw; ++t) {
     const int c = c0 + t;
-    // ---- pivot candidate of this CTA: largest |A[i][c]| over rows not yet pivots
+    const int par = t & 1;
+    // ---- candidate of this warp's rows: largest |A[i][c]| over rows not yet pivots
     R best = R(-1);
     int bi = INT_MAX;
-    for (int l = tid; l < nrows; l += kPanelThreads) {
+    for (int l = warp + kPanelWarps * lane; l < nrows; l += kPanelWarps * 32) {
       if (rstep[l] < 0) {
         const C v = Ps[l * kLDP + t];
         const R a = v.x * v.x + v.y * v.y;
-        if (a > best) { best = a; bi = row0 + l; }  // rows ascend with l: ties keep the first
+        if (a > best) { best = a; bi = row0 + l; }  // rows ascend along a lane: ties keep the first
       }
     }
 #pragma unroll
@@ -187,30 +196,30 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
         const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (lane == 0) { candv[t & 1] = best; candr[t & 1] = bi; }
+      const bool have = bi >= row0 && bi < row0 + nrows;
+      const C rv = (have && lane < pw) ? Ps[(bi - row0) * kLDP + lane] : czero<R>();
+      for (int d = 0; d < CL; ++d) {
+        cluster.map_shared_rank(&slot_row[par][q][0], d)[lane] = rv;
+        if (lane == 0) {
+          *cluster.map_shared_rank(&slot_val[par][q], d) = best;
+          *cluster.map_shared_rank(&slot_idx[par][q], d) = bi;
+        }
+      }
     }
     cluster.sync();
-    // ---- the cluster's pivot (every thread computes the same choice)
+    // ---- the cluster's pivot, from this CTA's own slots (same choice everywhere)
     R gb = R(-1);
-    int gr = INT_MAX;
+    int gr = INT_MAX, gq = 0;
     for (int r = 0; r < CL; ++r) {
-      const R a = *cluster.map_shared_rank(&candv[t & 1], r);
-      const int ri = *cluster.map_shared_rank(&candr[t & 1], r);
-      if (a > gb || (a == gb && ri < gr)) { gb = a; gr = ri; }
+      const R a = slot_val[par][r];
+      const int ri = slot_idx[par][r];
+      if (a > gb || (a == gb && ri < gr)) { gb = a; gr = ri; gq = r; }
     }
     const bool okp = gr >= 0 && gr < nb;
     if (!(gb > R(0)) || !isfinite(gb)) bad = true;
-    const int owner = okp ? gr / rpc : 0;
-    const int lr = okp ? gr - owner * rpc : 0;
-    if (tid < kPW) {
-      C v = czero<R>();
-      if (okp && tid < pw) v = cluster.map_shared_rank(Ps, owner)[lr * kLDP + tid];
-      prow[tid] = v;
-    }
-    cluster.sync();  // every CTA holds the pivot row before its owner rewrites it
     if (okp) {
-      const C inv = crecip(prow[t]);
-      const C pl = prow[lane];
+      const C pl = slot_row[par][gq][lane];
+      const C inv = crecip(slot_row[par][gq][t]);
       for (int l = warp; l < nrows; l += kPanelWarps) {
         C* rowp = Ps + l * kLDP;
         C v;
@@ -229,16 +238,17 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
         }
         __syncwarp();
         if (lane < pw) rowp[lane] = v;
+        if (row0 + l == gr && lane == 0) rstep[l] = c;  // set by the warp that owns the row
       }
-      if (tid == 0 && q == owner) rstep[lr] = c;
       if (tid == 0 && q == 0) {
         piv_row[c] = gr;
         col_of_row[gr] = c;
       }
     }
     if (tid == 0) pivs[t] = okp ? gr : 0;
-    __syncthreads();
+    __syncwarp();
   }
+  __syncthreads();
   for (int e = tid; e < nrows * pw; e += kPanelThreads) {
     const int l = e / pw, t = e - l * pw;
     A[(long long)(row0 + l) * ld + c0 + t] = Ps[l * kLDP + t];
@@ -368,11 +378,11 @@ template <typename R> struct Factor3Kernels {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t static_bytes = 4096;
+    const size_t static_bytes = 12288;  // the kernel's static shared arrays, with room
     const int rows_cap = (int)(((size_t)optin - static_bytes) / (kLDP * esz + sizeof(int)));
     int CL = (nbmax + rows_cap - 1) / rows_cap;
     if (CL < 1) CL = 1;
-    if (CL > 8) return cudaErrorInvalidValue;
+    if (CL > kMaxCluster) return cudaErrorInvalidValue;
     const int rpc = (nbmax + CL - 1) / CL;
     const size_t psmem = (size_t)rpc * (kLDP * esz + sizeof(int));
     cudaError_t e = cudaFuncSetAttribute(panel_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
