@@ -104,7 +104,7 @@ double2 hadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); 
 struct Sizes {
   int m = 0, wmax = 0, wmaxRL = 0, nsub = 0;
   size_t W_elems = 0, tmap_elems = 0, coef = 0;
-  size_t A_elems = 0, piv_elems = 0, z3_elems = 0;  // 3D
+  size_t A_elems = 0, piv_elems = 0, z3_elems = 0, tc_floats = 0;  // 3D
   int nbmaxM = 0, nbmaxRL = 0;                       // 3D
   size_t esz = 0;
   long long N = 0;
@@ -199,9 +199,12 @@ Sizes sizes_for3(const asp_params* p, int num_sms) {
     else Z.nbmaxM = std::max(Z.nbmaxM, nb);
     Z.nsub++;
   };
-  for (int q = 1; q <= P.m; ++q) addslab(P.m_lo[q], P.m_hi[q], false);
-  for (int q = 2; q <= P.m; ++q) addslab(P.alpha[q], P.m_hi[q], true);
-  for (int q = 1; q <= P.m - 1; ++q) addslab(P.m_lo[q], P.beta[q], true);
+  long long tc_rows_M = 0, tc_rows_RL = 0;
+  auto padr = [&](int lo, int hi) { return (long long)((n * (hi - lo + 1) + 127) / 128 * 128); };
+  for (int q = 1; q <= P.m; ++q) { addslab(P.m_lo[q], P.m_hi[q], false); tc_rows_M += padr(P.m_lo[q], P.m_hi[q]); }
+  for (int q = 2; q <= P.m; ++q) { addslab(P.alpha[q], P.m_hi[q], true); tc_rows_RL += padr(P.alpha[q], P.m_hi[q]); }
+  for (int q = 1; q <= P.m - 1; ++q) { addslab(P.m_lo[q], P.beta[q], true); tc_rows_RL += padr(P.m_lo[q], P.beta[q]); }
+  if (p->factor_prec == ASP_PREC_C64) Z.tc_floats = tc_group_floats(tc_rows_M) + tc_group_floats(tc_rows_RL);
   const long long R = p->restart;
   size_t n2, nd, ni;
   const size_t kst = krylov_state_bytes(p->restart, p->max_rhs, &n2, &nd, &ni);
@@ -210,6 +213,7 @@ Sizes sizes_for3(const asp_params* p, int num_sms) {
   bytes += Z.N * (sizeof(double) + rsz) + 3 * (size_t)n * (sizeof(double2) + Z.esz);  // k2, ca, cc, cd (both)
   bytes += Z.coef * (sizeof(SweepCoef) + 3 * Z.esz) + Z.nsub * sizeof(Slab) + Z.nsub * sizeof(int);
   bytes += (Z.W_elems + Z.A_elems + Z.z3_elems) * Z.esz + Z.piv_elems * sizeof(int);
+  bytes += Z.tc_floats * sizeof(float);
   bytes += (size_t)Z.N * mr * Z.esz * (3 + (Z.esz == 8 ? 1 : 0));                 // uM uR uL (+ r_lo)
   bytes += (size_t)(2 * R + 2) * Z.N * mr * sizeof(double2);                        // V, Z, work
   bytes += (size_t)num_sms * 4 * 9 * mr * sizeof(double2);                          // dot partials
@@ -584,9 +588,11 @@ void asp_destroy(asp_handle* hd) {
     caches().erase(&H);
   }
   release_jobs3(&H);
+  tc_group_release(H.tcM);
+  tc_group_release(H.tcRL);
   void* ptrs[] = {H.k2, H.ca, H.cc, H.cd, H.d_subs, H.d_coef, H.W, H.tmap, H.d_toffR, H.d_toffL, H.r_lo,
                   H.uM, H.uR, H.uL, H.accR, H.accL, H.zscr, H.bar, H.V, H.Z, H.wv, H.red, H.hess, H.kstate,
-                  H.kflags, H.err, H.d_slabs, H.d_slab_lists, H.A3, H.piv3, H.z3};
+                  H.kflags, H.err, H.d_slabs, H.d_slab_lists, H.A3, H.piv3, H.z3, H.tc_area};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : H.coef_bufs)
@@ -778,6 +784,7 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
     dal(&H.A3, (size_t)aoff * esz);
     dal((void**)&H.piv3, (size_t)poff * sizeof(int));
     dal(&H.z3, (size_t)zoff * esz);
+    if (H.prec == ASP_PREC_C64) dal((void**)&H.tc_area, Z.tc_floats * sizeof(float));
   }
   if (H.prec == ASP_PREC_C64) dal(&H.r_lo, (size_t)N * mr * esz);
   dal(&H.uM, (size_t)N * mr * esz);
@@ -822,6 +829,24 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
     for (size_t i = 0; i < lists.size(); ++i) lists[i] = (int)i;  // [M slabs | R slabs, L slabs]
     cp(H.d_slabs, H.slabs.data(), H.slabs.size() * sizeof(Slab));
     cp(H.d_slab_lists, lists.data(), lists.size() * sizeof(int));
+    if (up && H.prec == ASP_PREC_C64) {
+      // operand rows of the tensor-core update, per group in list order
+      std::vector<long long> rM, rRL;
+      long long nM = 0, nRL = 0;
+      for (size_t i = 0; i < H.slabs.size(); ++i) {
+        const long long pad = (H.slabs[i].nb + 127) / 128 * 128;
+        if ((int)i < m) { rM.push_back(nM); nM += pad; }
+        else { rRL.push_back(nRL); nRL += pad; }
+      }
+      int rc = ASP_OK;  // an empty group (m = 1 has no R/L slabs) needs no operand area
+      if (nM > 0) rc = tc_group_setup(H.tcM, H.tc_area, rM, nM);
+      if (rc == ASP_OK && nRL > 0) rc = tc_group_setup(H.tcRL, H.tc_area + tc_group_floats(nM), rRL, nRL);
+      if (rc != ASP_OK) {
+        const std::string why = asp_last_error_detail();
+        asp_destroy(hd);
+        return fail(rc, why);
+      }
+    }
   }
   // factor-precision copies of the layer coefficients
   {

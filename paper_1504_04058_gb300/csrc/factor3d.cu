@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(Slab3Params P, int 
 // ------------------------------------------------------------------ driver
 template <typename R> struct Factor3Kernels {
   static cudaError_t run_group(Handle& H, const FactorCoefs<R>& F, const int* d_list, int nlist, int nbmax,
-                               cudaStream_t s) {
+                               const TcGroup* tc, cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
     Slab3Params P{};
     P.slabs = H.d_slabs;
@@ -422,8 +422,13 @@ template <typename R> struct Factor3Kernels {
           update_kernel<R><<<igrid, kUpdThreads, usmem, s>>>(P, C0, c0, buf, 0);
           H.launches += 2;
         }
-        gather_kernel<R><<<dim3(kKO, nlist), 256, 0, s>>>(P, C0, buf);
-        update_kernel<R><<<bgrid, kUpdThreads, usmem, s>>>(P, C0, 0, buf, 1);
+        if (tc) {  // complex64: split-precision TF32 product on the tensor cores
+          e = launch_tc_update(*tc, P, nbmax, C0, buf, s);
+          if (e != cudaSuccess) return e;
+        } else {
+          gather_kernel<R><<<dim3(kKO, nlist), 256, 0, s>>>(P, C0, buf);
+          update_kernel<R><<<bgrid, kUpdThreads, usmem, s>>>(P, C0, 0, buf, 1);
+        }
         H.launches += 2;
       }
       e = cudaGetLastError();
@@ -445,15 +450,15 @@ int factor3d(Handle& H, cudaStream_t s) {
   cudaError_t ea, eb;
   PhaseTok ta = phase_begin(H, PH_FACTOR, H.aux);
   if (H.prec == ASP_PREC_C128)
-    ea = Factor3Kernels<double>::run_group(H, H.fc64, H.d_slab_lists, nM, H.nbmaxM, H.aux);
+    ea = Factor3Kernels<double>::run_group(H, H.fc64, H.d_slab_lists, nM, H.nbmaxM, nullptr, H.aux);
   else
-    ea = Factor3Kernels<float>::run_group(H, H.fc32, H.d_slab_lists, nM, H.nbmaxM, H.aux);
+    ea = Factor3Kernels<float>::run_group(H, H.fc32, H.d_slab_lists, nM, H.nbmaxM, &H.tcM, H.aux);
   phase_end(H, ta, H.aux);
   PhaseTok tb = phase_begin(H, PH_FACTOR, s);
   if (H.prec == ASP_PREC_C128)
-    eb = Factor3Kernels<double>::run_group(H, H.fc64, H.d_slab_lists + nM, nRL, H.nbmaxRL, s);
+    eb = Factor3Kernels<double>::run_group(H, H.fc64, H.d_slab_lists + nM, nRL, H.nbmaxRL, nullptr, s);
   else
-    eb = Factor3Kernels<float>::run_group(H, H.fc32, H.d_slab_lists + nM, nRL, H.nbmaxRL, s);
+    eb = Factor3Kernels<float>::run_group(H, H.fc32, H.d_slab_lists + nM, nRL, H.nbmaxRL, &H.tcRL, s);
   phase_end(H, tb, s);
   if (cudaEventRecord(H.ev_join, H.aux) != cudaSuccess || cudaStreamWaitEvent(s, H.ev_join, 0) != cudaSuccess)
     return fail(ASP_ERR_CUDA, "factor: stream join");

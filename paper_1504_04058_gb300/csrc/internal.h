@@ -154,6 +154,17 @@ struct Slab3Params {
   int* err;
 };
 
+// Operand area and tensor maps of the tensor-core update (tcupdate.cu) for
+// one slab group.
+struct TcGroup {
+  float* ahi = nullptr;
+  float* alo = nullptr;
+  float* bhi = nullptr;
+  float* blo = nullptr;
+  void* maps = nullptr;        // host copy of the four CUtensorMaps
+  long long* rowA = nullptr;   // device: first operand row of each slab of the group list
+};
+
 struct Solve3Job {
   int slab, mode, rhs0, nr;
   int item0;          // first work item of this job (prefix over the launch)
@@ -210,6 +221,10 @@ int factor3d(Handle& H, cudaStream_t s);
 int apply3d(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_t s);
 int subsolve3d(Handle& H, int slab, const double2* g, double2* v, int nrhs, cudaStream_t s);
 void release_jobs3(const Handle* H);
+long long tc_group_floats(long long rows);
+int tc_group_setup(TcGroup& G, float* area, const std::vector<long long>& rowA_host, long long rows);
+void tc_group_release(TcGroup& G);
+cudaError_t launch_tc_update(const TcGroup& G, const Slab3Params& P, int nbmax, int C0, int buf, cudaStream_t s);
 
 // ---- handle ----
 struct Handle {
@@ -297,6 +312,8 @@ struct Handle {
   void* A3 = nullptr;           // factor-time work matrices
   int* piv3 = nullptr;
   void* z3 = nullptr;           // solve scratch
+  float* tc_area = nullptr;     // tensor-core update operands (complex64 factors)
+  TcGroup tcM, tcRL;
 
   // second stream for work that overlaps the caller's stream (factor time)
   cudaStream_t aux = nullptr;

@@ -29,6 +29,7 @@ SMALL3 = {
     "two_layers": (13, 3 * math.pi, 3, 4, "bump", 1, None),       # m = 2
     "five_rhs": (13, 3 * math.pi, 3, 3, "lens", 5, None),         # right-hand sides 4 + 1
     "thin_aux": (17, 4 * math.pi, 4, 3, "bump", 2, 2),            # auxiliary PML of 2 points
+    "wide_blocks": (25, 4 * math.pi, 3, 10, "bump", 2, None),     # blocks of 350 / 300: two outer blocks
 }
 
 
@@ -84,7 +85,7 @@ def test_matvec3d_matches_oracle(name):
 
 
 @pytest.mark.parametrize("precision,tol", [("c128", 1e-11), ("c64", 2e-4)])
-@pytest.mark.parametrize("name", ["ragged_bump", "two_layers", "thin_aux"])
+@pytest.mark.parametrize("name", ["ragged_bump", "two_layers", "thin_aux", "wide_blocks"])
 def test_slab_solves_match_oracle(name, precision, tol):
     """Every slab: GPU block-inverse solve vs the oracle's banded LU."""
     import paper_1504_04058_gb300 as asp
