@@ -220,26 +220,33 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
     if (okp) {
       const C pl = slot_row[par][gq][lane];
       const C inv = crecip(slot_row[par][gq][t]);
-      for (int l = warp; l < nrows; l += kPanelWarps) {
-        C* rowp = Ps + l * kLDP;
-        C v;
-        if (row0 + l == gr) {
-          v = (lane == t) ? inv : cmul(pl, inv);
-        } else {
-          const C f = cmul(rowp[t], inv);
-          v = rowp[lane];
-          if (lane == t) {
-            v = f;
-            v.x = -v.x;
-            v.y = -v.y;
-          } else {
-            cfms(v, f, pl);
+      const C pscaled = (lane == t) ? inv : cmul(pl, inv);  // the pivot row's new entries
+      const int lg = gr - row0;                               // local index of the pivot row (if here)
+      // four rows per pass: all reads, one warp barrier, then all writes (lane t
+      // overwrites the column the other lanes read)
+      for (int l0 = warp; l0 < nrows; l0 += 4 * kPanelWarps) {
+        C v[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int l = l0 + a * kPanelWarps;
+          if (l < nrows) {
+            const C* rowp = Ps + l * kLDP;
+            const C f = cmul(rowp[t], inv);
+            C x = rowp[lane];
+            cfms(x, f, pl);
+            if (lane == t) { x.x = -f.x; x.y = -f.y; }
+            v[a] = (l == lg) ? pscaled : x;
           }
         }
         __syncwarp();
-        if (lane < pw) rowp[lane] = v;
-        if (row0 + l == gr && lane == 0) rstep[l] = c;  // set by the warp that owns the row
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int l = l0 + a * kPanelWarps;
+          if (l < nrows && lane < pw) Ps[l * kLDP + lane] = v[a];
+        }
+        __syncwarp();
       }
+      if (lg >= 0 && lg < nrows && (lg % kPanelWarps) == warp && lane == 0) rstep[lg] = c;
       if (tid == 0 && q == 0) {
         piv_row[c] = gr;
         col_of_row[gr] = c;
@@ -380,7 +387,13 @@ template <typename R> struct Factor3Kernels {
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t static_bytes = 12288;  // the kernel's static shared arrays, with room
     const int rows_cap = (int)(((size_t)optin - static_bytes) / (kLDP * esz + sizeof(int)));
-    int CL = (nbmax + rows_cap - 1) / rows_cap;
+    // about 512 rows per CTA (the per-step row updates are issue-bound) while
+    // all clusters of the group fit in one wave, and at least as many CTAs as
+    // shared memory requires
+    // (one CTA per SM: all clusters of the group in a single wave)
+    const int by_rows = std::min(kMaxCluster, (nbmax + 511) / 512);
+    const int by_sms = std::max(1, H.num_sms / std::max(nlist, 1));
+    int CL = std::max((nbmax + rows_cap - 1) / rows_cap, std::min(by_rows, by_sms));
     if (CL < 1) CL = 1;
     if (CL > kMaxCluster) return cudaErrorInvalidValue;
     const int rpc = (nbmax + CL - 1) / CL;
