@@ -36,7 +36,7 @@ EXPORTS = [
 ]
 NOALLOC_MAX_N = 4096
 NOALLOC_MAX_RHS = 64
-PHASES = ["factor", "tmap", "embed", "chain", "fill", "elementwise", "matvec", "krylov"]
+PHASES = ["factor", "tmap", "embed", "chain", "fill", "elementwise", "matvec", "krylov", "schur3d"]
 
 
 class asp_params(ctypes.Structure):

@@ -436,7 +436,9 @@ template <typename R> struct Factor3Kernels {
           H.launches += 2;
         }
         if (tc) {  // complex64: split-precision TF32 product on the tensor cores
+          PhaseTok ts = phase_begin(H, PH_SCHUR, s);
           e = launch_tc_update(*tc, P, nbmax, C0, buf, s);
+          phase_end(H, ts, s);
           if (e != cudaSuccess) return e;
         } else {
           gather_kernel<R><<<dim3(kKO, nlist), 256, 0, s>>>(P, C0, buf);

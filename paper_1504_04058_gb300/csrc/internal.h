@@ -194,7 +194,7 @@ struct Handle;
 
 enum Phase : int {
   PH_FACTOR = 0, PH_TMAP = 1, PH_EMBED = 2, PH_CHAIN = 3, PH_FILL = 4, PH_SUM = 5, PH_MATVEC = 6,
-  PH_KRYLOV = 7, PH_COUNT = 8
+  PH_KRYLOV = 7, PH_SCHUR = 8, PH_COUNT = 9
 };
 
 // Records CUDA events around launches when phase timing is enabled.
