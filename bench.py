@@ -186,6 +186,8 @@ def run_asp(args, rank, world):
         P = W.problem_2d_n1023_layered(nrhs=32, seed=1504 + rank)
     elif args.workload == "n95_3d":
         P = W.problem_3d_n95_bump()
+    elif args.workload == "n47_3d_slab":  # one 3D slab (m = 1), blocks of 47*47 unknowns: profiling case
+        P = W.small_problem(3, 47, 12 * math.pi, 6, 37, "bump", nrhs=1)
     else:  # smaller case of the same kernels, for profiler captures
         P = W.small_problem(2, 511, 64 * math.pi, 16, 4, "layered", nrhs=32, seed=1504 + rank)
         restart = 16
@@ -299,7 +301,8 @@ def run_asp(args, rank, world):
                             "ms_per_apply": apply_ms,
                             "GBps": alg3["apply_bytes"] / (apply_ms * 1e-3) / 1e9,
                             "frac_of_measured_hbm": alg3["apply_bytes"] / (apply_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
-        config = dict(WORKLOAD_3D, parallelism=f"replicas x{world}")
+        config = (dict(WORKLOAD_3D, parallelism=f"replicas x{world}") if args.workload == "n95_3d" else
+                  {"workload": "3d_helmholtz_n47_one_slab_omega12pi_pml6_b37 (profiling case)"})
         metric = METRIC_3D
     else:
         alg = algorithmic(P.n, P.pml, P.b, P.nrhs, 8)
@@ -429,9 +432,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["asp", "reference"], default="asp")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["n1023", "n511x32", "n95_3d"], default="n1023",
+    ap.add_argument("--workload", choices=["n1023", "n511x32", "n95_3d", "n47_3d_slab"], default="n1023",
                     help="n511x32: the same kernels on a 2D n=511 problem with 32 RHS (profiling); "
-                         "n95_3d: the 3D slab path on the n=95 bump problem (1 RHS)")
+                         "n95_3d: the 3D slab path on the n=95 bump problem (1 RHS); "
+                         "n47_3d_slab: one 3D slab with 2209-unknown blocks, 2.1 GB (profiling)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -449,7 +453,7 @@ def main():
         torch.distributed.barrier()
     line = run_asp(args, rank, world)
     if rank == 0:
-        if args.workload == "n95_3d":
+        if args.workload in ("n95_3d", "n47_3d_slab"):
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": "not run: one banded LU of a single 95^3 slab subproblem "
                                               "(162450 rows, half-bandwidth 1710) is minutes of CPU work"}
