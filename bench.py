@@ -191,8 +191,9 @@ def run_asp(args, rank, world):
     else:  # smaller case of the same kernels, for profiler captures
         P = W.small_problem(2, 511, 64 * math.pi, 16, 4, "layered", nrhs=32, seed=1504 + rank)
         restart = 16
-    prm = asp.make_params(P.n, P.omega, P.pml, P.b, C=P.C, precision="c64", max_rhs=P.nrhs, restart=restart,
-                          dim=P.dim)
+    pml_aux = args.pml_aux if args.pml_aux else (P.pml_aux or 0)
+    prm = asp.make_params(P.n, P.omega, P.pml, P.b, pml_aux=pml_aux, C=P.C, precision="c64", max_rhs=P.nrhs,
+                          restart=restart, dim=P.dim)
     h = asp.asp_setup(P.c, prm)
     f_host = torch.from_numpy(P.f).pin_memory()
     f = f_host.to(dev)
@@ -326,6 +327,9 @@ def run_asp(args, rank, world):
         config = (dict(WORKLOAD, parallelism=f"replicas x{world}") if args.workload == "n1023" else
                   {"workload": "2d_helmholtz_n511_layered_omega64pi_pml16_b4_32rhs (profiling case)"})
         metric = METRIC
+    if args.pml_aux:
+        config = dict(config, pml_aux=args.pml_aux,
+                      variant="thinner auxiliary PML inside the domain (the boundary PML keeps its width)")
     line = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -432,6 +436,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["asp", "reference"], default="asp")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pml-aux", type=int, default=0,
+                    help="width of the auxiliary PMLs between layers (default: the boundary PML width)")
     ap.add_argument("--workload", choices=["n1023", "n511x32", "n95_3d", "n47_3d_slab"], default="n1023",
                     help="n511x32: the same kernels on a 2D n=511 problem with 32 RHS (profiling); "
                          "n95_3d: the 3D slab path on the n=95 bump problem (1 RHS); "
