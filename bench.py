@@ -183,7 +183,7 @@ def run_asp(args, rank, world):
     torch.cuda.set_device(dev)
     restart = 40
     if args.workload == "n1023":
-        P = W.problem_2d_n1023_layered(nrhs=32, seed=1504 + rank)
+        P = W.problem_2d_n1023_layered(nrhs=32, seed=1504 + rank, source=args.source)
     elif args.workload == "n95_3d":
         P = W.problem_3d_n95_bump()
     elif args.workload == "n47_3d_slab":  # one 3D slab (m = 1), blocks of 47*47 unknowns: profiling case
@@ -327,6 +327,8 @@ def run_asp(args, rank, world):
         config = (dict(WORKLOAD, parallelism=f"replicas x{world}") if args.workload == "n1023" else
                   {"workload": "2d_helmholtz_n511_layered_omega64pi_pml16_b4_32rhs (profiling case)"})
         metric = METRIC
+    if args.source == "packet":
+        config = dict(config, sources="Gaussian wave packets, one wavelength wide, seeded centres and directions")
     if args.pml_aux:
         config = dict(config, pml_aux=args.pml_aux,
                       variant="thinner auxiliary PML inside the domain (the boundary PML keeps its width)")
@@ -436,6 +438,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["asp", "reference"], default="asp")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--source", choices=["point", "packet"], default="point",
+                    help="right-hand sides of the n=1023 workload: Gaussian point sources or wave packets")
     ap.add_argument("--pml-aux", type=int, default=0,
                     help="width of the auxiliary PMLs between layers (default: the boundary PML width)")
     ap.add_argument("--workload", choices=["n1023", "n511x32", "n95_3d", "n47_3d_slab"], default="n1023",

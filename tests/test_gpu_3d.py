@@ -180,3 +180,10 @@ def test_3d_n95_workload_properties():
     fr = P.f[..., 0].reshape(-1)
     assert info[0]["converged"]
     assert np.linalg.norm(fr - A @ u[..., 0].reshape(-1)) / np.linalg.norm(fr) <= P.tol
+
+
+def test_apply3d_wave_packet_sources():
+    P = W.small_problem(3, 19, 4 * math.pi, 3, 3, "bump", nrhs=2, source="packet")
+    h = handle3(P, "c128")
+    z = host(h.apply_preconditioner(dev(P.f)))
+    assert rel(z, oracle_pc3(P).apply(P.f)) <= 1e-10

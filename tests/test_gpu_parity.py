@@ -274,3 +274,27 @@ def test_invalid_calls_raise():
         h.matvec(dev(np.zeros((P.n + 1, P.n, 1))))
     with pytest.raises(asp.AspError):
         h.subproblem_width(asp.KIND_R, 1)  # no H_1^R
+
+
+# ------------------------------------------------- wave-packet sources (NEXT-3)
+
+def test_wave_packet_sources_match_oracle():
+    """The paper's second force family: Gaussian wave packets (complex sources
+    with a travelling phase).  Apply and FGMRES parity as for point sources."""
+    P = W.small_problem(2, 63, 8 * math.pi, 8, 4, "lens", nrhs=2, source="packet")
+    h = handle(P, "c128")
+    z = host(h.apply_preconditioner(dev(P.f)))
+    assert rel(z, oracle_pc(P).apply(P.f)) <= 1e-10
+    (uo, itso, _), A = _oracle_solve(P)
+    ug, info = h.gmres_solve(dev(P.f), tol=P.tol, maxit=200)
+    u = host(ug)
+    for r in range(P.nrhs):
+        assert abs(info[r]["iterations"] - int(itso[r])) <= 1, (info[r], itso[r])
+        fr = P.f[..., r].reshape(-1)
+        assert np.linalg.norm(fr - A @ u[..., r].reshape(-1)) / np.linalg.norm(fr) <= P.tol
+    h64 = handle(P, "c64")
+    ug, info = h64.gmres_solve(dev(P.f), tol=P.tol, maxit=200)
+    u = host(ug)
+    for r in range(P.nrhs):
+        fr = P.f[..., r].reshape(-1)
+        assert np.linalg.norm(fr - A @ u[..., r].reshape(-1)) / np.linalg.norm(fr) <= P.tol

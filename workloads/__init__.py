@@ -103,6 +103,26 @@ def gaussian_source(n: int, dim: int, centre, width: float) -> np.ndarray:
     return np.exp(-r2 / (2.0 * width * width))
 
 
+def wave_packet(n: int, dim: int, centre, direction, omega: float, c_typ: float = 1.0,
+                width: float | None = None) -> np.ndarray:
+    """Gaussian wave packet (the paper's second force family, Section 3.2/4.2):
+    envelope exp(-|x - centre|^2 / (2 s^2)) times the plane wave
+    exp(i k d.(x - centre)) with k = omega / c_typ and unit direction d.  The
+    paper gives no envelope width; s defaults to one wavelength 2 pi / k."""
+    k = omega / c_typ
+    s = width if width is not None else 2.0 * math.pi / k
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    xs = grid_nodes(n, dim)
+    r2 = np.zeros((n,) * dim, dtype=np.float64)
+    phase = np.zeros((n,) * dim, dtype=np.float64)
+    for ax in range(dim):
+        dx = xs[ax] - centre[ax]
+        r2 = r2 + dx * dx
+        phase = phase + d[ax] * dx
+    return np.exp(-r2 / (2.0 * s * s)) * np.exp(1j * k * phase)
+
+
 def constant_velocity(n: int, dim: int, value: float = 1.0) -> np.ndarray:
     return np.full((n,) * dim, value, dtype=np.float64)
 
@@ -172,19 +192,28 @@ def problem_2d_n511_lens() -> Problem:
                    lens_velocity(n, 2), _stack([f]))
 
 
-def problem_2d_n1023_layered(nrhs: int = 32, seed: int = 1504) -> Problem:
+def problem_2d_n1023_layered(nrhs: int = 32, seed: int = 1504, source: str = "point") -> Problem:
     """2D n=1023, omega=128*pi, 16 random smoothed horizontal layers, PML 20,
-    b=4, ``nrhs`` Gaussian sources (width 2h) at seeded positions drawn
-    uniformly from the physical square [gamma*h, 1-gamma*h]^2."""
+    b=4, ``nrhs`` sources at seeded positions drawn uniformly from the physical
+    square [gamma*h, 1-gamma*h]^2: Gaussian point sources of width 2h
+    (``source="point"``) or Gaussian wave packets of one wavelength with seeded
+    directions (``source="packet"``)."""
     n, gamma = 1023, 20
     h = 1.0 / (n + 1)
+    omega = 128 * math.pi
     c = layered_velocity(n, seed, dim=2)
     rng = np.random.default_rng(seed + 1)
     lo, hi = gamma * h, 1.0 - gamma * h
     pos = rng.uniform(lo, hi, size=(nrhs, 2))
-    fs = [gaussian_source(n, 2, tuple(p), 2 * h) for p in pos]
-    return Problem("2d_n1023_layered", 2, n, 128 * math.pi, gamma, 4, c, _stack(fs),
-                   seed=seed)
+    if source == "point":
+        fs = [gaussian_source(n, 2, tuple(p), 2 * h) for p in pos]
+    elif source == "packet":
+        ang = rng.uniform(0.0, 2.0 * math.pi, size=nrhs)
+        fs = [wave_packet(n, 2, tuple(p), (math.cos(a), math.sin(a)), omega) for p, a in zip(pos, ang)]
+    else:
+        raise ValueError(source)
+    return Problem("2d_n1023_layered" + ("" if source == "point" else "_packets"), 2, n, omega, gamma, 4, c,
+                   _stack(fs), seed=seed)
 
 
 def problem_3d_n95_bump() -> Problem:
@@ -198,7 +227,7 @@ def problem_3d_n95_bump() -> Problem:
 
 def small_problem(dim: int, n: int, omega: float, pml: int, b: int, velocity: str = "const",
                   nrhs: int = 1, seed: int = 7, pml_aux: int | None = None,
-                  C: float = 20.0) -> Problem:
+                  C: float = 20.0, source: str = "point") -> Problem:
     """A small seeded case for parity tests (several layers, ragged last layer).
 
     ``velocity`` is one of ``const``, ``lens``, ``layered``, ``bump``;
@@ -220,7 +249,11 @@ def small_problem(dim: int, n: int, omega: float, pml: int, b: int, velocity: st
     fs = []
     for _ in range(nrhs):
         p = rng.uniform(lo, hi, size=dim)
-        fs.append(gaussian_source(n, dim, tuple(p), 2 * h))
+        if source == "point":
+            fs.append(gaussian_source(n, dim, tuple(p), 2 * h))
+        else:  # wave packet with a seeded direction
+            d = rng.standard_normal(dim)
+            fs.append(wave_packet(n, dim, tuple(p), tuple(d), omega))
     return Problem(f"{dim}d_n{n}_{velocity}", dim, n, omega, pml, b, c, _stack(fs),
                    pml_aux=pml_aux, C=C, seed=seed)
 
