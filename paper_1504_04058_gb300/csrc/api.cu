@@ -64,6 +64,24 @@ void phase_end(Handle& H, PhaseTok t, cudaStream_t s) {
   }
 }
 
+// The dynamic shared-memory limit is a property of the kernel, shared by every
+// host thread; concurrent handles of different sizes must never lower it under
+// each other's launches, so it only ever grows.
+cudaError_t ensure_dyn_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> set_to;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(dev, func);
+  auto it = set_to.find(key);
+  if (it != set_to.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) set_to[key] = bytes;
+  return e;
+}
+
 void set_detail(const std::string& s) { g_detail = s; }
 int fail(int code, const std::string& detail) {
   g_detail = detail;

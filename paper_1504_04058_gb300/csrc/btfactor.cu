@@ -146,12 +146,12 @@ cudaError_t launch_factor(Handle& H, int first, int count, cudaStream_t s) {
   const size_t smem = 2 * (size_t)H.wmax * (H.wmax | 1) * esz;
   cudaError_t e;
   if (H.prec == ASP_PREC_C128) {
-    e = cudaFuncSetAttribute(btfactor_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_dyn_smem((const void*)btfactor_kernel<double>, smem);
     if (e != cudaSuccess) return e;
     btfactor_kernel<double><<<nsub, kFactorThreads, smem, s>>>(H.d_subs, first, H.fc64, H.n, (double2*)H.W,
                                                                 H.err);
   } else {
-    e = cudaFuncSetAttribute(btfactor_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_dyn_smem((const void*)btfactor_kernel<float>, smem);
     if (e != cudaSuccess) return e;
     btfactor_kernel<float><<<nsub, kFactorThreads, smem, s>>>(H.d_subs, first, H.fc32, H.n, (float2*)H.W,
                                                                H.err);

@@ -412,7 +412,7 @@ cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
   if (sizeof(R) == 4) G.wstage = (G.wstage + 1) & ~1;
   const size_t smem = T::total(G, nt);
   auto kern = btsolve_kernel<R, TRT, TC, LC, NCW, MAXT, MINB, CLS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_dyn_smem((const void*)kern, smem);
   if (e != cudaSuccess) return e;
   int grid = P.njobs < P.zslots ? P.njobs : P.zslots;
   if (grid <= 0) return cudaSuccess;

@@ -202,12 +202,12 @@ cudaError_t launch_chain(Handle& H, const ChainParams& P, cudaStream_t s) {
   dim3 grid(2 * half), block(kChainThreads);
   if (H.prec == ASP_PREC_C128) {
     const size_t smem = chain_smem<double>();
-    e = cudaFuncSetAttribute(chain_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_dyn_smem((const void*)chain_kernel<double>, smem);
     if (e != cudaSuccess) return e;
     e = cudaLaunchCooperativeKernel((void*)chain_kernel<double>, grid, block, args, smem, s);
   } else {
     const size_t smem = chain_smem<float>();
-    e = cudaFuncSetAttribute(chain_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_dyn_smem((const void*)chain_kernel<float>, smem);
     if (e != cudaSuccess) return e;
     e = cudaLaunchCooperativeKernel((void*)chain_kernel<float>, grid, block, args, smem, s);
   }

@@ -398,14 +398,14 @@ template <typename R> struct Factor3Kernels {
     if (CL > kMaxCluster) return cudaErrorInvalidValue;
     const int rpc = (nbmax + CL - 1) / CL;
     const size_t psmem = (size_t)rpc * (kLDP * esz + sizeof(int));
-    cudaError_t e = cudaFuncSetAttribute(panel_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    cudaError_t e = ensure_dyn_smem((const void*)panel_kernel<R>, psmem);
     if (e != cudaSuccess) return e;
     if (CL > 1) {
       e = cudaFuncSetAttribute(panel_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
       if (e != cudaSuccess) return e;
     }
     const size_t usmem = (size_t)(kBM * kLDP + kPW * kBN) * esz;
-    e = cudaFuncSetAttribute(update_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem);
+    e = ensure_dyn_smem((const void*)update_kernel<R>, usmem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t pc{};
     cudaLaunchAttribute pattr[1];

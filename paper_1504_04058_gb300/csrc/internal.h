@@ -321,6 +321,8 @@ struct Handle {
 };
 
 void set_detail(const std::string& s);
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it).
+cudaError_t ensure_dyn_smem(const void* func, size_t bytes);
 int fail(int code, const std::string& detail);
 
 }  // namespace asp

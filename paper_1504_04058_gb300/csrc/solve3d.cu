@@ -377,8 +377,7 @@ int get_jobs(Handle& H, long long key, int nrhs, int sub_slab, Jobs3** out) {
 template <typename R, int NR>
 cudaError_t launch_solve_t(Handle& H, Solve3Params P, int nbmax, cudaStream_t s) {
   const size_t smem = (size_t)stage_len(nbmax) * NR * sizeof(Cx<R>);
-  cudaError_t e = cudaFuncSetAttribute(slab_solve_kernel<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = ensure_dyn_smem((const void*)slab_solve_kernel<R, NR>, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slab_solve_kernel<R, NR>, kSolveThreads, smem);

@@ -383,7 +383,7 @@ cudaError_t launch_tc_update(const TcGroup& G, const Slab3Params& P, int nbmax, 
   const int nbpad = (nbmax + kTM - 1) / kTM * kTM;
   const dim3 pgrid((kSlabOuter / 32) * (nbpad / 32), P.nlist);
   tc_prep_kernel<<<pgrid, dim3(32, 8), 0, s>>>(P, G.rowA, C0, buf, G.ahi, G.alo, G.bhi, G.blo);
-  cudaError_t e = cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  cudaError_t e = ensure_dyn_smem((const void*)tc_update_kernel, kTcSmem);
   if (e != cudaSuccess) return e;
   const dim3 ugrid((nbmax + kTNc - 1) / kTNc, (nbmax + kTM - 1) / kTM, P.nlist);
   tc_update_kernel<<<ugrid, 128, kTcSmem, s>>>(*reinterpret_cast<const TcMaps*>(G.maps), P, G.rowA, C0, buf);

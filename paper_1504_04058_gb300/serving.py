@@ -319,6 +319,8 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--workers", type=int, default=2)
     ap.add_argument("--max-rhs", type=int, default=16)
+    ap.add_argument("--capacity", action="store_true",
+                    help="submit every request at once (measures the sustainable request rate)")
     ap.add_argument("--one-at-a-time", action="store_true",
                     help="baseline: complex128 factors, one request per solve, no cache reuse across keys")
     args = ap.parse_args()
@@ -329,10 +331,11 @@ def main():
                                           realtime=False, precision="c128", batching=False)
     else:
         results, wall, stats = run_stream(reqs, int(args.budget_gb * 2**30), workers=args.workers,
-                                          max_rhs=args.max_rhs, realtime=True)
+                                          max_rhs=args.max_rhs, realtime=not args.capacity)
     lat = [r.latency_s for r in results]
     nrhs = sum(len(r.iterations) for r in results)
     out = {"requests": len(results), "rhs": nrhs, "wall_s": wall, "solves_per_s": nrhs / wall,
+           "requests_per_s": len(results) / wall,
            **{k: v for k, v in percentiles(lat).items()}, "stats": stats,
            "worst_rel_res_true": max(max(r.rel_res_true) for r in results)}
     print(json.dumps(out))

@@ -69,3 +69,44 @@ def test_batched_concurrent_solutions_match_alone():
 
     lat = serving.percentiles([m.latency_s for m in mixed])
     assert 0 < lat["p50"] <= lat["p99"] < 300
+
+
+def test_concurrent_handles_of_different_sizes():
+    """Two host threads drive handles of different widths on their own streams
+    (as the serving workers do); every kernel's shared-memory limit only grows,
+    so neither thread's launches can fail, and results equal the serial ones."""
+    import threading
+
+    import torch
+
+    import paper_1504_04058_gb300 as asp
+    probs = [W.small_problem(2, 47, 6 * math.pi, 6, 4, "lens", nrhs=12, seed=1),
+             W.small_problem(2, 95, 12 * math.pi, 12, 4, "layered", nrhs=16, seed=2)]
+    handles, ref = [], []
+    for P in probs:
+        prm = asp.make_params(P.n, P.omega, P.pml, P.b, precision="c64", max_rhs=P.nrhs)
+        h = asp.asp_setup(P.c, prm)
+        h.factor()
+        handles.append(h)
+        ref.append(h.apply_preconditioner(torch.from_numpy(P.f).cuda()).cpu().numpy())
+    errors = []
+
+    def drive(k):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                f = torch.from_numpy(probs[k].f).cuda()
+                for _ in range(30):
+                    z = handles[k].apply_preconditioner(f, stream=s)
+                s.synchronize()
+                errors.append((k, float(np.abs(z.cpu().numpy() - ref[k]).max())))
+        except Exception as ex:  # reported below
+            errors.append((k, repr(ex)))
+
+    ts = [threading.Thread(target=drive, args=(k,)) for k in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert sorted(e[0] for e in errors) == [0, 1], errors
+    assert all(isinstance(e[1], float) and e[1] == 0.0 for e in errors), errors
