@@ -13,13 +13,14 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * Grid.  n interior nodes per axis, h = 1/(n+1), node i at x = i*h (Section 2).
- *        dim = 2 only in this version of the library (3D is rejected with
- *        ASP_ERR_UNSUPPORTED).
+ *        dim = 2 or 3 (Section 4 for 3D).
  * Vectors.  A batch of nrhs grid functions is stored point-major with the
  *        right-hand side fastest ("RHS-interleaved"):
- *            element (i1, i2, r) at offset ((i2-1)*n + (i1-1))*nrhs + r,
+ *            2D: element (i1, i2, r)     at ((i2-1)*n + (i1-1))*nrhs + r,
+ *            3D: element (i1, i2, i3, r) at (((i3-1)*n + (i2-1))*n + (i1-1))*nrhs + r,
  *        i.e. for nrhs = 1 exactly the paper's column-major ordering (x1 fastest,
- *        Section 3.1).  The sweep axis is x2.  Complex numbers are interleaved
+ *        Section 3.1).  The sweep axis is the slowest one: x2 in 2D, x3 in 3D
+ *        (layers are columns in 2D and slabs of planes in 3D).  Complex numbers are interleaved
  *        (re, im) pairs: complex128 = two doubles.  All vector arguments are
  *        DEVICE pointers unless the name says _host.
  * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
@@ -60,15 +61,16 @@ extern "C" {
 #define ASP_PREC_C64 1  /* complex64 factors and applies inside FP64 FGMRES      */
 
 /* Problem parameters (Section 2 and Section 3.1 notation).
- *   dim        spatial dimension (2)
+ *   dim        spatial dimension (2 or 3)
  *   n          interior nodes per axis; h = 1/(n+1)
  *   omega      angular frequency (> 0)
  *   pml        gamma: boundary PML width eta = gamma*h (>= 2)
  *   pml_aux    gamma_a: width of the auxiliary PMLs of the padded layer grids
  *              (Section 3.1, practical remark 2); 0 means gamma_a = gamma
- *   b          interior layer width in grid columns along x2 (>= 1); with
- *              P = n + 2 - 2*gamma physical columns there are m = floor(P/b)
- *              layers and the last one absorbs the remainder P - m*b
+ *   b          interior layer width in grid columns (planes in 3D) along the
+ *              sweep axis (>= 1); with P = n + 2 - 2*gamma physical columns there
+ *              are m = floor(P/b) layers and the last one absorbs the remainder
+ *              P - m*b
  *   C          PML strength: sigma = (C/eta) (d/eta)^2 at distance d past the
  *              physical edge (Section 2); > 0
  *   factor_prec ASP_PREC_C128 or ASP_PREC_C64
@@ -102,8 +104,10 @@ typedef struct asp_solve_info {
  * X_p^R, X_p^L), compute the PML profiles, copy the velocity c (n^dim doubles,
  * natural ordering, HOST memory if c_is_device == 0, else DEVICE) and allocate
  * the handle's device memory.  Returns ASP_ERR_INVALID for out-of-range
- * parameters or a non-positive / non-finite velocity, ASP_ERR_OOM if the
- * footprint does not fit.  Synchronizes the device before returning. */
+ * parameters or a non-positive / non-finite velocity, ASP_ERR_UNSUPPORTED for a
+ * valid problem this build does not take (2D: a padded layer wider than 64
+ * columns; 3D: a slab block n * (padded width) above 3072 unknowns), ASP_ERR_OOM
+ * if the footprint does not fit.  Synchronizes the device before returning. */
 int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle** out);
 
 /* Bytes of device memory asp_setup + asp_factor will hold for these
@@ -120,7 +124,10 @@ int asp_layer_range(const asp_handle* h, int p, int* x_lo, int* x_hi);
  * (p=1..m-1) in the precision chosen at setup, all in one batched launch, and
  * builds the dense trace-transfer maps of the R and L sweeps (the linear maps
  * from a layer's incoming boundary trace to the outgoing trace of G~_p^R /
- * G~_p^L, Section 3.1 "Putting together").  Enqueued on `stream`; the pivot
+ * G~_p^L, Section 3.1 "Putting together").  In 3D every slab subproblem is
+ * factored by blocked Gauss-Jordan over its x2 planes (dense blocks of
+ * n*w unknowns; complex64 factors do the rank-256 Schur updates on the tensor
+ * cores) and no transfer maps are built.  Enqueued on `stream`; the pivot
  * check synchronizes `stream` and returns ASP_ERR_SMALL_PIVOT if any block
  * pivot was zero or non-finite. */
 int asp_factor(asp_handle* h, void* stream);
@@ -132,15 +139,17 @@ int asp_factor(asp_handle* h, void* stream);
  * asp_factor.  Enqueued on `stream`. */
 int asp_apply_preconditioner(asp_handle* h, const void* r, void* z, int nrhs, void* stream);
 
-/* y = A x: the 5-point operator of Eq. (4) with the PML on all four sides, for
- * nrhs complex128 DEVICE vectors (RHS-interleaved, no aliasing).  Needs only
- * asp_setup.  Enqueued on `stream`. */
+/* y = A x: the 5-point operator of Eq. (4) with the PML on all four sides (3D:
+ * the 7-point operator, PML on all six sides), for nrhs complex128 DEVICE
+ * vectors (RHS-interleaved, no aliasing).  Needs only asp_setup.  Enqueued on
+ * `stream`. */
 int asp_matvec(asp_handle* h, const void* x, void* y, int nrhs, void* stream);
 
 /* One layer subproblem on its own (for checking): v = H^-1 g for the
  * subproblem kind (0 = H_p^M, 1 = H_p^R, 2 = H_p^L) of layer p, with g and v
- * complex128 DEVICE arrays of shape [w][n][nrhs] (padded x2 columns of the
- * subproblem outermost, x1, then the right-hand side), w = asp_subproblem_width.
+ * complex128 DEVICE arrays of shape [w][n][nrhs] (2D: padded x2 columns of the
+ * subproblem outermost, x1, then the right-hand side) or [w][n][n][nrhs] (3D:
+ * padded x3 planes, x2, x1, right-hand side), w = asp_subproblem_width.
  * Uses the stored factors.  Enqueued on `stream`. */
 int asp_subproblem_width(const asp_handle* h, int kind, int p);
 int asp_subproblem_solve(asp_handle* h, int kind, int p, const void* g, void* v, int nrhs,
@@ -148,7 +157,9 @@ int asp_subproblem_solve(asp_handle* h, int kind, int p, const void* g, void* v,
 
 /* asp_gmres_solve: right-preconditioned flexible GMRES (Section 3.2), zero
  * initial guess, restart `restart` (<= the setup value), FP64 Arnoldi
- * (classical Gram-Schmidt applied twice) and Givens rotations on the device,
+ * (classical Gram-Schmidt, with a second pass for a right-hand side whose new
+ * vector lost more than a factor 1000 of its norm) and Givens rotations on the
+ * device,
  * independent Krylov spaces per right-hand side.  Stops a right-hand side when
  * its residual estimate / ||f|| <= tol; stops when all have stopped or after
  * `maxit` iterations.  tol = 0 with maxit = k runs exactly k iterations.
