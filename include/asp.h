@@ -116,7 +116,8 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
 size_t asp_footprint_bytes(const asp_params* p);
 
 /* Number of layers m, and the partition of layer p (1-based): X_p = [x_lo, x_hi]
- * along x2 (global 1-based indices).  Returns ASP_ERR_INVALID for a bad p. */
+ * along the sweep axis (global 1-based indices).  Returns ASP_ERR_INVALID for a
+ * bad p. */
 int asp_num_layers(const asp_handle* h);
 int asp_layer_range(const asp_handle* h, int p, int* x_lo, int* x_hi);
 
