@@ -606,8 +606,11 @@ void asp_destroy(asp_handle* hd) {
     caches().erase(&H);
   }
   release_jobs3(&H);
-  tc_group_release(H.tcM);
-  tc_group_release(H.tcRL);
+  for (auto& g : H.fgroups) {
+    tc_group_release(g.tc);
+    if (g.stream) cudaStreamDestroy(g.stream);
+    if (g.done) cudaEventDestroy(g.done);
+  }
   void* ptrs[] = {H.k2, H.ca, H.cc, H.cd, H.d_subs, H.d_coef, H.W, H.tmap, H.d_toffR, H.d_toffL, H.r_lo,
                   H.uM, H.uR, H.uL, H.accR, H.accL, H.zscr, H.bar, H.V, H.Z, H.wv, H.red, H.hess, H.kstate,
                   H.kflags, H.err, H.d_slabs, H.d_slab_lists, H.A3, H.piv3, H.z3, H.tc_area};
@@ -847,18 +850,42 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
     for (size_t i = 0; i < lists.size(); ++i) lists[i] = (int)i;  // [M slabs | R slabs, L slabs]
     cp(H.d_slabs, H.slabs.data(), H.slabs.size() * sizeof(Slab));
     cp(H.d_slab_lists, lists.data(), lists.size() * sizeof(int));
-    if (up && H.prec == ASP_PREC_C64) {
-      // operand rows of the tensor-core update, per group in list order
-      std::vector<long long> rM, rRL;
-      long long nM = 0, nRL = 0;
-      for (size_t i = 0; i < H.slabs.size(); ++i) {
-        const long long pad = (H.slabs[i].nb + 127) / 128 * 128;
-        if ((int)i < m) { rM.push_back(nM); nM += pad; }
-        else { rRL.push_back(nRL); nRL += pad; }
+    // factor groups: one per kind (the M slabs; the R and L slabs).  Finer
+    // splits measured slower at n = 95: four streams took 3.88 s per factor
+    // against 3.06 s for two.
+    if (up) {
+      auto add_group = [&](int first, int count) {
+        if (count <= 0) return;
+        Handle::FGroup g;
+        g.first = first;
+        g.count = count;
+        for (int i = first; i < first + count; ++i) g.nbmax = std::max(g.nbmax, H.slabs[i].nb);
+        H.fgroups.push_back(g);
+      };
+      add_group(0, m);
+      add_group(m, (int)H.slabs.size() - m);
+      for (size_t gi = 0; gi < H.fgroups.size() && up; ++gi) {
+        Handle::FGroup& g = H.fgroups[gi];
+        if (gi + 1 < H.fgroups.size() &&  // the last group runs on the caller's stream
+            cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess)
+          up = false;
+        if (up && cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess) up = false;
       }
-      int rc = ASP_OK;  // an empty group (m = 1 has no R/L slabs) needs no operand area
-      if (nM > 0) rc = tc_group_setup(H.tcM, H.tc_area, rM, nM);
-      if (rc == ASP_OK && nRL > 0) rc = tc_group_setup(H.tcRL, H.tc_area + tc_group_floats(nM), rRL, nRL);
+    }
+    if (up && H.prec == ASP_PREC_C64) {
+      // operand rows of the tensor-core update, per factor group in list order
+      long long off = 0;
+      int rc = ASP_OK;
+      for (auto& g : H.fgroups) {
+        std::vector<long long> rows;
+        long long nrows = 0;
+        for (int i = g.first; i < g.first + g.count; ++i) {
+          rows.push_back(nrows);
+          nrows += (H.slabs[i].nb + 127) / 128 * 128;
+        }
+        if (rc == ASP_OK) rc = tc_group_setup(g.tc, H.tc_area + off, rows, nrows);
+        off += tc_group_floats(nrows);
+      }
       if (rc != ASP_OK) {
         const std::string why = asp_last_error_detail();
         asp_destroy(hd);

@@ -455,30 +455,30 @@ template <typename R> struct Factor3Kernels {
 
 }  // namespace
 
-// Factors every slab: the M group on the handle's internal stream, the R and L
-// group on the caller's stream, then joins the two.
+// Factors every slab: each factor group (the M slabs; the R and L slabs) on its
+// own stream, forked from and joined back into the caller's.
 int factor3d(Handle& H, cudaStream_t s) {
-  const int m = H.m;
-  const int nM = m, nRL = (int)H.slabs.size() - m;
-  if (cudaEventRecord(H.ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(H.aux, H.ev_fork, 0) != cudaSuccess)
-    return fail(ASP_ERR_CUDA, "factor: stream fork");
-  cudaError_t ea, eb;
-  PhaseTok ta = phase_begin(H, PH_FACTOR, H.aux);
-  if (H.prec == ASP_PREC_C128)
-    ea = Factor3Kernels<double>::run_group(H, H.fc64, H.d_slab_lists, nM, H.nbmaxM, nullptr, H.aux);
-  else
-    ea = Factor3Kernels<float>::run_group(H, H.fc32, H.d_slab_lists, nM, H.nbmaxM, &H.tcM, H.aux);
-  phase_end(H, ta, H.aux);
-  PhaseTok tb = phase_begin(H, PH_FACTOR, s);
-  if (H.prec == ASP_PREC_C128)
-    eb = Factor3Kernels<double>::run_group(H, H.fc64, H.d_slab_lists + nM, nRL, H.nbmaxRL, nullptr, s);
-  else
-    eb = Factor3Kernels<float>::run_group(H, H.fc32, H.d_slab_lists + nM, nRL, H.nbmaxRL, &H.tcRL, s);
-  phase_end(H, tb, s);
-  if (cudaEventRecord(H.ev_join, H.aux) != cudaSuccess || cudaStreamWaitEvent(s, H.ev_join, 0) != cudaSuccess)
-    return fail(ASP_ERR_CUDA, "factor: stream join");
-  if (ea != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("3D factor (M) launch: ") + cudaGetErrorString(ea));
-  if (eb != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("3D factor (R/L) launch: ") + cudaGetErrorString(eb));
+  auto cuda_fail = [](const char* what, cudaError_t e) {
+    return fail(ASP_ERR_CUDA, std::string("3D factor: ") + what + ": " + cudaGetErrorString(e));
+  };
+  cudaError_t e = cudaEventRecord(H.ev_fork, s);
+  if (e != cudaSuccess) return cuda_fail("fork record", e);
+  cudaError_t first_err = cudaSuccess;
+  for (auto& g : H.fgroups) {
+    cudaStream_t gs = g.stream ? g.stream : s;
+    if (g.stream && (e = cudaStreamWaitEvent(gs, H.ev_fork, 0)) != cudaSuccess) return cuda_fail("fork wait", e);
+    PhaseTok tk = phase_begin(H, PH_FACTOR, gs);
+    if (H.prec == ASP_PREC_C128)
+      e = Factor3Kernels<double>::run_group(H, H.fc64, H.d_slab_lists + g.first, g.count, g.nbmax, nullptr, gs);
+    else
+      e = Factor3Kernels<float>::run_group(H, H.fc32, H.d_slab_lists + g.first, g.count, g.nbmax, &g.tc, gs);
+    phase_end(H, tk, gs);
+    if (e != cudaSuccess && first_err == cudaSuccess) first_err = e;
+    if ((e = cudaEventRecord(g.done, gs)) != cudaSuccess) return cuda_fail("join record", e);
+  }
+  for (auto& g : H.fgroups)
+    if (g.stream && (e = cudaStreamWaitEvent(s, g.done, 0)) != cudaSuccess) return cuda_fail("join wait", e);
+  if (first_err != cudaSuccess) return cuda_fail("launch", first_err);
   return ASP_OK;
 }
 

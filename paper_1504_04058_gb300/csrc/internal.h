@@ -313,7 +313,15 @@ struct Handle {
   int* piv3 = nullptr;
   void* z3 = nullptr;           // solve scratch
   float* tc_area = nullptr;     // tensor-core update operands (complex64 factors)
-  TcGroup tcM, tcRL;
+  // factor groups: contiguous ranges of the slab list, each factored on its own
+  // stream so that one group's latency-bound panels overlap another's updates
+  struct FGroup {
+    int first = 0, count = 0, nbmax = 0;
+    TcGroup tc;
+    cudaStream_t stream = nullptr;  // owned (nullptr: the caller's stream)
+    cudaEvent_t done = nullptr;
+  };
+  std::vector<FGroup> fgroups;
 
   // second stream for work that overlaps the caller's stream (factor time)
   cudaStream_t aux = nullptr;
