@@ -18,7 +18,7 @@
 //     (the dropped A_lo B_lo term is 2^-22 relative).
 // A prep kernel writes A_hi, A_lo (rows of 2*kSlabOuter floats) and B'^T_hi,
 // B'^T_lo (2nb rows of 2*kSlabOuter floats, K-major) for every slab of the
-// launch.  The update kernel computes one 128 x 128 complex tile per CTA:
+// launch.  The update kernel computes 128 x 128 complex tiles of C:
 //   * one thread issues TMA 2D tiled loads (128-byte swizzle) of 32-float K
 //     chunks of the four operands into a two-stage shared-memory ring, tracked
 //     by mbarriers;
@@ -26,8 +26,8 @@
 //     instruction, both operands K-major from shared-memory descriptors) into
 //     a 128 x 256 FP32 accumulator in tensor memory; tcgen05.commit releases
 //     each ring stage and finally signals the epilogue;
-//   * four warps read the accumulator with tcgen05.ld (warp w: lanes 32w..32w+31
-//     = tile rows) and add it into (or, for pivot rows, store it as) C.
+//   * four warps read the accumulator with tcgen05.ld and add it into (or, for
+//     pivot rows, store it as) C.
 // Every wait is bounded; a timeout records ASP_ERR_TIMEOUT, and the CTA still
 // waits (bounded) for its copies and products in flight and frees its tensor
 // memory before it returns.
@@ -174,40 +174,80 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(Slab3Params P, const long 
   }
 }
 
-// ----------------------------------------------------------------- update
-// Grid (column tiles of kTNc, row tiles of kTM, slab); 128 threads.
-__global__ void __launch_bounds__(128, 1) tc_update_kernel(const __grid_constant__ TcMaps maps, Slab3Params P,
-                                                           const long long* rowA, int C0, int buf) {
-  const Slab S = P.slabs[P.list[blockIdx.z]];
-  const int nb = S.nb, ld = S.ld;
-  if (C0 >= nb) return;
-  const int K = min(kSlabOuter, nb - C0);
-  const int j0 = blockIdx.x * kTNc, i0 = blockIdx.y * kTM;
-  if (j0 >= nb || i0 >= nb) return;
-  if (j0 >= C0 && j0 + kTNc <= C0 + K) return;  // inside the eliminated block
-  const int nch = (2 * K + kKC - 1) / kKC;
-  const long long ra = rowA[blockIdx.z];
+// ------------------------------------------------------ persistent update
+// The same tiles, with one CTA per SM walking them (tile t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... over (column tile, row tile, slab), skipping
+// tiles that lie inside the eliminated block).  Warp roles:
+//   warp 0 lane 0  TMA producer for every K chunk of every tile, into the
+//                  two-stage ring (counters run on across tiles);
+//   warp 1 lane 0  MMA issuer; tile it accumulates into tensor-memory buffer
+//                  it & 1 (two 256-column accumulators), once the epilogue has
+//                  released that buffer;
+//   warps 2-5      epilogue of tile it while the MMAs of tile it+1 run; warp w
+//                  reads accumulator lanes 32*(w%4) .. +31 and releases the
+//                  buffer with one arrival per warp.
+// Every wait is bounded; on a timeout the role records ASP_ERR_TIMEOUT and
+// stops, the others time out in turn, and before the tensor memory is freed the
+// issuer waits (bounded) for its last products and the producer for its last
+// copies.
+constexpr int kPersistThreads = 192;
 
+__device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+struct TcTile {
+  int valid, z, i0, j0, K, nb, ld;
+  long long ra, aoff;
+  int poff;
+};
+
+__device__ __forceinline__ TcTile tc_tile(const Slab3Params& P, const long long* rowA, int C0, int ncx, int ncy,
+                                          int t) {
+  TcTile T;
+  const int bx = t % ncx, by = (t / ncx) % ncy, z = t / (ncx * ncy);
+  const Slab S = P.slabs[P.list[z]];
+  T.z = z;
+  T.nb = S.nb;
+  T.ld = S.ld;
+  T.i0 = by * kTM;
+  T.j0 = bx * kTNc;
+  T.K = min(kSlabOuter, S.nb - C0);
+  T.ra = rowA[z];
+  T.aoff = S.aoff;
+  T.poff = (int)S.poff;
+  T.valid = C0 < S.nb && T.j0 < S.nb && T.i0 < S.nb && !(T.j0 >= C0 && T.j0 + kTNc <= C0 + T.K);
+  return T;
+}
+
+__global__ void __launch_bounds__(kPersistThreads, 1)
+    tc_update_persistent_kernel(const __grid_constant__ TcMaps maps, Slab3Params P, const long long* rowA, int C0,
+                                int buf, int ncx, int ncy) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t sbase = (smem_addr(smem_raw) + 1023u) & ~1023u;
   unsigned char* sgen = smem_raw + (sbase - smem_addr(smem_raw));
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], last;
   __shared__ uint32_t tmem_base;
   __shared__ int s_err;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = ncx * ncy * P.nlist;
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&done, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    mbar_init(&last, 1);
     s_err = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
-                 "r"(kTmemCols)
+                 "r"(2 * kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -217,101 +257,152 @@ __global__ void __launch_bounds__(128, 1) tc_update_kernel(const __grid_constant
   const uint32_t tmem = tmem_base;
 
   auto stage_ptr = [&](int s, int which) -> unsigned char* {
-    // which: 0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo
     const uint32_t off = (uint32_t)s * kStageBytes +
                          (which < 2 ? which * kABytes : 2 * kABytes + (which - 2) * kBBytes);
     return sgen + off;
   };
-
-  if (warp == 0 && lane == 0) {
-    // ---- producer: TMA loads of the K chunks
-    int issued = 0;
-    for (int ch = 0; ch < nch; ++ch) {
-      const int s = ch % kStages;
-      if (ch >= kStages && !mbar_wait(&empty[s], (uint32_t)((ch / kStages - 1) & 1))) {
-        record_error(P.err, ASP_ERR_TIMEOUT, 3000000 + blockIdx.x);
-        atomicExch(&s_err, 1);
-        break;
-      }
-      mbar_arrive_expect_tx(&full[s], kStageBytes);
-      const int x = ch * kKC;
-      tma_load_2d(stage_ptr(s, 0), &maps.ahi, x, (int)(ra + i0), &full[s]);
-      tma_load_2d(stage_ptr(s, 1), &maps.alo, x, (int)(ra + i0), &full[s]);
-      tma_load_2d(stage_ptr(s, 2), &maps.bhi, x, (int)(2 * ra + 2 * j0), &full[s]);
-      tma_load_2d(stage_ptr(s, 3), &maps.blo, x, (int)(2 * ra + 2 * j0), &full[s]);
-      issued = ch + 1;
-    }
-    if (s_err) {
-      // drain: the last load issued on each stage
-      for (int s = 0; s < kStages; ++s) {
-        int last = -1;
-        for (int ch = s; ch < issued; ch += kStages) last = ch;
-        if (last >= 0) mbar_wait(&full[s], (uint32_t)((last / kStages) & 1));
-      }
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    for (int ch = 0; ch < nch; ++ch) {
-      const int s = ch % kStages;
-      if (!mbar_wait(&full[s], (uint32_t)((ch / kStages) & 1))) {
-        record_error(P.err, ASP_ERR_TIMEOUT, 3100000 + blockIdx.x);
-        atomicExch(&s_err, 1);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t ah = smem_addr(stage_ptr(s, 0)), al = smem_addr(stage_ptr(s, 1));
-      const uint32_t bh = smem_addr(stage_ptr(s, 2)), bl = smem_addr(stage_ptr(s, 3));
-#pragma unroll
-      for (int kk = 0; kk < kKC / 8; ++kk) {
-        const uint32_t ko = kk * 32;  // 8 floats
-        const uint32_t acc = (ch > 0 || kk > 0) ? 1u : 0u;
-        mma_tf32(tmem, sw128_desc(ah + ko), sw128_desc(bh + ko), acc);
-        mma_tf32(tmem, sw128_desc(ah + ko), sw128_desc(bl + ko), 1u);
-        mma_tf32(tmem, sw128_desc(al + ko), sw128_desc(bh + ko), 1u);
-      }
-      mma_commit(&empty[s]);
-    }
-    mma_commit(&done);
-  }
-  __syncwarp();
-
-  // ---- epilogue: every warp reads its 32 accumulator rows
-  const bool ok = mbar_wait(&done, 0u);
-  if (!ok && lane == 0) {
-    record_error(P.err, ASP_ERR_TIMEOUT, 3200000 + blockIdx.x);
+  auto timeout = [&](int where) {
+    record_error(P.err, ASP_ERR_TIMEOUT, where + blockIdx.x);
     atomicExch(&s_err, 1);
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int i = i0 + warp * 32 + lane;
-  const int* row_step = P.piv + S.poff + 2 * nb;
-  const int st = i < nb ? row_step[i] : -1;
-  const bool piv = st >= C0 && st < C0 + K;
-  float2* crow = reinterpret_cast<float2*>(P.A) + S.aoff + (long long)buf * nb * ld + (long long)min(i, nb - 1) * ld;
-  const bool write = ok && s_err == 0 && i < nb;
-#pragma unroll 1
-  for (int cc = 0; cc < kTN / 32; ++cc) {
-    float v[32];
-    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
-    if (write) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int j = j0 + cc * 16 + q;
-        if (j < nb && !(j >= C0 && j < C0 + K)) {
-          const float2 a = make_float2(v[2 * q], v[2 * q + 1]);
-          if (piv) {
-            crow[j] = a;
-          } else {
-            const float2 c = crow[j];
-            crow[j] = make_float2(c.x + a.x, c.y + a.y);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer
+      long long g = 0;  // chunks issued by this CTA
+      bool stop = false;
+      for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+        const TcTile T = tc_tile(P, rowA, C0, ncx, ncy, t);
+        if (!T.valid) continue;
+        const int nch = (2 * T.K + kKC - 1) / kKC;
+        for (int ch = 0; ch < nch; ++ch, ++g) {
+          const int s = (int)(g % kStages);
+          const long long u = g / kStages;
+          if (u >= 1 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1))) {
+            timeout(3300000);
+            stop = true;
+            break;
           }
+          if (s_err) { stop = true; break; }
+          mbar_arrive_expect_tx(&full[s], kStageBytes);
+          const int x = ch * kKC;
+          tma_load_2d(stage_ptr(s, 0), &maps.ahi, x, (int)(T.ra + T.i0), &full[s]);
+          tma_load_2d(stage_ptr(s, 1), &maps.alo, x, (int)(T.ra + T.i0), &full[s]);
+          tma_load_2d(stage_ptr(s, 2), &maps.bhi, x, (int)(2 * T.ra + 2 * T.j0), &full[s]);
+          tma_load_2d(stage_ptr(s, 3), &maps.blo, x, (int)(2 * T.ra + 2 * T.j0), &full[s]);
+        }
+      }
+      if (stop) {
+        // copies still in flight complete on their stage's full barrier
+        for (int s = 0; s < kStages; ++s) {
+          long long lastg = -1;
+          for (long long q = g - 1; q >= 0 && q >= g - kStages; --q)
+            if (q % kStages == s) lastg = q;
+          if (lastg >= 0) mbar_wait(&full[s], (uint32_t)((lastg / kStages) & 1));
         }
       }
     }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      long long g = 0;
+      int it = 0;
+      bool stop = false;
+      bool issued_any = false;
+      for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+        const TcTile T = tc_tile(P, rowA, C0, ncx, ncy, t);
+        if (!T.valid) continue;
+        const int a = it & 1, ua = it >> 1;
+        if (ua >= 1 && !mbar_wait(&acc_empty[a], (uint32_t)((ua - 1) & 1))) {
+          timeout(3400000);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dacc = tmem + (uint32_t)(a * kTmemCols);
+        const int nch = (2 * T.K + kKC - 1) / kKC;
+        for (int ch = 0; ch < nch; ++ch, ++g) {
+          const int s = (int)(g % kStages);
+          if (!mbar_wait(&full[s], (uint32_t)((g / kStages) & 1)) || s_err) {
+            if (!s_err) timeout(3500000);
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t ah = smem_addr(stage_ptr(s, 0)), al = smem_addr(stage_ptr(s, 1));
+          const uint32_t bh = smem_addr(stage_ptr(s, 2)), bl = smem_addr(stage_ptr(s, 3));
+#pragma unroll
+          for (int kk = 0; kk < kKC / 8; ++kk) {
+            const uint32_t ko = kk * 32;
+            const uint32_t acc = (ch > 0 || kk > 0) ? 1u : 0u;
+            mma_tf32(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), acc);
+            mma_tf32(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), 1u);
+            mma_tf32(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), 1u);
+          }
+          issued_any = true;
+          mma_commit(&empty[s]);
+        }
+        if (stop) break;
+        mma_commit(&acc_full[a]);
+        ++it;
+      }
+      // every product issued by this thread has completed once `last` fires
+      if (issued_any) {
+        mma_commit(&last);
+        mbar_wait(&last, 0u);
+      }
+    }
+  } else {
+    // ---- epilogue warps 2..5
+    const int q = warp & 3;  // accumulator lane quarter this warp may read
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const TcTile T = tc_tile(P, rowA, C0, ncx, ncy, t);
+      if (!T.valid) continue;
+      const int a = it & 1, ua = it >> 1;
+      const bool ok = mbar_wait(&acc_full[a], (uint32_t)(ua & 1));
+      if (!ok) {
+        if (lane == 0) timeout(3600000);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int i = T.i0 + q * 32 + lane;
+      const int* row_step = P.piv + T.poff + 2 * T.nb;
+      const int st = i < T.nb ? row_step[i] : -1;
+      const bool piv = st >= C0 && st < C0 + T.K;
+      float2* crow = reinterpret_cast<float2*>(P.A) + T.aoff + (long long)buf * T.nb * T.ld +
+                     (long long)min(i, T.nb - 1) * T.ld;
+      const bool write = s_err == 0 && i < T.nb;
+#pragma unroll 1
+      for (int cc = 0; cc < kTN / 32; ++cc) {
+        float v[32];
+        tmem_ld32(tmem + (uint32_t)(a * kTmemCols) + ((uint32_t)(q * 32) << 16) + (uint32_t)(cc * 32), v);
+        if (write) {
+#pragma unroll
+          for (int qq = 0; qq < 16; ++qq) {
+            const int j = T.j0 + cc * 16 + qq;
+            if (j < T.nb && !(j >= C0 && j < C0 + T.K)) {
+              const float2 av = make_float2(v[2 * qq], v[2 * qq + 1]);
+              if (piv) {
+                crow[j] = av;
+              } else {
+                const float2 c = crow[j];
+                crow[j] = make_float2(c.x + av.x, c.y + av.y);
+              }
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(&acc_empty[a]);
+      ++it;
+    }
   }
+  __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols) : "memory");
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -383,10 +474,15 @@ cudaError_t launch_tc_update(const TcGroup& G, const Slab3Params& P, int nbmax, 
   const int nbpad = (nbmax + kTM - 1) / kTM * kTM;
   const dim3 pgrid((kSlabOuter / 32) * (nbpad / 32), P.nlist);
   tc_prep_kernel<<<pgrid, dim3(32, 8), 0, s>>>(P, G.rowA, C0, buf, G.ahi, G.alo, G.bhi, G.blo);
-  cudaError_t e = ensure_dyn_smem((const void*)tc_update_kernel, kTcSmem);
+  cudaError_t e = ensure_dyn_smem((const void*)tc_update_persistent_kernel, kTcSmem);
   if (e != cudaSuccess) return e;
-  const dim3 ugrid((nbmax + kTNc - 1) / kTNc, (nbmax + kTM - 1) / kTM, P.nlist);
-  tc_update_kernel<<<ugrid, 128, kTcSmem, s>>>(*reinterpret_cast<const TcMaps*>(G.maps), P, G.rowA, C0, buf);
+  const int ncx = (nbmax + kTNc - 1) / kTNc, ncy = (nbmax + kTM - 1) / kTM;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(ncx * ncy * P.nlist, sms));
+  tc_update_persistent_kernel<<<grid, kPersistThreads, kTcSmem, s>>>(*reinterpret_cast<const TcMaps*>(G.maps), P,
+                                                                     G.rowA, C0, buf, ncx, ncy);
   return cudaGetLastError();
 }
 
