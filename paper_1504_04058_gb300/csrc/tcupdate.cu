@@ -183,14 +183,15 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(Slab3Params P, const long 
 //   warp 1 lane 0  MMA issuer; tile it accumulates into tensor-memory buffer
 //                  it & 1 (two 256-column accumulators), once the epilogue has
 //                  released that buffer;
-//   warps 2-5      epilogue of tile it while the MMAs of tile it+1 run; warp w
-//                  reads accumulator lanes 32*(w%4) .. +31 and releases the
-//                  buffer with one arrival per warp.
+//   warps 2..      epilogue of tile it while the MMAs of tile it+1 run; warp w
+//                  reads accumulator lanes 32*(w%4) .. +31, its share of the
+//                  columns, and releases the buffer with one arrival per warp.
 // Every wait is bounded; on a timeout the role records ASP_ERR_TIMEOUT and
 // stops, the others time out in turn, and before the tensor memory is freed the
 // issuer waits (bounded) for its last products and the producer for its last
 // copies.
-constexpr int kPersistThreads = 192;
+constexpr int kEpiWarps = 8;  // kEpiWarps / 4 per accumulator lane quarter, splitting the columns (4 and 16 measured slower)
+constexpr int kPersistThreads = 64 + 32 * kEpiWarps;
 
 __device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
-      mbar_init(&acc_empty[a], 4);
+      mbar_init(&acc_empty[a], kEpiWarps);
     }
     mbar_init(&last, 1);
     s_err = 0;
@@ -352,8 +353,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       }
     }
   } else {
-    // ---- epilogue warps 2..5
+    // ---- epilogue warps 2..9
     const int q = warp & 3;  // accumulator lane quarter this warp may read
+    const int part = (warp - 2) >> 2;
+    constexpr int kChunksPerWarp = (kTN / 32) / (kEpiWarps / 4);
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const TcTile T = tc_tile(P, rowA, C0, ncx, ncy, t);
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
                      (long long)min(i, T.nb - 1) * T.ld;
       const bool write = s_err == 0 && i < T.nb;
 #pragma unroll 1
-      for (int cc = 0; cc < kTN / 32; ++cc) {
+      for (int cc = part * kChunksPerWarp; cc < (part + 1) * kChunksPerWarp; ++cc) {
         float v[32];
         tmem_ld32(tmem + (uint32_t)(a * kTmemCols) + ((uint32_t)(q * 32) << 16) + (uint32_t)(cc * 32), v);
         if (write) {
