@@ -301,7 +301,7 @@ def run_asp(args, rank, world):
         flops_per_launch = alg3["schur_flops"] * args.steps / max(sch_n, 1)
         ach = flops_per_launch / (sch_avg * 1e-3) / 1e12 if sch_n else 0.0
         roof = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
-                "kernel": "tc_update_kernel: complex64 rank-256 Schur update of the slab factor on tcgen05 "
+                "kernel": "tc_update_persistent_kernel: complex64 rank-256 Schur update of the slab factor on tcgen05 "
                           "(split TF32, 3 tensor products per useful product; achieved counts useful flops)",
                 "peak_source": f"bf16_tflops ({peak_kind}) x 0.5 nominal tf32/bf16 ratio",
                 "traffic": None, "avg_launch_ms": sch_avg, "launches_per_step": sch_n / args.steps,
