@@ -38,6 +38,8 @@
 
 #include <algorithm>
 #include <string>
+#include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -368,11 +370,28 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(Slab3Params P, int 
 }
 
 // ------------------------------------------------------------------ driver
-template <typename R> struct Factor3Kernels {
-  static cudaError_t run_group(Handle& H, const FactorCoefs<R>& F, const int* d_list, int nlist, int nbmax,
-                               const TcGroup* tc, cudaStream_t s) {
+// One factor group (slabs of one kind of subproblem sharing a stream).  setup()
+// sizes the launches once; block(k) enqueues the store of W_{k-1} and, for
+// k < n, the inversion of S_k.  The groups' blocks are enqueued alternately, so
+// that each stream always has queued work and the groups overlap on the GPU
+// (enqueued one group after the other, the host would block on the full launch
+// queue of the first group until that group was nearly done).
+template <typename R> struct Factor3Group {
+  Slab3Params P{};
+  cudaLaunchConfig_t pc{};
+  cudaLaunchAttribute pattr[1];
+  dim3 igrid, bgrid;
+  size_t usmem = 0;
+  int nbmax = 0, nlist = 0;
+  const TcGroup* tc = nullptr;
+  cudaStream_t s = nullptr;
+
+  cudaError_t setup(Handle& H, const int* d_list, int nlist_, int nbmax_, const TcGroup* tc_, cudaStream_t s_) {
+    nlist = nlist_;
+    nbmax = nbmax_;
+    tc = tc_;
+    s = s_;
     if (nlist <= 0) return cudaSuccess;
-    Slab3Params P{};
     P.slabs = H.d_slabs;
     P.list = d_list;
     P.nlist = nlist;
@@ -388,9 +407,8 @@ template <typename R> struct Factor3Kernels {
     const size_t static_bytes = 12288;  // the kernel's static shared arrays, with room
     const int rows_cap = (int)(((size_t)optin - static_bytes) / (kLDP * esz + sizeof(int)));
     // about 512 rows per CTA (the per-step row updates are issue-bound) while
-    // all clusters of the group fit in one wave, and at least as many CTAs as
-    // shared memory requires
-    // (one CTA per SM: all clusters of the group in a single wave)
+    // all clusters of the group fit in one wave (one CTA per SM), and at least
+    // as many CTAs as shared memory requires
     const int by_rows = std::min(kMaxCluster, (nbmax + 511) / 512);
     const int by_sms = std::max(1, H.num_sms / std::max(nlist, 1));
     int CL = std::max((nbmax + rows_cap - 1) / rows_cap, std::min(by_rows, by_sms));
@@ -404,11 +422,9 @@ template <typename R> struct Factor3Kernels {
       e = cudaFuncSetAttribute(panel_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
       if (e != cudaSuccess) return e;
     }
-    const size_t usmem = (size_t)(kBM * kLDP + kPW * kBN) * esz;
+    usmem = (size_t)(kBM * kLDP + kPW * kBN) * esz;
     e = ensure_dyn_smem((const void*)update_kernel<R>, usmem);
     if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t pc{};
-    cudaLaunchAttribute pattr[1];
     pattr[0].id = cudaLaunchAttributeClusterDimension;
     pattr[0].val.clusterDim.x = CL;
     pattr[0].val.clusterDim.y = 1;
@@ -417,41 +433,61 @@ template <typename R> struct Factor3Kernels {
     pc.blockDim = dim3(kPanelThreads);
     pc.dynamicSmemBytes = psmem;
     pc.stream = s;
-    pc.attrs = pattr;
     pc.numAttrs = 1;
-    const dim3 igrid(kKO / kBN, (nbmax + kBM - 1) / kBM, nlist);
-    const dim3 bgrid((nbmax + kBN - 1) / kBN, (nbmax + kBM - 1) / kBM, nlist);
+    igrid = dim3(kKO / kBN, (nbmax + kBM - 1) / kBM, nlist);
+    bgrid = dim3((nbmax + kBN - 1) / kBN, (nbmax + kBM - 1) / kBM, nlist);
+    return cudaSuccess;
+  }
+
+  cudaError_t block(Handle& H, const FactorCoefs<R>& F, int k) {
+    if (nlist <= 0) return cudaSuccess;
     const int n = H.n;
-    for (int k = 0; k <= n; ++k) {
-      const int store = k > 0, form = k < n;
-      form_store_kernel<R><<<dim3(nbmax, nlist), 256, 0, s>>>(P, F, k, (k + 1) & 1, store, form);
-      H.launches += 1;
-      if (!form) break;
-      const int buf = k & 1;
-      for (int C0 = 0; C0 < nbmax; C0 += kKO) {
-        for (int c0 = C0; c0 < std::min(C0 + kKO, nbmax); c0 += kPW) {
-          e = cudaLaunchKernelEx(&pc, panel_kernel<R>, P, c0, C0, buf);
-          if (e != cudaSuccess) return e;
-          update_kernel<R><<<igrid, kUpdThreads, usmem, s>>>(P, C0, c0, buf, 0);
-          H.launches += 2;
-        }
-        if (tc) {  // complex64: split-precision TF32 product on the tensor cores
-          PhaseTok ts = phase_begin(H, PH_SCHUR, s);
-          e = launch_tc_update(*tc, P, nbmax, C0, buf, s);
-          phase_end(H, ts, s);
-          if (e != cudaSuccess) return e;
-        } else {
-          gather_kernel<R><<<dim3(kKO, nlist), 256, 0, s>>>(P, C0, buf);
-          update_kernel<R><<<bgrid, kUpdThreads, usmem, s>>>(P, C0, 0, buf, 1);
-        }
+    const int store = k > 0, form = k < n;
+    form_store_kernel<R><<<dim3(nbmax, nlist), 256, 0, s>>>(P, F, k, (k + 1) & 1, store, form);
+    H.launches += 1;
+    if (!form) return cudaGetLastError();
+    const int buf = k & 1;
+    pc.attrs = pattr;  // the struct may have moved since setup
+    cudaError_t e;
+    for (int C0 = 0; C0 < nbmax; C0 += kKO) {
+      for (int c0 = C0; c0 < std::min(C0 + kKO, nbmax); c0 += kPW) {
+        e = cudaLaunchKernelEx(&pc, panel_kernel<R>, P, c0, C0, buf);
+        if (e != cudaSuccess) return e;
+        update_kernel<R><<<igrid, kUpdThreads, usmem, s>>>(P, C0, c0, buf, 0);
         H.launches += 2;
       }
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
+      if (tc) {  // complex64: split-precision TF32 product on the tensor cores
+        PhaseTok ts = phase_begin(H, PH_SCHUR, s);
+        e = launch_tc_update(*tc, P, nbmax, C0, buf, s);
+        phase_end(H, ts, s);
+        if (e != cudaSuccess) return e;
+      } else {
+        gather_kernel<R><<<dim3(kKO, nlist), 256, 0, s>>>(P, C0, buf);
+        update_kernel<R><<<bgrid, kUpdThreads, usmem, s>>>(P, C0, 0, buf, 1);
+      }
+      H.launches += 2;
     }
     return cudaGetLastError();
   }
 };
+
+template <typename R> cudaError_t factor_groups(Handle& H, const FactorCoefs<R>& F, cudaStream_t s) {
+  std::vector<Factor3Group<R>> runs(H.fgroups.size());
+  std::vector<PhaseTok> toks(H.fgroups.size());
+  cudaError_t e = cudaSuccess;
+  for (size_t g = 0; g < H.fgroups.size(); ++g) {
+    auto& G = H.fgroups[g];
+    cudaStream_t gs = G.stream ? G.stream : s;
+    const TcGroup* tc = std::is_same<R, float>::value ? &G.tc : nullptr;
+    if ((e = runs[g].setup(H, H.d_slab_lists + G.first, G.count, G.nbmax, tc, gs)) != cudaSuccess) return e;
+  }
+  for (size_t g = 0; g < runs.size(); ++g) toks[g] = phase_begin(H, PH_FACTOR, runs[g].s);
+  for (int k = 0; k <= H.n && e == cudaSuccess; ++k)
+    for (auto& r : runs)
+      if ((e = r.block(H, F, k)) != cudaSuccess) break;
+  for (size_t g = 0; g < runs.size(); ++g) phase_end(H, toks[g], runs[g].s);
+  return e;
+}
 
 }  // namespace
 
@@ -463,22 +499,16 @@ int factor3d(Handle& H, cudaStream_t s) {
   };
   cudaError_t e = cudaEventRecord(H.ev_fork, s);
   if (e != cudaSuccess) return cuda_fail("fork record", e);
-  cudaError_t first_err = cudaSuccess;
-  for (auto& g : H.fgroups) {
-    cudaStream_t gs = g.stream ? g.stream : s;
-    if (g.stream && (e = cudaStreamWaitEvent(gs, H.ev_fork, 0)) != cudaSuccess) return cuda_fail("fork wait", e);
-    PhaseTok tk = phase_begin(H, PH_FACTOR, gs);
-    if (H.prec == ASP_PREC_C128)
-      e = Factor3Kernels<double>::run_group(H, H.fc64, H.d_slab_lists + g.first, g.count, g.nbmax, nullptr, gs);
-    else
-      e = Factor3Kernels<float>::run_group(H, H.fc32, H.d_slab_lists + g.first, g.count, g.nbmax, &g.tc, gs);
-    phase_end(H, tk, gs);
-    if (e != cudaSuccess && first_err == cudaSuccess) first_err = e;
-    if ((e = cudaEventRecord(g.done, gs)) != cudaSuccess) return cuda_fail("join record", e);
-  }
   for (auto& g : H.fgroups)
-    if (g.stream && (e = cudaStreamWaitEvent(s, g.done, 0)) != cudaSuccess) return cuda_fail("join wait", e);
-  if (first_err != cudaSuccess) return cuda_fail("launch", first_err);
+    if (g.stream && (e = cudaStreamWaitEvent(g.stream, H.ev_fork, 0)) != cudaSuccess) return cuda_fail("fork wait", e);
+  const cudaError_t launch_err =
+      H.prec == ASP_PREC_C128 ? factor_groups<double>(H, H.fc64, s) : factor_groups<float>(H, H.fc32, s);
+  for (auto& g : H.fgroups) {
+    if (!g.stream) continue;
+    if ((e = cudaEventRecord(g.done, g.stream)) != cudaSuccess) return cuda_fail("join record", e);
+    if ((e = cudaStreamWaitEvent(s, g.done, 0)) != cudaSuccess) return cuda_fail("join wait", e);
+  }
+  if (launch_err != cudaSuccess) return cuda_fail("launch", launch_err);
   return ASP_OK;
 }
 
