@@ -49,7 +49,7 @@ enum ModeClass : int { CLS_EMBED = 0, CLS_FILL = 1, CLS_TMAP = 2, CLS_SUB = 3 };
 
 namespace bts {
 
-constexpr int kStages = 3;  // W-block ring depth
+constexpr int kMaxStages = 8;  // W-block ring depth: 3 by default, deeper for few right-hand sides
 constexpr int kRing = 3;    // per-thread input ring depth
 
 struct Geometry {
@@ -59,16 +59,17 @@ struct Geometry {
 
 __host__ __device__ inline size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
 
-template <typename R, int TR_, int TC, int LC, int NCW>
+template <typename R, int TR_, int TC, int LC, int NCW, int STG = 3, int KS = 1>
 struct Tiling {
+  static_assert(STG >= 2 && STG <= kMaxStages, "W-block ring depth");
   using C = Cx<R>;
-  static constexpr int TR = TR_;               // rows per thread (2 or 4)
-  static constexpr int WR = (32 / LC) * TR;    // rows per warp
+  static constexpr int TR = TR_;                   // rows per thread (2 or 4)
+  static constexpr int WR = (32 / (LC * KS)) * TR;  // rows per warp
   static constexpr int WC = LC * TC;           // right-hand sides per warp
   static constexpr int NR = WC * NCW;          // right-hand sides per CTA
   static constexpr int E = TR * TC;            // panel entries per thread
   __host__ __device__ static size_t bars() { return 64; }
-  __host__ __device__ static size_t wst(const Geometry& g) { return (size_t)kStages * g.wstage * sizeof(C); }
+  __host__ __device__ static size_t wst(const Geometry& g) { return (size_t)STG * g.wstage * sizeof(C); }
   __host__ __device__ static size_t ybuf(const Geometry& g) { return (size_t)2 * g.wcap * NR * sizeof(C); }
   __host__ __device__ static size_t ring(int nt) { return (size_t)kRing * E * nt * sizeof(C); }
   __host__ __device__ static size_t total(const Geometry& g, int nt) {
@@ -109,10 +110,11 @@ template <typename C, int TC, int PS> __device__ __forceinline__ void st_cols(C*
   }
 }
 
-template <typename R, int TRT, int TC, int LC, int NCW, int MAXT, int MINB, int CLS>
+template <typename R, int TRT, int TC, int LC, int NCW, int MAXT, int MINB, int CLS, int STG, int KS>
 __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geometry G) {
   using C = Cx<R>;
-  using T = Tiling<R, TRT, TC, LC, NCW>;
+  using T = Tiling<R, TRT, TC, LC, NCW, STG, KS>;
+  constexpr int kStages = STG;
   constexpr int TR = T::TR, WR = T::WR, WC = T::WC, NR = T::NR, E = T::E;
   constexpr int CB = (int)sizeof(C);
   constexpr int PS = 2 * LC;  // column distance between a thread's pairs
@@ -127,8 +129,13 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int wr = warp / NCW, wc = warp % NCW;
-  const int i0 = wr * WR + (lane / LC) * TR;                            // first row of the tile
-  const int r0 = wc * WC + (TC == 1 ? (lane % LC) : 2 * (lane % LC));  // first column of the tile
+  // lane = (row group * LC + column lane) * KS + column slice: with KS > 1 the
+  // KS lanes of a group share the tile and split the block's columns j
+  const int js = lane % KS;
+  const bool wlane = js == 0;  // the lane of a group that stores the tile's results
+  const int cl = (lane / KS) % LC;
+  const int i0 = wr * WR + (lane / (LC * KS)) * TR;             // first row of the tile
+  const int r0 = wc * WC + (TC == 1 ? cl : 2 * cl);            // first column of the tile
   auto rhs_of = [&](int c) { return TC == 1 ? r0 : r0 + (c & 1) + (c >> 1) * PS; };
   const int n = P.n, ldv = P.ldv, lda = P.ldacc, ldT = P.ldT;
   const C* __restrict__ Wg = reinterpret_cast<const C*>(P.W);
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
 #pragma unroll
           for (int c = 0; c < TC; ++c) y[c] = carry[a][c];
         }
-        st_cols<C, TC, PS>(yb + (size_t)(i0 + a) * NR + r0, y);
+        if (wlane) st_cols<C, TC, PS>(yb + (size_t)(i0 + a) * NR + r0, y);
       }
       __syncthreads();
       if (s_abort) return;
@@ -318,10 +325,10 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
 #pragma unroll
         for (int c = 0; c < TC; ++c) acc[a][c] = czero<R>();
       if (row_ok[0]) {
-        const C* yj = yb + r0;
-        const C* wj = Wk + i0;
+        const C* yj = yb + r0 + (size_t)js * NR;
+        const C* wj = Wk + i0 + (size_t)js * wp;
 #pragma unroll 2
-        for (int j = 0; j < w; ++j) {
+        for (int j = js; j < w; j += KS) {
           C yv[TC];
           ld_cols<C, TC, PS>(yj, yv);
           C wv[TR];
@@ -331,9 +338,20 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
           for (int a = 0; a < TR; ++a)
 #pragma unroll
             for (int c = 0; c < TC; ++c) cfma(acc[a][c], wv[a], yv[c]);
-          yj += NR;
-          wj += wp;
+          yj += KS * NR;
+          wj += KS * wp;
         }
+      }
+      if constexpr (KS > 1) {  // every lane of the group ends with the full sums
+#pragma unroll
+        for (int off = 1; off < KS; off <<= 1)
+#pragma unroll
+          for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int c = 0; c < TC; ++c) {
+              acc[a][c].x += __shfl_xor_sync(0xffffffffu, acc[a][c].x, off);
+              acc[a][c].y += __shfl_xor_sync(0xffffffffu, acc[a][c].y, off);
+            }
       }
 
       // ---- epilogue
@@ -342,7 +360,7 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
         if (!row_ok[a]) continue;
         C x[TC];
         if (fwd) {
-          if (k <= n - 3) st_cols<C, TC, PS>(zrow[a] + (long long)k * zstep + r0, acc[a]);
+          if (k <= n - 3 && wlane) st_cols<C, TC, PS>(zrow[a] + (long long)k * zstep + r0, acc[a]);
           if (k != n - 1) {
 #pragma unroll
             for (int c = 0; c < TC; ++c) carry[a][c] = acc[a][c];
@@ -361,7 +379,7 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
         }
 #pragma unroll
         for (int c = 0; c < TC; ++c) carry[a][c] = x[c];
-        if (out_row[a]) {
+        if (out_row[a] && wlane) {
           C* o = out_base[a] + (long long)k * out_step;
 #pragma unroll
           for (int c = 0; c < TC; ++c)
@@ -373,7 +391,7 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
                 o[rhs_of(c)] = x[c];
             }
         }
-        if (CLS == CLS_EMBED) {
+        if (CLS == CLS_EMBED && wlane) {
           if (trR[a]) {
 #pragma unroll
             for (int c = 0; c < TC; ++c)
@@ -396,10 +414,13 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
 }
 
 // TRT: rows per thread.  MAXT / MINB: largest CTA the instance is compiled for
-// and the number of such CTAs per SM its register budget is sized for.
-template <typename R, int TRT, int TC, int LC, int NCW, int CLS, int MAXT = 512, int MINB = 1>
+// and the number of such CTAs per SM its register budget is sized for.  STG:
+// W-block ring depth (few right-hand sides do little work per block, so they
+// need more blocks in flight to keep HBM busy).
+template <typename R, int TRT, int TC, int LC, int NCW, int CLS, int MAXT = 512, int MINB = 1, int STG = 3,
+          int KS = 1>
 cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
-  using T = Tiling<R, TRT, TC, LC, NCW>;
+  using T = Tiling<R, TRT, TC, LC, NCW, STG, KS>;
   const int nrw = (wcap + T::WR - 1) / T::WR;
   const int nt = 32 * nrw * NCW;
   if (nt > MAXT) return cudaErrorInvalidValue;
@@ -411,7 +432,7 @@ cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
   G.wstage = wcap * wpc + T::WR * nrw + 2;
   if (sizeof(R) == 4) G.wstage = (G.wstage + 1) & ~1;
   const size_t smem = T::total(G, nt);
-  auto kern = btsolve_kernel<R, TRT, TC, LC, NCW, MAXT, MINB, CLS>;
+  auto kern = btsolve_kernel<R, TRT, TC, LC, NCW, MAXT, MINB, CLS, STG, KS>;
   cudaError_t e = ensure_dyn_smem((const void*)kern, smem);
   if (e != cudaSuccess) return e;
   int grid = P.njobs < P.zslots ? P.njobs : P.zslots;

@@ -12,18 +12,18 @@ cudaError_t launch_btsolve_apply(Handle& H, const SolveParams& P, int cls, int c
         case 32: return run<float, 4, 2, 8, 2, CLS_EMBED, 256, 2>(H, P, wmax, s);
         case 16: return run<float, 2, 2, 8, 1, CLS_EMBED>(H, P, wmax, s);
         case 8: return run<float, 2, 2, 4, 1, CLS_EMBED>(H, P, wmax, s);
-        case 4: return run<float, 2, 2, 2, 1, CLS_EMBED>(H, P, wmax, s);
-        case 2: return run<float, 2, 2, 1, 1, CLS_EMBED>(H, P, wmax, s);
-        case 1: return run<float, 2, 1, 1, 1, CLS_EMBED>(H, P, wmax, s);
+        case 4: return run<float, 2, 2, 2, 1, CLS_EMBED, 512, 1, 6>(H, P, wmax, s);
+        case 2: return run<float, 2, 2, 1, 1, CLS_EMBED, 512, 1, 6, 4>(H, P, wmax, s);
+        case 1: return run<float, 2, 1, 1, 1, CLS_EMBED, 512, 1, 6, 4>(H, P, wmax, s);
       }
     } else {
       switch (cap) {
         case 32: return run<float, 2, 2, 8, 2, CLS_FILL, 384, 2>(H, P, wmax, s);
         case 16: return run<float, 2, 2, 8, 1, CLS_FILL>(H, P, wmax, s);
         case 8: return run<float, 2, 2, 4, 1, CLS_FILL>(H, P, wmax, s);
-        case 4: return run<float, 2, 2, 2, 1, CLS_FILL>(H, P, wmax, s);
-        case 2: return run<float, 2, 2, 1, 1, CLS_FILL>(H, P, wmax, s);
-        case 1: return run<float, 2, 1, 1, 1, CLS_FILL>(H, P, wmax, s);
+        case 4: return run<float, 2, 2, 2, 1, CLS_FILL, 512, 1, 6>(H, P, wmax, s);
+        case 2: return run<float, 2, 2, 1, 1, CLS_FILL, 512, 1, 6, 4>(H, P, wmax, s);
+        case 1: return run<float, 2, 1, 1, 1, CLS_FILL, 512, 1, 6, 4>(H, P, wmax, s);
       }
     }
   } else {

@@ -42,30 +42,39 @@ namespace {
 constexpr int kWarps = 8;                       // consumer warps
 constexpr int kConsumers = kWarps * 32;
 constexpr int kChainThreads = kConsumers + 32;  // + the producer warp
-constexpr int kRhs = 32;     // right-hand sides per launch (two per lane, 16 lanes)
-// chunk width and ring depths (fewer, larger chunks: each handoff costs about a microsecond)
-// (the widest complex64 tile takes narrower chunks so that everything fits the 227 KB)
-template <typename R, int RPL> struct ChainKC { static constexpr int v = 64, ts = 6, ss = 3; };
-template <int RPL> struct ChainKC<float, RPL> {
-  static constexpr int v = RPL <= 7 ? 256 : 128, ts = RPL <= 7 ? 3 : 6, ss = RPL <= 7 ? 2 : 3;
+constexpr int kRhs = 32;     // most right-hand sides per launch
+// Chunk width and ring depths: fewer, larger chunks (each handoff costs about
+// a microsecond) as far as shared memory allows.  MRT: map rows a CTA holds
+// (the launcher gives a CTA at most 16 rows).
+template <typename R, int MRT, int NR> struct ChainKC { static constexpr int v = 64, ts = 6, ss = 3; };
+template <int MRT, int NR> struct ChainKC<float, MRT, NR> {
+  static constexpr bool wide = MRT <= 14 || NR <= 8;
+  static constexpr int v = wide ? 256 : 128, ts = wide ? (NR <= 8 ? 4 : 3) : 6, ss = wide ? 2 : 3;
 };
 
-template <typename R, int RPL> struct ChainLayout {
+// Lane layout: RP right-hand-side pairs across a warp row, RH = 32 / RP row
+// groups of RPL rows each.  RP = 16 serves up to 32 right-hand sides, RP = 4
+// up to 8, RP = 1 up to 2 (fewer right-hand sides do proportionally less work);
+// lanes whose rows lie past MRT sit out the products.
+template <typename R, int RPL, int RP> struct ChainLayout {
   using C = Cx<R>;
-  static constexpr int KC = ChainKC<R, RPL>::v;
-  static constexpr int kTStages = ChainKC<R, RPL>::ts;  // map-chunk ring depth
-  static constexpr int kSStages = ChainKC<R, RPL>::ss;  // trace-chunk ring depth
-  static constexpr int KCP = KC + 2;  // padded map row: rows RPL apart fall in different banks
-  static constexpr int MR = 2 * RPL;  // rows per CTA
+  static constexpr int RH = 32 / RP;
+  static constexpr int MR = RH * RPL;              // rows the lane layout covers
+  static constexpr int MRT = MR < 16 ? MR : 16;    // rows a CTA holds
+  static constexpr int NR = 2 * RP;                // right-hand sides per launch
+  static constexpr int KC = ChainKC<R, MRT, NR>::v;
+  static constexpr int kTStages = ChainKC<R, MRT, NR>::ts;  // map-chunk ring depth
+  static constexpr int kSStages = ChainKC<R, MRT, NR>::ss;  // trace-chunk ring depth
+  static constexpr int KCP = KC + 2;  // padded map row: neighbouring row groups fall in different banks
   static constexpr size_t bar_bytes = 256;
-  static constexpr size_t t_elems = (size_t)kTStages * MR * KCP;
-  static constexpr size_t s_stage = (size_t)KC * kRhs;  // a trace chunk, rows lda <= kRhs apart
+  static constexpr size_t t_elems = (size_t)kTStages * MRT * KCP;
+  static constexpr size_t s_stage = (size_t)KC * NR;  // a trace chunk, rows lda <= NR apart
   static constexpr size_t s_elems = (size_t)kSStages * s_stage;
-  static constexpr size_t d_elems = (size_t)MR * kRhs;  // the layer's own trace rows (u~_{p,p} on entry)
-  // the cross-warp reduction reuses the trace ring, in passes over row halves if needed
-  static constexpr int NPASS = ((size_t)kWarps * MR * kRhs <= s_elems) ? 1 : 2;
-  static constexpr int RPP = NPASS == 1 ? MR : RPL;  // rows per reduction pass
-  static_assert((size_t)kWarps * RPP * kRhs <= s_elems, "reduction buffer must fit in the trace ring");
+  static constexpr size_t d_elems = (size_t)MRT * NR;  // the layer's own trace rows (u~_{p,p} on entry)
+  // the cross-warp reduction reuses the trace ring, in passes over halves of the rows if needed
+  static constexpr int NPASS = ((size_t)kWarps * MRT * NR <= s_elems) ? 1 : 2;
+  static constexpr int RPP = (MRT + NPASS - 1) / NPASS;  // rows per reduction pass
+  static_assert((size_t)kWarps * RPP * NR <= s_elems, "reduction buffer must fit in the trace ring");
   static_assert((2 * (kTStages + kSStages) + 1) * 8 <= bar_bytes, "mbarrier area");
   static constexpr size_t bytes() { return bar_bytes + (t_elems + s_elems + d_elems) * sizeof(C); }
   static_assert(bar_bytes + (t_elems + s_elems + d_elems) * sizeof(C) + 64 <= 232448, "shared memory per CTA");
@@ -118,11 +127,11 @@ __device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
 }
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory"); }
 
-template <typename R, int RPL>
+template <typename R, int RPL, int RP>
 __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) {
   using C = Cx<R>;
-  using Lay = ChainLayout<R, RPL>;
-  constexpr int KC = Lay::KC, KCP = Lay::KCP, MR = Lay::MR;
+  using Lay = ChainLayout<R, RPL, RP>;
+  constexpr int KC = Lay::KC, KCP = Lay::KCP, MRT = Lay::MRT, NR = Lay::NR;
   constexpr int kTStages = Lay::kTStages, kSStages = Lay::kSStages;
   constexpr int CB = (int)sizeof(C);
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -131,10 +140,10 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
   uint64_t* fullS = emptyT + kTStages;                      // [kSStages]
   uint64_t* emptyS = fullS + kSStages;                      // [kSStages]
   uint64_t* fullD = emptyS + kSStages;                       // the layer's own trace rows
-  C* s_T = reinterpret_cast<C*>(smem_raw + Lay::bar_bytes);  // [kTStages][MR][KCP]
+  C* s_T = reinterpret_cast<C*>(smem_raw + Lay::bar_bytes);  // [kTStages][MRT][KCP]
   C* s_S = s_T + Lay::t_elems;                               // [kSStages][KC][lda]
   C* s_D = s_S + Lay::s_elems;                               // [rows][lda]
-  C* red = s_S;                                              // [kWarps][RPP][kRhs]
+  C* red = s_S;                                              // [kWarps][RPP][NR]
   __shared__ int s_abort;
   volatile int* abort = &s_abort;
 
@@ -147,8 +156,13 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
   unsigned int* bar = P.bar + (isR ? 0 : 1);
   C* acc = reinterpret_cast<C*>(isR ? P.accR : P.accL);
 
+  // this launch's columns of a trace row, rounded up to even (16 bytes for
+  // complex64; lda is even, so the padded row holds the extra column)
+  const int nr2 = (nrhs + 1) & ~1;
+  const uint32_t rb = (uint32_t)(nr2 * CB);
+  const bool whole = lda == nr2;
   const int row0 = (int)((long long)cta * n / nct);
-  const int rows = (int)((long long)(cta + 1) * n / nct) - row0;  // <= MR (checked on the host)
+  const int rows = (int)((long long)(cta + 1) * n / nct) - row0;  // <= MRT (checked on the host)
   const int nch = (n + KC - 1) / KC;
   const int layers = m - 2;
   const int total = layers * nch;  // chunks of each kind this CTA consumes
@@ -177,22 +191,39 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
       if (lane == 0) mbar_arrive_expect_tx(&fullT[st], rbytes * (uint32_t)rows);
       __syncwarp();
       for (int r = lane; r < rows; r += 32)
-        bulk_g2s(s_T + ((size_t)st * MR + r) * KCP, T + (long long)r * ldT, rbytes, &fullT[st]);
+        bulk_g2s(s_T + ((size_t)st * MRT + r) * KCP, T + (long long)r * ldT, rbytes, &fullT[st]);
     };
-    auto issue_S = [&](int g) {  // trace chunk g: rows kc .. kc+kn of the previous layer's trace; lane 0
+    // trace chunk g: rows kc .. kc+kn of the previous layer's trace, this
+    // launch's nr2 columns of each, packed nr2 apart in shared memory; with a
+    // layer's first chunk also the CTA's rows of that layer's own trace.  When
+    // the launch covers whole trace rows (lda == nr2, every handle with at most
+    // 32 right-hand sides) each is one contiguous bulk copy; otherwise one copy
+    // per row across the warp (small copies are slow, but only handles with
+    // more than 32 right-hand sides take this path)
+    auto issue_S = [&](int g) {  // whole warp
       const int t = g / nch, kc = (g - t * nch) * KC;
       const int kn = min(KC, n - kc);
       const int pp = layer_p(t);
-      if (kc == 0) {  // with a layer's first chunk: the CTA's rows of that layer's own trace
-        const uint32_t dbytes = (uint32_t)((long long)rows * lda * CB);
-        mbar_arrive_expect_tx(fullD, dbytes);
-        bulk_g2s(s_D, acc + (long long)pp * n * lda + (long long)row0 * lda, dbytes, fullD);
-      }
-      const C* src = acc + (long long)(isR ? pp - 1 : pp + 1) * n * lda + (long long)kc * lda;
-      const uint32_t bytes = (uint32_t)((long long)kn * lda * CB);  // lda even: a 16-byte multiple
       const int ss = g % kSStages;
-      mbar_arrive_expect_tx(&fullS[ss], bytes);
-      bulk_g2s(s_S + (size_t)ss * Lay::s_stage, src, bytes, &fullS[ss]);
+      if (lane == 0) {
+        if (kc == 0) mbar_arrive_expect_tx(fullD, rb * (uint32_t)rows);
+        mbar_arrive_expect_tx(&fullS[ss], rb * (uint32_t)kn);
+      }
+      __syncwarp();
+      asm volatile("fence.proxy.async.global;" ::: "memory");  // traces written by other CTAs
+      const C* own = acc + (long long)pp * n * lda + (long long)row0 * lda;
+      const C* src = acc + (long long)(isR ? pp - 1 : pp + 1) * n * lda + (long long)kc * lda;
+      C* dS = s_S + (size_t)ss * Lay::s_stage;
+      if (whole) {
+        if (lane == 0) {
+          if (kc == 0) bulk_g2s(s_D, own, rb * (uint32_t)rows, fullD);
+          bulk_g2s(dS, src, rb * (uint32_t)kn, &fullS[ss]);
+        }
+      } else {
+        if (kc == 0)
+          for (int r = lane; r < rows; r += 32) bulk_g2s(s_D + (size_t)r * nr2, own + (long long)r * lda, rb, fullD);
+        for (int kk = lane; kk < kn; kk += 32) bulk_g2s(dS + (size_t)kk * nr2, src + (long long)kk * lda, rb, &fullS[ss]);
+      }
     };
     // the producer's own bounded wait for every CTA's rows of layers < t (lane 0)
     auto grid_wait = [&](int t) {
@@ -212,11 +243,9 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
       asm volatile("fence.proxy.async.global;" ::: "memory");
       return true;
     };
-    int gT = 0, gS = 0;  // next map / trace chunk to issue
+    int gT = 0, gS = 0;  // next map / trace chunk to issue (warp-uniform)
     for (; gT < kTStages && gT < total; ++gT) issue_T(gT);
-    if (lane == 0)
-      for (; gS < kSStages && gS < nch; ++gS) issue_S(gS);
-    gS = __shfl_sync(0xffffffffu, gS, 0);
+    for (; gS < kSStages && gS < nch; ++gS) issue_S(gS);
     bool ok = true;
     // each chunk the consumers release frees one stage of each ring
     for (int c = 0; c < total && ok; ++c) {
@@ -226,21 +255,18 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
         if (!__shfl_sync(0xffffffffu, freed, 0)) { ok = false; break; }
         issue_T(gT++);
       }
-      if (lane == 0) {
-        // trace chunks whose stage is free (held chunk <= c); a layer's first
-        // chunk only once every CTA has written the previous layer
-        for (; ok && gS < total && gS <= c + kSStages; ++gS) {
+      // trace chunks whose stage is free (held chunk <= c); a layer's first
+      // chunk only once every CTA has written the previous layer
+      for (; ok && gS < total && gS <= c + kSStages; ++gS) {
+        int go = 1;
+        if (lane == 0) {
           const int prev = gS - kSStages;  // the chunk this stage held
-          if (prev >= 0 && !wait_or_abort(&emptyS[prev % kSStages], (uint32_t)((prev / kSStages) & 1), abort)) {
-            ok = false;
-            break;
-          }
-          if (gS % nch == 0 && !grid_wait(gS / nch)) { ok = false; break; }
-          issue_S(gS);
+          if (prev >= 0 && !wait_or_abort(&emptyS[prev % kSStages], (uint32_t)((prev / kSStages) & 1), abort)) go = 0;
+          else if (gS % nch == 0 && !grid_wait(gS / nch)) go = 0;
         }
+        if (!__shfl_sync(0xffffffffu, go, 0)) { ok = false; break; }
+        issue_S(gS);
       }
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      gS = __shfl_sync(0xffffffffu, gS, 0);
     }
     // drain: the last chunk issued into each stage has landed (bounded)
     if (lane == 0) {
@@ -254,8 +280,9 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
   // ================================================================ consumers
   // After an abort the consumers still pass every consumer barrier and arrive at
   // the grid barrier (so that no warp or CTA waits on them), doing no work.
-  const int rp = lane & 15;  // right-hand-side pair of this lane
-  const int rh = lane >> 4;  // row half: rows rh*RPL .. rh*RPL+RPL-1
+  const int rp = lane % RP;  // right-hand-side pair of this lane
+  const int rh = lane / RP;  // row group: rows rh*RPL .. rh*RPL+RPL-1
+  const bool active = rh * RPL + RPL <= MRT;  // this lane's rows are held (MRT is a multiple of RPL)
   bool live = true;
   for (int t = 0; t < layers; ++t) {
     C* dst = acc + (long long)layer_p(t) * n * lda;
@@ -277,7 +304,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
         break;
       }
       const int kn = min(KC, n - ch * KC);
-      const C* bT = s_T + (size_t)st * MR * KCP + (size_t)rh * RPL * KCP;
+      const C* bT = s_T + (size_t)st * MRT * KCP + (size_t)(active ? rh * RPL : 0) * KCP;
       const C* bS = s_S + (size_t)ss * Lay::s_stage + 2 * rp;
       const int npair = kn >> 1;
       // column pairs warp, warp + kWarps, ...; the next pair's operands are
@@ -285,8 +312,8 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
       C sv[sizeof(R) == 4 ? 2 : 1][4], tv[sizeof(R) == 4 ? 2 : 1][RPL][2];
       auto ld = [&](int b, int kp) {
         const int kk = 2 * kp;
-        pair_ld(bS + kk * lda, sv[b][0], sv[b][1]);
-        pair_ld(bS + (kk + 1) * lda, sv[b][2], sv[b][3]);
+        pair_ld(bS + kk * nr2, sv[b][0], sv[b][1]);
+        pair_ld(bS + (kk + 1) * nr2, sv[b][2], sv[b][3]);
 #pragma unroll
         for (int i = 0; i < RPL; ++i) pair_ld(bT + i * KCP + kk, tv[b][i][0], tv[b][i][1]);
       };
@@ -317,7 +344,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
       if ((kn & 1) && warp == npair % kWarps) {  // odd last column
         const int kk = kn - 1;
         C s0, s1;
-        pair_ld(bS + kk * lda, s0, s1);
+        pair_ld(bS + kk * nr2, s0, s1);
 #pragma unroll
         for (int i = 0; i < RPL; ++i) {
           const C tv = bT[i * KCP + kk];
@@ -346,24 +373,27 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
     live = live && !*abort;
 #pragma unroll
     for (int h = 0; h < Lay::NPASS; ++h) {
-      if (live && (Lay::NPASS == 1 || rh == h)) {
+      constexpr int RPP = Lay::RPP;
+      if (live && active) {
 #pragma unroll
         for (int i = 0; i < RPL; ++i) {
-          const int rr = (Lay::NPASS == 1 ? rh * RPL : 0) + i;
-          C* rw = red + ((size_t)warp * Lay::RPP + rr) * kRhs + 2 * rp;
-          rw[0] = a[i][0];
-          rw[1] = a[i][1];
+          const int rr = rh * RPL + i - h * RPP;  // this lane's row within the pass
+          if (rr >= 0 && rr < RPP) {
+            C* rw = red + ((size_t)warp * RPP + rr) * NR + 2 * rp;
+            rw[0] = a[i][0];
+            rw[1] = a[i][1];
+          }
         }
       }
       consumer_sync();
-      for (int o = tid; live && o < Lay::RPP * nrhs; o += kConsumers) {
+      for (int o = tid; live && o < RPP * nrhs; o += kConsumers) {
         const int rr = o / nrhs, r = o - rr * nrhs;
-        const int row = (Lay::NPASS == 1 ? 0 : h * RPL) + rr;
+        const int row = h * RPP + rr;
         if (row >= rows) continue;
         C s = czero<R>();
 #pragma unroll
-        for (int wv = 0; wv < kWarps; ++wv) s = cadd(s, red[((size_t)wv * Lay::RPP + rr) * kRhs + r]);
-        dst[(long long)(row0 + row) * lda + r] = cadd(s_D[row * lda + r], s);
+        for (int wv = 0; wv < kWarps; ++wv) s = cadd(s, red[((size_t)wv * RPP + rr) * NR + r]);
+        dst[(long long)(row0 + row) * lda + r] = cadd(s_D[row * nr2 + r], s);
       }
       // red (shared) and the trace (global) are next written or read by bulk copies
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -377,19 +407,22 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(ChainParams P) 
   }
 }
 
-template <typename R, int RPL> cudaError_t launch_rpl(const ChainParams& P, int grid, cudaStream_t s) {
-  const size_t smem = ChainLayout<R, RPL>::bytes();
-  cudaError_t e = ensure_dyn_smem((const void*)chain_kernel<R, RPL>, smem);
+template <typename R, int RPL, int RP> cudaError_t launch_rpl(const ChainParams& P, int grid, cudaStream_t s) {
+  const size_t smem = ChainLayout<R, RPL, RP>::bytes();
+  cudaError_t e = ensure_dyn_smem((const void*)chain_kernel<R, RPL, RP>, smem);
   if (e != cudaSuccess) return e;
   ChainParams Q = P;
   void* args[] = {&Q};
-  return cudaLaunchCooperativeKernel((void*)chain_kernel<R, RPL>, dim3(grid), dim3(kChainThreads), args, smem, s);
+  return cudaLaunchCooperativeKernel((void*)chain_kernel<R, RPL, RP>, dim3(grid), dim3(kChainThreads), args, smem, s);
 }
 
+// maxrows <= 16 (the launcher sizes the grid so)
 template <typename R> cudaError_t launch_prec(const ChainParams& P, int grid, int maxrows, cudaStream_t s) {
-  if (maxrows <= 8) return launch_rpl<R, 4>(P, grid, s);
-  if (maxrows <= 14) return launch_rpl<R, 7>(P, grid, s);
-  return launch_rpl<R, 8>(P, grid, s);
+  if (P.nrhs <= 2) return launch_rpl<R, 1, 1>(P, grid, s);   // 32 rows per CTA at most
+  if (P.nrhs <= 8) return launch_rpl<R, 2, 4>(P, grid, s);   // 16 rows
+  if (maxrows <= 8) return launch_rpl<R, 4, 16>(P, grid, s);
+  if (maxrows <= 14) return launch_rpl<R, 7, 16>(P, grid, s);
+  return launch_rpl<R, 8, 16>(P, grid, s);
 }
 
 }  // namespace

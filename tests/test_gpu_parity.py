@@ -135,6 +135,26 @@ def test_apply_matches_oracle(name, precision, tol):
     assert rel(z, zo) <= tol, rel(z, zo)
 
 
+# Layers longer than one sweep-chain chunk (256 trace rows), right-hand-side
+# counts that take every chain lane layout (32-wide blocks with a trace row
+# stride above 32; 8-wide; 2-wide).
+CHAIN_WIDE = {
+    "n300_34rhs": (300, 24 * math.pi, 4, 3, "layered", 34, None),
+    "n300_5rhs": (300, 24 * math.pi, 4, 3, "lens", 5, None),
+}
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4)])
+@pytest.mark.parametrize("name", list(CHAIN_WIDE))
+def test_apply_matches_oracle_long_layers(name, precision, tol):
+    n, om, g, b, vel, R, ga = CHAIN_WIDE[name]
+    P = W.small_problem(2, n, om, g, b, vel, nrhs=R, pml_aux=ga)
+    h = handle(P, precision)
+    z = host(h.apply_preconditioner(dev(P.f)))
+    zo = oracle_pc(P).apply(P.f)
+    assert rel(z, zo) <= tol, rel(z, zo)
+
+
 def test_apply_is_linear_and_rhs_independent():
     """Each right-hand side's result is the same alone and inside a batch."""
     P = small("33_rhs")
