@@ -122,13 +122,15 @@ __global__ void __launch_bounds__(256) form_store_kernel(Slab3Params P, FactorCo
 
 // ------------------------------------------------------------------- panel
 // Grid (CL, nlist) with clusters of CL CTAs along x: CTA rank q holds rows
-// [q*rpc, (q+1)*rpc) of the panel in shared memory; warp w owns the local rows
-// w, w + kPanelWarps, ... for both the pivot search and the updates, so within a
-// step only the CTA-wide candidate reduction needs a block barrier.  Per step
+// [q*rpc, (q+1)*rpc) of the panel in shared memory; warp w owns the contiguous
+// local rows [w*R, (w+1)*R) for both the pivot search and the updates, so within
+// a step only the CTA-wide candidate reduction needs a block barrier (and the
+// search, one row per lane, reads rows kLDP apart: no bank conflicts).  Per step
 // every CTA pushes its pivot candidate (|value|^2, row, and the row's kPW
 // entries) into a slot of every CTA of the cluster (distributed shared memory,
 // slots double-buffered by step parity); after one cluster barrier each CTA
-// picks the same winner from its own slots and applies the step to its rows.
+// picks the same winner from its own slots and applies the step to its rows,
+// two rows per warp instruction (a half-warp per row, two columns per lane).
 constexpr int kMaxCluster = 8;
 
 template <typename R>
@@ -155,6 +157,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
   __shared__ int wrow[kPanelWarps];
   __shared__ int pivs[kPW];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rpw = (nrows + kPanelWarps - 1) / kPanelWarps;  // rows per warp
+  const int wlo = min(warp * rpw, nrows), whi = min(wlo + rpw, nrows);
   C* A = work<R>(P, S, buf);
   int* piv_row = P.piv + S.poff;
   int* col_of_row = piv_row + nb;
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
     // ---- candidate of this warp's rows: largest |A[i][c]| over rows not yet pivots
     R best = R(-1);
     int bi = INT_MAX;
-    for (int l = warp + kPanelWarps * lane; l < nrows; l += kPanelWarps * 32) {
+    for (int l = wlo + lane; l < whi; l += 32) {
       if (rstep[l] < 0) {
         const C v = Ps[l * kLDP + t];
         const R a = v.x * v.x + v.y * v.y;
@@ -220,35 +224,46 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
     const bool okp = gr >= 0 && gr < nb;
     if (!(gb > R(0)) || !isfinite(gb)) bad = true;
     if (okp) {
-      const C pl = slot_row[par][gq][lane];
-      const C inv = crecip(slot_row[par][gq][t]);
-      const C pscaled = (lane == t) ? inv : cmul(pl, inv);  // the pivot row's new entries
-      const int lg = gr - row0;                               // local index of the pivot row (if here)
-      // four rows per pass: all reads, one warp barrier, then all writes (lane t
-      // overwrites the column the other lanes read)
-      for (int l0 = warp; l0 < nrows; l0 += 4 * kPanelWarps) {
-        C v[4];
+      // lane: half-warp hw takes rows wlo + hw, wlo + hw + 2, ...; columns cj and cj + 1
+      const int hw = lane >> 4, cj = 2 * (lane & 15);
+      const C* prow = slot_row[par][gq];
+      const C inv = crecip(prow[t]);
+      const C pl0 = prow[cj], pl1 = prow[cj + 1];
+      // the pivot row's new entries
+      const C ps0 = (cj == t) ? inv : cmul(pl0, inv);
+      const C ps1 = (cj + 1 == t) ? inv : cmul(pl1, inv);
+      const int lg = gr - row0;  // local index of the pivot row (if here)
+      // four row pairs per pass: all reads, one warp barrier, then all writes
+      // (the lanes of column t overwrite the entry the other lanes read)
+      for (int l0 = wlo; l0 < whi; l0 += 8) {  // warp-uniform bound (the barriers below)
+        C v0[4], v1[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-          const int l = l0 + a * kPanelWarps;
-          if (l < nrows) {
+          const int l = l0 + 2 * a + hw;
+          if (l < whi) {
             const C* rowp = Ps + l * kLDP;
             const C f = cmul(rowp[t], inv);
-            C x = rowp[lane];
-            cfms(x, f, pl);
-            if (lane == t) { x.x = -f.x; x.y = -f.y; }
-            v[a] = (l == lg) ? pscaled : x;
+            C x0 = rowp[cj], x1 = rowp[cj + 1];
+            cfms(x0, f, pl0);
+            cfms(x1, f, pl1);
+            if (cj == t) { x0.x = -f.x; x0.y = -f.y; }
+            if (cj + 1 == t) { x1.x = -f.x; x1.y = -f.y; }
+            v0[a] = (l == lg) ? ps0 : x0;
+            v1[a] = (l == lg) ? ps1 : x1;
           }
         }
         __syncwarp();
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-          const int l = l0 + a * kPanelWarps;
-          if (l < nrows && lane < pw) Ps[l * kLDP + lane] = v[a];
+          const int l = l0 + 2 * a + hw;
+          if (l < whi) {
+            if (cj < pw) Ps[l * kLDP + cj] = v0[a];
+            if (cj + 1 < pw) Ps[l * kLDP + cj + 1] = v1[a];
+          }
         }
         __syncwarp();
       }
-      if (lg >= 0 && lg < nrows && (lg % kPanelWarps) == warp && lane == 0) rstep[lg] = c;
+      if (lg >= wlo && lg < whi && lane == 0) rstep[lg] = c;
       if (tid == 0 && q == 0) {
         piv_row[c] = gr;
         col_of_row[gr] = c;
