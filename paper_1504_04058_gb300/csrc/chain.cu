@@ -4,7 +4,7 @@
 //     (u~_{p,1:p})^R = (G~_p^R (u~_{p-1,1:p-1})^R)^R + (u~_{p,p})^R,   p = 2..m-1
 //     (u~_{p,p:m})^L = (u~_{p,p})^L + (G~_p^L (u~_{p+1,p+1:m})^L)^L,   p = m-1..2
 // Only the traces travel from layer to layer, so the map w -> (G~_p^R w)^R is
-// applied as a dense n x n matrix T_p^R built once at factor time (btsolve.cu,
+// applied as a dense n x n matrix T_p^R built once at factor time (btsolve.cuh,
 // MODE_TMAP_R); the full layer fields G~_p^R w are then computed for all p at
 // once afterwards.  This turns a chain of 2(m-1) dependent banded solves, each
 // n block-steps long, into 2(m-2) dependent dense products spread over the

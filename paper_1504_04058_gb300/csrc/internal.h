@@ -32,7 +32,7 @@ struct SubDesc {
   long long toff;    // element offset of its trace-transfer map (-1: none)
 };
 
-// Solve modes of the batched block-tridiagonal solver (btsolve.cu).
+// Solve modes of the batched block-tridiagonal solver (btsolve.cuh).
 enum SolveMode : int {
   MODE_EMBED = 0,   // G~_q^M: right-hand side = input restricted to X_q
   MODE_FILL_R = 1,  // G~_p^R: right-hand side = -(1/h^2) accR[p-1] on local column 0
