@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) form_store_kernel(Slab3Params P, FactorCo
 // entries) into a slot of every CTA of the cluster (distributed shared memory,
 // slots double-buffered by step parity); after one cluster barrier each CTA
 // picks the same winner from its own slots and applies the step to its rows,
-// two rows per warp instruction (a half-warp per row, two columns per lane).
+// two rows per warp instruction (a half-warp per row, columns c and c + 16 per lane).
 constexpr int kMaxCluster = 8;
 
 template <typename R>
@@ -224,14 +224,15 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
     const bool okp = gr >= 0 && gr < nb;
     if (!(gb > R(0)) || !isfinite(gb)) bad = true;
     if (okp) {
-      // lane: half-warp hw takes rows wlo + hw, wlo + hw + 2, ...; columns cj and cj + 1
-      const int hw = lane >> 4, cj = 2 * (lane & 15);
+      // lane: half-warp hw takes rows wlo + hw, wlo + hw + 2, ...; columns cj and cj + 16
+      // (unit stride across the half-warp: no bank conflicts)
+      const int hw = lane >> 4, cj = lane & 15, cj1 = cj + 16;
       const C* prow = slot_row[par][gq];
       const C inv = crecip(prow[t]);
-      const C pl0 = prow[cj], pl1 = prow[cj + 1];
+      const C pl0 = prow[cj], pl1 = prow[cj1];
       // the pivot row's new entries
       const C ps0 = (cj == t) ? inv : cmul(pl0, inv);
-      const C ps1 = (cj + 1 == t) ? inv : cmul(pl1, inv);
+      const C ps1 = (cj1 == t) ? inv : cmul(pl1, inv);
       const int lg = gr - row0;  // local index of the pivot row (if here)
       // four row pairs per pass: all reads, one warp barrier, then all writes
       // (the lanes of column t overwrite the entry the other lanes read)
@@ -243,11 +244,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
           if (l < whi) {
             const C* rowp = Ps + l * kLDP;
             const C f = cmul(rowp[t], inv);
-            C x0 = rowp[cj], x1 = rowp[cj + 1];
+            C x0 = rowp[cj], x1 = rowp[cj1];
             cfms(x0, f, pl0);
             cfms(x1, f, pl1);
             if (cj == t) { x0.x = -f.x; x0.y = -f.y; }
-            if (cj + 1 == t) { x1.x = -f.x; x1.y = -f.y; }
+            if (cj1 == t) { x1.x = -f.x; x1.y = -f.y; }
             v0[a] = (l == lg) ? ps0 : x0;
             v1[a] = (l == lg) ? ps1 : x1;
           }
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
           const int l = l0 + 2 * a + hw;
           if (l < whi) {
             if (cj < pw) Ps[l * kLDP + cj] = v0[a];
-            if (cj + 1 < pw) Ps[l * kLDP + cj + 1] = v1[a];
+            if (cj1 < pw) Ps[l * kLDP + cj1] = v1[a];
           }
         }
         __syncwarp();
