@@ -218,6 +218,17 @@ int asp_phase_times(asp_handle* h, double* ms, long long* launches, int nphases)
 int asp_residual_norms_noalloc(const asp_params* p, const double* c, const void* f, const void* u, int nrhs,
                                double* rel_res, void* stream);
 
+/* Self-test of failure detection on the device.  Launches one CTA that waits,
+ * with the library's bounded mbarrier wait and a limit of `polls` polls, on a
+ * barrier that nothing arrives on.  Every device-side wait of the library gives
+ * up the same way (after 2^26 polls) and reports through the error word; this
+ * call runs that path on purpose with a short limit.  Expected result:
+ * ASP_ERR_TIMEOUT, with the context still usable for further calls.  ASP_OK would
+ * mean the barrier completed (a library defect).  polls: 1 .. 2^26, else
+ * ASP_ERR_INVALID.  Allocates and frees 8 bytes of device memory; synchronizes
+ * `stream`. */
+int asp_selftest_bounded_wait(int polls, void* stream);
+
 /* Free everything the handle owns.  NULL is accepted; calling it twice on the
  * same pointer is undefined (the handle is gone after the first call). */
 void asp_destroy(asp_handle* h);

@@ -19,7 +19,8 @@ from . import _lib
 from ._lib import (ASP_PREC_C64, ASP_PREC_C128, KIND_L, KIND_M, KIND_R, AspError,  # noqa: F401
                    asp_params, asp_solve_info)
 
-__all__ = ["asp_setup", "asp_footprint_bytes", "asp_residual_norms_noalloc", "AspHandle", "make_params",
+__all__ = ["asp_setup", "asp_footprint_bytes", "asp_residual_norms_noalloc", "asp_selftest_bounded_wait",
+           "AspHandle", "make_params",
            "AspError",
            "ASP_PREC_C64", "ASP_PREC_C128", "KIND_M", "KIND_R", "KIND_L"]
 
@@ -191,6 +192,13 @@ def asp_residual_norms_noalloc(params: asp_params, c, f, u, rel_res=None, stream
         ctypes.c_void_p(u.data_ptr()), nrhs, ctypes.c_void_p(rel_res.data_ptr()),
         ctypes.c_void_p(_stream_ptr(stream))), "asp_residual_norms_noalloc")
     return rel_res
+
+
+def asp_selftest_bounded_wait(polls: int = 4096, stream=None) -> int:
+    """Run the device-side bounded-wait path on purpose (a barrier nothing
+    arrives on) and return the library's status code: ASP_ERR_TIMEOUT is the
+    expected result."""
+    return int(_lib.load().asp_selftest_bounded_wait(int(polls), ctypes.c_void_p(_stream_ptr(stream))))
 
 
 def asp_setup(c, params: asp_params) -> AspHandle:

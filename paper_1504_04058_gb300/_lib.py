@@ -33,6 +33,7 @@ EXPORTS = [
     "asp_apply_preconditioner", "asp_matvec", "asp_subproblem_width", "asp_subproblem_solve",
     "asp_gmres_solve", "asp_take_launch_count", "asp_set_phase_timing", "asp_phase_times",
     "asp_destroy", "asp_error_string", "asp_last_error_detail", "asp_residual_norms_noalloc",
+    "asp_selftest_bounded_wait",
 ]
 NOALLOC_MAX_N = 4096
 NOALLOC_MAX_RHS = 64
@@ -98,6 +99,7 @@ def load() -> ctypes.CDLL:
         "asp_phase_times": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), I]),
         "asp_destroy": (V, [P]),
         "asp_residual_norms_noalloc": (I, [ctypes.POINTER(asp_params), P, P, P, I, P, P]),
+        "asp_selftest_bounded_wait": (I, [I, P]),
         "asp_error_string": (ctypes.c_char_p, [I]),
         "asp_last_error_detail": (ctypes.c_char_p, []),
     }

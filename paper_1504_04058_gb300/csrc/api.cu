@@ -457,6 +457,23 @@ SolveParams base_params(Handle& H, int ldv) {
   return P;
 }
 
+// Self-test of the bounded-wait path: an mbarrier that nothing arrives on, waited
+// for with the library's wait helper and a short poll limit.  The wait must give
+// up and record ASP_ERR_TIMEOUT in the error word; no copy is in flight, so the
+// CTA then simply exits.
+__global__ void wait_selftest_kernel(int* err, uint32_t limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool done = mbar_wait(&bar, 0u, limit);  // phase 0 never completes
+  if (!done && threadIdx.x == 0) record_error(err, ASP_ERR_TIMEOUT, 0);
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_inval(&bar);
+}
+
 int check_err(Handle& H, cudaStream_t s, const char* what) {
   int e[2] = {0, 0};
   if (cudaMemcpyAsync(e, H.err, sizeof(e), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -1090,6 +1107,25 @@ long long asp_take_launch_count(asp_handle* hd) {
   long long v = hd->h.launches;
   hd->h.launches = 0;
   return v;
+}
+
+int asp_selftest_bounded_wait(int polls, void* stream) {
+  if (polls < 1 || polls > (int)(1u << 26)) return fail(ASP_ERR_INVALID, "polls out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d_err = nullptr;
+  if (cudaMalloc(&d_err, 2 * sizeof(int)) != cudaSuccess) return fail(ASP_ERR_OOM, "self-test error word");
+  int e[2] = {0, 0};
+  cudaError_t ce = cudaMemsetAsync(d_err, 0, 2 * sizeof(int), s);
+  if (ce == cudaSuccess) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(d_err, (uint32_t)polls);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(e, d_err, sizeof(e), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  cudaFree(d_err);
+  if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("self-test: ") + cudaGetErrorString(ce));
+  if (e[0] == ASP_ERR_TIMEOUT) return fail(ASP_ERR_TIMEOUT, "self-test: the bounded wait gave up, as designed");
+  return e[0];
 }
 
 }  // extern "C"

@@ -138,3 +138,12 @@ def test_footprint_matches_layer_sizes(lib):
         w = g + b - 1
         fac += n * w * (w + (w % 2))
     assert f1 > fac * 8
+
+
+def test_selftest_bounded_wait_rejects_bad_limits():
+    """The argument check of the bounded-wait self-test runs before any CUDA call."""
+    from paper_1504_04058_gb300 import _lib
+    lib = _lib.load()
+    assert lib.asp_selftest_bounded_wait(0, None) == _lib.ASP_ERR_INVALID
+    assert lib.asp_selftest_bounded_wait(-3, None) == _lib.ASP_ERR_INVALID
+    assert lib.asp_selftest_bounded_wait((1 << 26) + 1, None) == _lib.ASP_ERR_INVALID
