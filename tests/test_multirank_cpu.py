@@ -1,7 +1,8 @@
 """The N > 1 path of bench.py on CPU: two ranks over the gloo backend (one
 replica per rank, no data-path collective).  The step time the job reports
 is the maximum over ranks, the whole-job rate counts every rank's right-hand
-sides, and the reference arm runs on rank 0 only."""
+sides, the reference arm runs on rank 0 only, and a rank that dies before the
+timing collective makes the surviving rank's collective fail instead of hang."""
 import os
 import socket
 import subprocess
@@ -58,3 +59,35 @@ def test_reference_arm_runs_on_rank_zero_only():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2"],
                        capture_output=True, text=True, env=env, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def _rank_dies(rank, world, port, q):
+    import datetime
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=15))
+    import bench
+    if rank == 1:
+        os._exit(3)  # this replica fails between steps, before the timing all-reduce
+    try:
+        bench.dist_max(1.0)
+        q.put("completed")
+    except Exception as e:  # the collective reports the lost peer
+        q.put("error " + type(e).__name__)
+
+
+def test_surviving_rank_sees_a_failed_peer():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_dies, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    msg = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert msg.startswith("error"), msg
+    assert procs[1].exitcode == 3
+
