@@ -338,11 +338,24 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(Slab3Params P, int 
   const int* row_step = P.piv + S.poff + 2 * nb;
   const int tid = threadIdx.x;
   const int ty = tid >> 4, tx = tid & 15;
+  // The accumulators start from this thread's entries of the tile, loaded before
+  // the staging below so that their latency overlaps it and the products:
+  // A[i][j] for the other rows, zero for the pivot rows of the step block (their
+  // old values leave through Z).  The epilogue then only stores.
   C acc[8][4];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < 8; ++a) {
+    const int i = i0 + ty + 16 * a;
+    const int st = i < nb ? row_step[i] : -1;
+    const bool piv = st >= a0 && st < a0 + K;
+    const C* rowp = A + (long long)min(i, nb - 1) * ld;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = czero<R>();
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + tx + 16 * b;
+      const bool in = i < nb && j < jhi && !(j >= a0 && j < a0 + K);
+      acc[a][b] = (in && !piv) ? rowp[j] : czero<R>();
+    }
+  }
   for (int kc = 0; kc < K; kc += kPW) {
     const int kw = min(kPW, K - kc);
     __syncthreads();
@@ -373,14 +386,12 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(Slab3Params P, int 
   for (int a = 0; a < 8; ++a) {
     const int i = i0 + ty + 16 * a;
     if (i >= nb) continue;
-    const int st = row_step[i];
-    const bool piv = st >= a0 && st < a0 + K;  // this row's old value leaves through Z
     C* rowp = A + (long long)i * ld;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int j = j0 + tx + 16 * b;
       if (j >= jhi || (j >= a0 && j < a0 + K)) continue;
-      rowp[j] = piv ? acc[a][b] : cadd(rowp[j], acc[a][b]);
+      rowp[j] = acc[a][b];
     }
   }
 }
