@@ -141,6 +141,7 @@ def test_apply_matches_oracle(name, precision, tol):
 CHAIN_WIDE = {
     "n300_34rhs": (300, 24 * math.pi, 4, 3, "layered", 34, None),
     "n300_5rhs": (300, 24 * math.pi, 4, 3, "lens", 5, None),
+    "n300_17rhs": (300, 24 * math.pi, 4, 3, "layered", 17, None),
 }
 
 
