@@ -18,11 +18,11 @@
 //   * a producer warp moves both operands into shared memory by bulk (TMA)
 //     copies that complete on mbarriers: map rows, KC columns per chunk, in a
 //     kTStages-deep ring (the maps do not depend on the sweep, so this ring runs
-//     ahead across layer boundaries), and trace chunks (KC rows of the previous
-//     layer's trace, one contiguous block since its rows are lda apart) in a
-//     kSStages-deep ring.  It also waits at the grid barrier, and issues a
-//     layer's trace chunks only once the barrier shows every CTA's part of the
-//     previous layer written;
+//     ahead across layer boundaries), and trace chunks (the launch's columns of
+//     KC rows of the previous layer's trace, packed) in a kSStages-deep ring,
+//     with a layer's first chunk also the CTA's rows of that layer's own trace.
+//     It also waits at the grid barrier, and issues a layer's trace chunks only
+//     once the barrier shows every CTA's part of the previous layer written;
 //   * 8 consumer warps wait on the full barriers, split each chunk's columns in
 //     pairs (each lane holds an RPL-row x 2-right-hand-side tile, reads the
 //     two columns of a map row with one 16-byte load, and loads the next pair
@@ -55,7 +55,7 @@ template <int MRT, int NR> struct ChainKC<float, MRT, NR> {
 // Lane layout: RP right-hand-side pairs across a warp row, RH = 32 / RP row
 // groups of RPL rows each.  RP = 16 serves up to 32 right-hand sides, RP = 4
 // up to 8, RP = 1 up to 2 (fewer right-hand sides do proportionally less work);
-// lanes whose rows lie past MRT sit out the products.
+// lanes whose rows lie past MRT repeat row group 0 and their results are dropped.
 template <typename R, int RPL, int RP> struct ChainLayout {
   using C = Cx<R>;
   static constexpr int RH = 32 / RP;
@@ -68,7 +68,7 @@ template <typename R, int RPL, int RP> struct ChainLayout {
   static constexpr int KCP = KC + 2;  // padded map row: neighbouring row groups fall in different banks
   static constexpr size_t bar_bytes = 256;
   static constexpr size_t t_elems = (size_t)kTStages * MRT * KCP;
-  static constexpr size_t s_stage = (size_t)KC * NR;  // a trace chunk, rows lda <= NR apart
+  static constexpr size_t s_stage = (size_t)KC * NR;  // a trace chunk, rows nr2 <= NR apart
   static constexpr size_t s_elems = (size_t)kSStages * s_stage;
   static constexpr size_t d_elems = (size_t)MRT * NR;  // the layer's own trace rows (u~_{p,p} on entry)
   // the cross-warp reduction reuses the trace ring, in passes over halves of the rows if needed
