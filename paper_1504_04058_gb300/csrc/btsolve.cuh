@@ -10,17 +10,21 @@
 //     forward   z_k = W_k (g_k - a_k z_{k-1}),           k = k0 .. n-1
 //     backward  x_{n-1} = z_{n-1},  x_k = z_k - c_k W_k x_{k+1},   k = n-2 .. 0
 // Each step multiplies the dense w x w block W_k by a w x NR panel of
-// right-hand sides.  Work split: every thread owns a 2-row x TC-column tile of
+// right-hand sides.  Work split: every thread owns a TR-row x TC-column tile of
 // the panel for the whole job, so the recurrences (z_{k-1} -> y_k,
-// x_{k+1} -> x_k) stay in its registers; a warp covers (32/LC)*TR rows x LC*TC
-// right-hand sides, the CTA stacks warps over rows (and NCW column blocks).
-// The inner product loads TR rows of W_k (16-byte shared loads of row pairs)
-// and TC panel entries per column j and issues 4*TR*TC FMAs.  A
+// x_{k+1} -> x_k) stay in its registers; a warp covers (32/(LC*KS))*TR rows x
+// LC*TC right-hand sides, the CTA stacks warps over rows (and NCW column
+// blocks).  The inner product loads TR rows of W_k (16-byte shared loads of row
+// pairs) and TC panel entries per column j and issues 4*TR*TC FMAs.  A
 // thread's TC columns come in pairs 2*LC apart so that lanes sharing a row
-// touch one contiguous span (no shared-memory bank conflicts).
+// touch one contiguous span (no shared-memory bank conflicts).  With KS > 1
+// (one or two right-hand sides, where a step is a short dependent chain) KS
+// lanes share each tile, each takes every KS-th column j, and a butterfly of
+// shuffles sums their partial products; one lane of the group stores.
 //
-// Data movement: the W_k blocks stream from HBM through a 3-stage
-// shared-memory ring filled by 1D bulk (TMA) copies that complete on
+// Data movement: the W_k blocks stream from HBM through an STG-stage
+// shared-memory ring (3, or 6 for few right-hand sides) filled by 1D bulk
+// (TMA) copies that complete on
 // mbarriers; the per-step right-hand-side entries (and, in the backward pass,
 // the z_k saved by the forward pass in a per-CTA scratch slot) stream through
 // a per-thread cp.async ring.  One __syncthreads per step publishes the panel.
