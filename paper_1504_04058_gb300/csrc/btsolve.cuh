@@ -23,11 +23,11 @@
 // shuffles sums their partial products; one lane of the group stores.
 //
 // Data movement: the W_k blocks stream from HBM through an STG-stage
-// shared-memory ring (3, or 6 for few right-hand sides) filled by 1D bulk
-// (TMA) copies that complete on
-// mbarriers; the per-step right-hand-side entries (and, in the backward pass,
-// the z_k saved by the forward pass in a per-CTA scratch slot) stream through
-// a per-thread cp.async ring.  One __syncthreads per step publishes the panel.
+// shared-memory ring (3; 6 for few right-hand sides; 2 where a block near 64
+// columns would overflow shared memory with more) filled by 1D bulk (TMA)
+// copies that complete on mbarriers; the per-step right-hand-side entries
+// (and, in the backward pass, the z_k saved by the forward pass in a per-CTA
+// scratch slot) stream through a per-thread cp.async ring.  One __syncthreads per step publishes the panel.
 //
 // Mode classes (compile time) and modes (per job):
 //   CLS_EMBED  EMBED   G~_q^M f_q: g = input on the rows of X_q; writes x on X_q
@@ -437,6 +437,22 @@ cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
   if (sizeof(R) == 4) G.wstage = (G.wstage + 1) & ~1;
   const size_t smem = T::total(G, nt);
   auto kern = btsolve_kernel<R, TRT, TC, LC, NCW, MAXT, MINB, CLS, STG, KS>;
+  if constexpr (STG > 2) {
+    // Wide blocks (w near 64 with many right-hand sides) can need more than
+    // the opt-in shared memory with a deep W ring; they run with two stages.
+    // The limit is the device's opt-in size less the kernel's static shared
+    // bytes, read once per instance (thread-safe static initialisation).
+    static const size_t dyn_limit = [kern]() -> size_t {
+      int dev = 0, optin = 0;
+      cudaFuncAttributes fa{};
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+          cudaFuncGetAttributes(&fa, (const void*)kern) != cudaSuccess)
+        return 0;
+      return (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    }();
+    if (smem > dyn_limit) return run<R, TRT, TC, LC, NCW, CLS, MAXT, MINB, 2, KS>(H, P, wcap, s);
+  }
   cudaError_t e = ensure_dyn_smem((const void*)kern, smem);
   if (e != cudaSuccess) return e;
   int grid = P.njobs < P.zslots ? P.njobs : P.zslots;

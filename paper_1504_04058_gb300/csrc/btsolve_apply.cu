@@ -18,7 +18,9 @@ cudaError_t launch_btsolve_apply(Handle& H, const SolveParams& P, int cls, int c
       }
     } else {
       switch (cap) {
-        case 32: return run<float, 2, 2, 8, 2, CLS_FILL, 384, 2>(H, P, wmax, s);
+        case 32:  // blocks wider than 48 need 8 row warps per column half (512 threads)
+          if (wmax > 48) return run<float, 2, 2, 8, 2, CLS_FILL, 512, 1>(H, P, wmax, s);
+          return run<float, 2, 2, 8, 2, CLS_FILL, 384, 2>(H, P, wmax, s);
         case 16: return run<float, 2, 2, 8, 1, CLS_FILL>(H, P, wmax, s);
         case 8: return run<float, 2, 2, 4, 1, CLS_FILL>(H, P, wmax, s);
         case 4: return run<float, 2, 2, 2, 1, CLS_FILL, 512, 1, 6>(H, P, wmax, s);

@@ -6,10 +6,14 @@ dense transfer maps for the sweep traces), so its deviation is rounding times
 the conditioning of the layer problems: 1e-11 relative for single solves, 1e-10
 for a preconditioner apply, and the 1e-9 bound on the FGMRES solution at a
 fixed iteration count.  The complex64 path rounds the factors and applies to
-FP32 (unit roundoff 6e-8); its apply is compared at 2e-4 relative (the measured
-error growth through n-step block recurrences stays below that), and its
-FGMRES result is judged by the FP64 true residual <= tol, which is what the
-mixed-precision path promises.
+FP32 (unit roundoff 6e-8); its apply is compared at 2e-4 relative up to
+n = 300 and at 2e-4 * n / 300 above (c64_tol): the deviation of either
+precision is its unit roundoff times an effective condition number of the
+n-step block recurrences, and on the same problems the complex128 deviation
+(divided by 2^-53) and the complex64 deviation (divided by 2^-24) give the same
+factor, about 4.5 n for n = 247 ... 1000.  The complex64 FGMRES result is judged
+by the FP64 true residual <= tol, which is what the mixed-precision path
+promises.
 """
 import math
 
@@ -43,6 +47,11 @@ def host(t):
 
 def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def c64_tol(n):
+    """complex64 apply tolerance: linear in n beyond n = 300 (module docstring)."""
+    return 2e-4 * max(1.0, n / 300)
 
 
 def handle(P, precision="c128", max_rhs=None, restart=40):
@@ -153,6 +162,44 @@ def test_apply_matches_oracle_long_layers(name, precision, tol):
     h = handle(P, precision)
     z = host(h.apply_preconditioner(dev(P.f)))
     zo = oracle_pc(P).apply(P.f)
+    assert rel(z, zo) <= tol, rel(z, zo)
+
+
+@pytest.fixture(scope="module")
+def wide_n1000():
+    """n = 1000 with wide layers (PML 4, b = 47, 21 layers; M-layers 53 wide,
+    60 for the last; R/L layers 50, 57 for the last R-layer): the oracle's
+    setup stays under a minute, while the sweep chain runs the
+    lane layout of the n = 1023 benchmark (13-14 rows per CTA, the 32-wide
+    right-hand-side layout for 9 right-hand sides)."""
+    P = W.small_problem(2, 1000, 40 * math.pi, 4, 47, "lens", nrhs=9)
+    return P, oracle_pc(P).apply(P.f)
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", c64_tol(1000))])
+def test_apply_at_n1000_matches_oracle(wide_n1000, precision, tol):
+    P, zo = wide_n1000
+    h = handle(P, precision)
+    z = host(h.apply_preconditioner(dev(P.f)))
+    assert rel(z, zo) <= tol, rel(z, zo)
+
+
+@pytest.fixture(scope="module")
+def widest_blocks():
+    """Blocks near the 64-column limit (n = 330, PML 4, b = 54, six layers):
+    M-layers 60 wide, R/L layers and transfer maps 57 wide, 33 right-hand
+    sides.  At these widths the transfer-map solve of both precisions and the
+    complex128 M-solve hold a two-stage W ring (three stages would overflow
+    shared memory), and the complex64 32-column fill runs 16 warps."""
+    P = W.small_problem(2, 330, 16 * math.pi, 4, 54, "lens", nrhs=33)
+    return P, oracle_pc(P).apply(P.f)
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4)])
+def test_apply_with_widest_blocks_matches_oracle(widest_blocks, precision, tol):
+    P, zo = widest_blocks
+    h = handle(P, precision)
+    z = host(h.apply_preconditioner(dev(P.f)))
     assert rel(z, zo) <= tol, rel(z, zo)
 
 
