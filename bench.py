@@ -211,6 +211,9 @@ def run_asp(args, rank, world):
     elif args.workload == "n255x32":  # the n=1023 workload's layer widths (PML 20, b = 4) on 4.2 GB: profiler captures
         P = W.small_problem(2, 255, 32 * math.pi, 20, 4, "layered", nrhs=32, seed=1504 + rank)
         restart = 4
+    elif args.workload == "n255x1":  # the same with one right-hand side, for captures of the 1-RHS layer solves
+        P = W.small_problem(2, 255, 32 * math.pi, 20, 4, "layered", nrhs=1, seed=1504 + rank)
+        restart = 4
     else:  # smaller case of the same kernels, for profiler captures
         P = W.small_problem(2, 511, 64 * math.pi, 16, 4, "layered", nrhs=32, seed=1504 + rank)
         restart = 16
@@ -383,6 +386,8 @@ def run_asp(args, rank, world):
         config = (dict(WORKLOAD, parallelism=f"replicas x{world}") if args.workload == "n1023" else
                   {"workload": "2d_helmholtz_n255_layered_omega32pi_pml20_b4_32rhs (profiling case)"}
                   if args.workload == "n255x32" else
+                  {"workload": "2d_helmholtz_n255_layered_omega32pi_pml20_b4_1rhs (profiling case)"}
+                  if args.workload == "n255x1" else
                   {"workload": "2d_helmholtz_n511_layered_omega64pi_pml16_b4_32rhs (profiling case)"})
         metric = METRIC
     if args.source == "packet":
@@ -595,9 +600,10 @@ def main():
                     help="right-hand sides of the n=1023 workload: Gaussian point sources or wave packets")
     ap.add_argument("--pml-aux", type=int, default=0,
                     help="width of the auxiliary PMLs between layers (default: the boundary PML width)")
-    ap.add_argument("--workload", choices=["n1023", "n511x32", "n255x32", "n95_3d", "n47_3d_slab"], default="n1023",
+    ap.add_argument("--workload", choices=["n1023", "n511x32", "n255x32", "n255x1", "n95_3d", "n47_3d_slab"], default="n1023",
                     help="n511x32: the same kernels on a 2D n=511 problem with 32 RHS (profiling); "
                          "n255x32: the n=1023 workload's layer widths (PML 20, b = 4) at n=255, 4.2 GB (profiling); "
+                         "n255x1: the same with one RHS (profiling); "
                          "n95_3d: the 3D slab path on the n=95 bump problem (1 RHS); "
                          "n47_3d_slab: one 3D slab with 2209-unknown blocks, 2.1 GB (profiling)")
     args = ap.parse_args()
