@@ -106,13 +106,17 @@ typedef struct asp_solve_info {
  * the handle's device memory.  Returns ASP_ERR_INVALID for out-of-range
  * parameters or a non-positive / non-finite velocity, ASP_ERR_UNSUPPORTED for a
  * valid problem this build does not take (2D: a padded layer wider than 64
- * columns; 3D: a slab block n * (padded width) above 3072 unknowns), ASP_ERR_OOM
- * if the footprint does not fit.  Synchronizes the device before returning. */
+ * columns, or n above 16 * (SMs / 2) = 1216 on a 152-SM GPU with three or more
+ * layers, since the sweep chain holds at most 16 map rows per CTA on half of
+ * the SMs; 3D: a slab block n * (padded width) above 3072 unknowns),
+ * ASP_ERR_OOM if the footprint does not fit.  Synchronizes the device before
+ * returning. */
 int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle** out);
 
 /* Bytes of device memory asp_setup + asp_factor will hold for these
  * parameters (factors, transfer maps, apply and Krylov workspaces).  Pure
- * function of `p`; 0 for invalid parameters. */
+ * function of `p` and the device's SM count (152 without a device); 0 for
+ * invalid or unsupported parameters. */
 size_t asp_footprint_bytes(const asp_params* p);
 
 /* Number of layers m, and the partition of layer p (1-based): X_p = [x_lo, x_hi]

@@ -176,15 +176,27 @@ Part partition(int n, int gamma, int ga, int b) {
 // Largest 3D block size (n * padded width) the slab kernels take.
 constexpr int kMaxNb3 = 3072;
 
-// Valid problems that this build does not handle: 2D padded layers wider than
-// 64 columns, 3D blocks larger than kMaxNb3.
-bool supported(const asp_params* p, std::string* why) {
+// SM count assumed by size and support queries made without a device (GB300).
+constexpr int kDefaultSms = 152;
+
+// Valid problems that this build does not handle on a GPU with `sms` SMs: 2D
+// padded layers wider than 64 columns, 2D grids with more than
+// kChainMaxRows * (sms / 2) points per side (sweep chain with three or more
+// layers), 3D blocks larger than kMaxNb3.
+bool supported(const asp_params* p, std::string* why, int sms) {
   const int ga = p->pml_aux ? p->pml_aux : p->pml;
   Part P = partition(p->n, p->pml, ga, p->b);
   int wmax = 0;
   for (int q = 1; q <= P.m; ++q) wmax = std::max(wmax, P.m_hi[q] - P.m_lo[q] + 1);
   if (p->dim == 2 && wmax > 64) {
     *why = "padded layer width 2*gamma_a + b - 2 (+ remainder) exceeds 64 columns";
+    return false;
+  }
+  const int max_n2 = kChainMaxRows * (sms / 2);
+  if (p->dim == 2 && P.m >= 3 && p->n > max_n2) {
+    *why = "2D n exceeds " + std::to_string(max_n2) + " on " + std::to_string(sms) +
+           " SMs (the sweep chain holds at most " + std::to_string(kChainMaxRows) +
+           " map rows per CTA on half of the SMs)";
     return false;
   }
   if (p->dim == 3 && (long long)p->n * wmax > kMaxNb3) {
@@ -570,9 +582,9 @@ const char* asp_last_error_detail(void) { return g_detail.c_str(); }
 
 size_t asp_footprint_bytes(const asp_params* p) {
   std::string why;
-  if (!valid(p, &why) || !supported(p, &why)) return 0;
   int sms = device_sms();
-  if (sms <= 0) sms = 152;
+  if (sms <= 0) sms = kDefaultSms;
+  if (!valid(p, &why) || !supported(p, &why, sms)) return 0;
   return sizes_for(p, sms).bytes;
 }
 
@@ -647,7 +659,8 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   if (!out) return fail(ASP_ERR_INVALID, "out is null");
   *out = nullptr;
   if (!valid(p, &why)) return fail(ASP_ERR_INVALID, why);
-  if (!supported(p, &why)) return fail(ASP_ERR_UNSUPPORTED, why);
+  const int sms = device_sms();
+  if (!supported(p, &why, sms > 0 ? sms : kDefaultSms)) return fail(ASP_ERR_UNSUPPORTED, why);
   if (!c) return fail(ASP_ERR_INVALID, "velocity pointer is null");
   const int n = p->n;
   const long long N = p->dim == 3 ? (long long)n * n * n : (long long)n * n;
@@ -660,7 +673,6 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   }
   for (long long i = 0; i < N; ++i)
     if (!(ch[i] > 0) || !isfinite(ch[i])) return fail(ASP_ERR_INVALID, "velocity must be positive and finite");
-  const int sms = device_sms();
   if (sms <= 0) return fail(ASP_ERR_CUDA, "no CUDA device");
 
   asp_handle* hd = new asp_handle();

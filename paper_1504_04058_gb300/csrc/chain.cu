@@ -433,7 +433,7 @@ cudaError_t launch_chain(Handle& H, const ChainParams& P, cudaStream_t s) {
   int half = H.num_sms / 2;
   if (half > P.n) half = P.n;
   if (half < 1) half = 1;
-  while ((P.n + half - 1) / half > 16) ++half;  // rows per CTA must fit the largest tile
+  while ((P.n + half - 1) / half > kChainMaxRows) ++half;  // rows per CTA must fit the largest tile
   if (2 * half > H.num_sms) return cudaErrorInvalidValue;  // cooperative: one CTA per SM
   const int maxrows = (P.n + half - 1) / half;
   cudaError_t e = cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned int), s);

@@ -139,6 +139,11 @@ struct Slab {
 // kSlabOuter).
 constexpr int kSlabPanel = 32;
 constexpr int kSlabOuter = 256;
+
+// Most map rows one CTA of the 2D sweep chain holds.  The chain runs one CTA
+// per SM, half of the SMs per sweep direction, so 2D problems take
+// n <= kChainMaxRows * (SMs / 2): 1216 on 152 SMs.
+constexpr int kChainMaxRows = 16;
 inline long long slab_work_elems(int nb, int ld) {
   return 2LL * nb * ld + (long long)kSlabOuter * ld + (long long)kSlabPanel * kSlabOuter;
 }

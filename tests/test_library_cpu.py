@@ -84,6 +84,24 @@ def test_dimension_checks(lib):
     assert lib.asp_footprint_bytes(ctypes.byref(p)) == 0
 
 
+def test_2d_grid_beyond_the_sweep_chain_is_unsupported(lib):
+    """The sweep chain holds at most 16 map rows per CTA on half of the SMs,
+    so on 152 SMs (the count assumed without a device) a 2D grid of more
+    than 1216 points per side is refused by setup, not by the first apply."""
+    import numpy as np
+    from paper_1504_04058_gb300 import _lib, make_params
+    ok = make_params(1216, 128 * 3.141592653589793, 20, 4, precision="c64", max_rhs=1, restart=4)
+    big = make_params(1217, 128 * 3.141592653589793, 20, 4, precision="c64", max_rhs=1, restart=4)
+    assert lib.asp_footprint_bytes(ctypes.byref(ok)) > 0
+    assert lib.asp_footprint_bytes(ctypes.byref(big)) == 0
+    out = ctypes.c_void_p()
+    c = np.ones(1217 ** 2)
+    assert lib.asp_setup(ctypes.byref(big), c.ctypes.data_as(ctypes.c_void_p), 0,
+                         ctypes.byref(out)) == _lib.ASP_ERR_UNSUPPORTED
+    assert b"sweep chain" in lib.asp_last_error_detail()
+    assert not out.value
+
+
 def test_3d_footprint_counts_every_slab_factor(lib):
     """3D factors: n dense blocks of (n w) x (n w) per slab (rows padded to a
     multiple of 4), for every M, R and L slab."""
