@@ -153,9 +153,12 @@ def _layer_widths(n, gamma, b, gamma_a=None):
 
 
 def algorithmic(n, gamma, b, nrhs, esz, gamma_a=None):
-    """Algorithmic bytes and flops per launch of each phase:
-    a banded solve reads its L and U band once, n*w*(2w+1) entries, and does
-    8*(2w+1) real flops per entry row per right-hand side."""
+    """Algorithmic bytes and flops per launch of each phase: a banded solve
+    reads its L and U band once, n*w*(2w+1) entries, and does 8*(2w+1) real
+    flops per entry row per right-hand side.  A transfer map T_p has n
+    columns; column r's forward pass starts at its own block (n - r steps of
+    w^2 complex MACs) and its backward pass takes all n, so one map costs
+    1.5*n^2*w^2 complex MACs, and it is written once (n*n entries)."""
     m, wM, wR, wL, wT = _layer_widths(n, gamma, b, gamma_a)
     band = lambda ws: sum(n * w * (2 * w + 1) for w in ws)  # noqa: E731
     N = n * n
@@ -164,7 +167,7 @@ def algorithmic(n, gamma, b, nrhs, esz, gamma_a=None):
     out["embed"] = {"bytes": band(wM) * esz + 2 * vec, "flops": 8.0 * nrhs * band(wM)}
     out["fill"] = {"bytes": (band(wR) + band(wL)) * esz + 2 * vec, "flops": 8.0 * nrhs * (band(wR) + band(wL))}
     out["tmap"] = {"bytes": 2 * band(wT) * esz + 2 * len(wT) * n * n * esz,
-                   "flops": 2 * 8.0 * 1.5 * n * band(wT)}
+                   "flops": 2 * 8.0 * 1.5 * n * n * sum(w * w for w in wT)}
     out["chain"] = {"bytes": 2 * len(wT) * n * n * esz, "flops": 8.0 * nrhs * 2 * len(wT) * n * n}
     out["factor"] = {"bytes": (band(wM) + band(wR) + band(wL)) * esz,
                      "flops": 8.0 * n * sum(w ** 3 for w in wM + wR + wL)}
@@ -373,7 +376,7 @@ def run_asp(args, rank, world):
             ach = alg[dom]["flops"] / (avg_ms * 1e-3) / 1e12
             roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": ach / fp32_peak, "kernel": f"btsolve/btfactor ({dom})",
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived, see DESIGN.md)"}
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock (derived; no measured FP32 peak is available)"}
         else:
             ach = alg[dom]["bytes"] / (avg_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
