@@ -278,6 +278,55 @@ def test_preconditioner_approximates_the_green_operator():
 
 # --------------------------------------------------------------- FGMRES
 
+def test_givens_rotation_is_unitary_and_annihilates():
+    """The complex Givens rotation of the FGMRES least-squares update: the
+    2 x 2 matrix [[c, s], [-conj(s), c]] is unitary, maps (a, b) to (r, 0) with
+    |r| = |(a, b)|, and keeps the phase of a (r = e^{i arg a} |(a, b)|), also
+    when a or b is zero."""
+    rng = np.random.default_rng(11)
+    pairs = [(complex(*rng.standard_normal(2)), complex(*rng.standard_normal(2))) for _ in range(20)]
+    pairs += [(1.5 - 2j, 0j), (0j, -0.3 + 0.4j), (0j, 0j), (1e-300 + 0j, 1.0 + 0j)]
+    for a, b in pairs:
+        c, s = fgmres.givens(a, b)
+        G = np.array([[c, s], [-np.conj(s), c]])
+        assert abs(np.imag(c)) == 0.0
+        assert np.allclose(G @ G.conj().T, np.eye(2), atol=1e-14)
+        r, zero = G @ np.array([a, b])
+        rho = math.hypot(abs(a), abs(b))
+        assert abs(zero) <= 1e-14 * max(rho, 1e-300)
+        assert math.isclose(abs(r), rho, rel_tol=1e-14, abs_tol=1e-300)
+        if a != 0 and rho > 0:
+            assert abs(r - rho * a / abs(a)) <= 1e-14 * rho
+
+
+@pytest.mark.parametrize("dim,n", [(2, 9), (3, 5)])
+def test_matrix_free_apply_handles_single_and_batched_fields(dim, n):
+    """apply_A on a sine eigenmode (C = 0, constant c) returns lambda times
+    the mode, for one grid function and for a batch with a trailing
+    right-hand-side axis whose columns are different modes."""
+    omega, cval = 5.1, 0.9
+    h = 1.0 / (n + 1)
+    c = np.full((n,) * dim, cval)
+    xs = W.grid_nodes(n, dim)
+    modes, lams = [], []
+    for ks in ([1] * dim, [2] + [1] * (dim - 1), [n] * dim):
+        mode = np.ones((n,) * dim)
+        lam = omega**2 / cval**2
+        for ax in range(dim):
+            mode = mode * np.sin(math.pi * ks[ax] * xs[ax])
+            lam -= 4.0 / h**2 * math.sin(math.pi * ks[ax] * h / 2) ** 2
+        modes.append(mode)
+        lams.append(lam)
+    y0 = operator.apply_A(dim, n, omega, c, 3, 0.0, modes[0])
+    assert y0.shape == modes[0].shape
+    assert np.allclose(y0, lams[0] * modes[0], rtol=1e-12, atol=1e-9 * abs(lams[0]))
+    batch = np.stack(modes, axis=-1).astype(np.complex128)
+    yb = operator.apply_A(dim, n, omega, c, 3, 0.0, batch)
+    assert yb.shape == batch.shape
+    for r, lam in enumerate(lams):
+        assert np.allclose(yb[..., r], lam * modes[r], rtol=1e-12, atol=1e-9 * abs(lam))
+
+
 def test_fgmres_identity_preconditioner_is_minimal_residual():
     """With M = I, FGMRES after k steps returns the minimal-residual vector of
     the Krylov space span{f, Af, ..., A^{k-1} f}; compare with a brute-force
