@@ -180,6 +180,38 @@ def test_subproblems_without_pml_are_principal_submatrices():
             assert np.allclose(H, A[np.ix_(idx, idx)], atol=1e-9)
 
 
+@pytest.mark.parametrize("dim,n,gamma,b,gamma_a", [(1, 40, 4, 5, None), (2, 17, 4, 3, 2), (3, 9, 2, 2, None)])
+def test_subproblem_rows_away_from_the_auxiliary_pml_equal_rows_of_A(dim, n, gamma, b, gamma_a):
+    """C > 0: a row of H_p^M, H_p^R or H_p^L whose stencil stays inside the
+    layer's PML-free columns (alpha_p .. beta_p) is the row of A, restricted to
+    the subproblem's grid; so are the rows in the boundary PML of the first
+    and last layers, which keep it unchanged (Section 3.1).  An auxiliary PML
+    placed one column off, or the boundary PML of the end layers replaced by
+    the auxiliary one, changes one of these rows."""
+    omega, C = 9.0, 20.0
+    c = W.lens_velocity(n, dim)
+    part = partition.make_partition(n, gamma, b, gamma_a)
+    A = operator.helmholtz_matrix(dim, n, omega, c, gamma, C).toarray()
+    T = n ** (dim - 1)
+    checked = 0
+    for p in range(1, part.m + 1):
+        L = part.layers[p - 1]
+        first = 1 if p == 1 else L.phys_lo + 1
+        last = n if p == part.m else L.phys_hi - 1
+        for kind, (lo, hi) in (("M", (L.m_lo, L.m_hi)), ("R", (L.r_lo, L.r_hi)), ("L", (L.l_lo, L.l_hi))):
+            if (kind == "R" and p == 1) or (kind == "L" and p == part.m):
+                continue
+            H = subproblems.subproblem_matrix(dim, n, omega, c, gamma, C, part, p, kind, order="natural").toarray()
+            cols = np.arange((lo - 1) * T, hi * T)
+            rows_g = np.arange((first - 1) * T, last * T)
+            rows_l = rows_g - (lo - 1) * T
+            outside = np.setdiff1d(np.arange(n ** dim), cols)
+            assert np.all(A[np.ix_(rows_g, outside)] == 0)
+            assert np.allclose(H[rows_l], A[np.ix_(rows_g, cols)], rtol=1e-13, atol=1e-9)
+            checked += len(rows_l)
+    assert checked > 0
+
+
 def _bvp_solution(dim, n, omega, c, gamma, C, part, p, kind, w):
     """Independent form of G~_p^R w / G~_p^L w: the boundary value problem of
     Section 3.1 with v = w held on the boundary column (x2 = alpha_p - 1 for R,
