@@ -149,7 +149,8 @@ class Server:
         fit now (all candidates busy)."""
         fp = asp_footprint_bytes(self._params(req))
         if fp == 0:
-            raise ValueError("invalid request parameters")
+            raise ValueError(f"request parameters are invalid or unsupported (n={req.n}, pml={req.pml}, b={req.b}; "
+                             "2D takes padded layer widths up to 64 columns and n up to 1216 on 152 SMs)")
         if fp > self.memory_budget:
             raise MemoryError(f"request needs {fp} bytes, budget is {self.memory_budget}")
         while self.used_bytes + fp > self.memory_budget:

@@ -105,6 +105,16 @@ def test_request_larger_than_budget_is_refused(serving):
     srv.close()
 
 
+def test_unsupported_size_is_refused_at_admission(serving):
+    """A 2D grid above what the sweep chain takes (n = 1217 on 152 SMs) gets a
+    footprint of 0 from the library and is refused before any setup."""
+    srv = serving.Server(1 << 40, workers=1, max_rhs=4, start=False)
+    with pytest.raises(ValueError, match="unsupported"):
+        srv._admit(make_req(serving, "A", n=1217))
+    assert srv.used_bytes == 0
+    srv.close()
+
+
 def test_percentiles(serving):
     p = serving.percentiles(np.arange(1, 101, dtype=float))
     assert p["p50"] == pytest.approx(50.5) and p["p99"] == pytest.approx(99.01)
