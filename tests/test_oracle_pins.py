@@ -239,15 +239,16 @@ def _bvp_solution(dim, n, omega, c, gamma, C, part, p, kind, w):
     return inner[L.x_lo - lo: L.x_hi - lo + 1]
 
 
-@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("dim", [1, 2, 3])
 def test_transmission_operators_solve_the_boundary_value_problem(dim):
     """G~_p^R w (g = (-1/h^2)[w, 0, ...]) and G~_p^L w (g on the last column)
     equal the restriction to X_p of the Helmholtz solution on D_p^R / D_p^L
     with v = w on the left / right boundary and zero elsewhere (Section 3.1).
     A wrong sign, scale or side of g fails this."""
-    n, gamma, b, omega, C = (30, 4, 3, 12.0, 20.0) if dim == 1 else (13, 3, 2, 9.0, 20.0)
-    c = np.linspace(0.9, 1.1, n) if dim == 1 else W.lens_velocity(n, 2)
+    n, gamma, b, omega, C = {1: (30, 4, 3, 12.0, 20.0), 2: (13, 3, 2, 9.0, 20.0), 3: (9, 2, 2, 6.0, 20.0)}[dim]
+    c = np.linspace(0.9, 1.1, n) if dim == 1 else W.lens_velocity(n, dim)
     part = partition.make_partition(n, gamma, b)
+    assert part.m >= 3
     rng = np.random.default_rng(3)
     T = n ** (dim - 1)
     for p in range(2, part.m):
