@@ -45,7 +45,8 @@ constexpr int kChainThreads = kConsumers + 32;  // + the producer warp
 constexpr int kRhs = 32;     // most right-hand sides per launch
 // Chunk width and ring depths: fewer, larger chunks (each handoff costs about
 // a microsecond) as far as shared memory allows.  MRT: map rows a CTA holds
-// (the launcher gives a CTA at most 16 rows).
+// (the launcher gives a CTA at most kChainMaxRows = 16 rows, and asp_setup
+// refuses 2D grids that would need more).
 template <typename R, int MRT, int NR> struct ChainKC { static constexpr int v = 64, ts = 6, ss = 3; };
 template <int MRT, int NR> struct ChainKC<float, MRT, NR> {
   static constexpr bool wide = MRT <= 14 || NR <= 8;
@@ -60,7 +61,8 @@ template <typename R, int RPL, int RP> struct ChainLayout {
   using C = Cx<R>;
   static constexpr int RH = 32 / RP;
   static constexpr int MR = RH * RPL;              // rows the lane layout covers
-  static constexpr int MRT = MR < 16 ? MR : 16;    // rows a CTA holds
+  static_assert(kChainMaxRows == 16, "the lane layouts and ring sizes are chosen for 16 rows per CTA");
+  static constexpr int MRT = MR < kChainMaxRows ? MR : kChainMaxRows;  // rows a CTA holds
   static constexpr int NR = 2 * RP;                // right-hand sides per launch
   static constexpr int KC = ChainKC<R, MRT, NR>::v;
   static constexpr int kTStages = ChainKC<R, MRT, NR>::ts;  // map-chunk ring depth
