@@ -133,6 +133,30 @@ def test_nonpositive_velocity_rejected(lib):
     assert code == _lib.ASP_ERR_INVALID
 
 
+def test_non_finite_inputs_rejected(lib):
+    """NaN or infinite velocity entries, omega or C are invalid (the checks
+    are written so that NaN fails them), reported before any device work."""
+    import numpy as np
+    from paper_1504_04058_gb300 import _lib, make_params
+    out = ctypes.c_void_p()
+    for bad in (np.nan, np.inf):
+        p = make_params(31, 20.0, 4, 3)
+        c = np.ones(31 * 31)
+        c[7] = bad
+        assert lib.asp_setup(ctypes.byref(p), c.ctypes.data_as(ctypes.c_void_p), 0,
+                             ctypes.byref(out)) == _lib.ASP_ERR_INVALID
+        assert b"velocity" in lib.asp_last_error_detail()
+        for field in ("omega", "C"):
+            p = make_params(31, 20.0, 4, 3)
+            setattr(p, field, bad)
+            assert lib.asp_footprint_bytes(ctypes.byref(p)) == 0
+            c = np.ones(31 * 31)
+            assert lib.asp_setup(ctypes.byref(p), c.ctypes.data_as(ctypes.c_void_p), 0,
+                                 ctypes.byref(out)) == _lib.ASP_ERR_INVALID
+            assert field.encode() in lib.asp_last_error_detail()
+    assert not out.value
+
+
 def test_footprint_matches_layer_sizes(lib):
     """The footprint grows with n and includes the factor bytes of every layer
     subproblem: sum over 3m-2 subproblems of n*w*w_pad elements."""
