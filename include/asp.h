@@ -202,11 +202,12 @@ int asp_phase_times(asp_handle* h, double* ms, long long* launches, int nphases)
  * asp_residual_norms_noalloc: rel_res[r] = ||f_r - A u_r|| / ||f_r|| (0 when
  * f_r = 0) for r < nrhs, with A the operator of asp_matvec for the problem in
  * `p` (dim, n, omega, pml, C are read; the other fields are ignored).  The
- * paper has no counterpart of this call: it exists for callers that cannot
- * allocate device memory -- code inside a CUDA-graph capture, processes whose
- * device memory belongs to another allocator, serving loops that must not
- * allocate -- and therefore takes no handle.
- *   c        DEVICE, n*n doubles, the velocity in the natural ordering
+ * paper has no counterpart of this call.  It is for callers that cannot
+ * allocate device memory -- a process whose device memory belongs to another
+ * allocator (a framework's caching pool, a fixed arena), or a serving loop
+ * that must not allocate once it runs -- and therefore takes no handle.
+ *   c        DEVICE, n*n doubles, the velocity in the natural ordering; every
+ *            entry must be positive and finite, else every rel_res entry is NaN
  *   f, u     DEVICE complex128 vectors, RHS-interleaved as everywhere
  *   rel_res  DEVICE, nrhs doubles, written
  * It allocates nothing: its temporaries live in one fixed device array inside

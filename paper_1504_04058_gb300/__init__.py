@@ -173,8 +173,9 @@ class AspHandle:
 
 def asp_residual_norms_noalloc(params: asp_params, c, f, u, rel_res=None, stream=None):
     """||f_r - A u_r|| / ||f_r|| per right-hand side without any device allocation
-    inside the library (for callers that cannot allocate: graph captures,
-    foreign allocators, allocation-free serving loops).  ``c`` is the float64
+    inside the library (for callers that cannot allocate: a process whose
+    device memory belongs to another allocator, or a serving loop that must
+    not allocate once it runs).  ``c`` is the float64
     CUDA velocity (n, n); ``f``, ``u`` complex128 CUDA tensors (n, n, nrhs);
     ``rel_res`` an optional float64 CUDA tensor of nrhs entries that receives
     the result (allocated here, by torch, if omitted)."""

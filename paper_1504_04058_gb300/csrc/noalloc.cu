@@ -2,27 +2,27 @@
 // (rel_res[r] = ||f_r - A u_r|| / ||f_r||) for callers that cannot allocate
 // device memory.
 //
-// Who needs it: code that runs where cudaMalloc is not allowed or not wanted --
-// inside a region that is being captured into a CUDA graph (an allocation
-// there would break the capture), in a process whose device memory is owned
-// by another allocator (a framework's caching pool, a fixed arena), or in a
-// steady-state serving loop that must not allocate at all.  Such a caller
-// owns f, u and the output and only needs to know how good a solution is.
+// Who needs it: a process whose device memory is owned by another allocator
+// (a framework's caching pool or a fixed arena that must account for every
+// byte), or a steady-state serving loop that is not allowed to allocate at
+// all once it runs.  Such a caller owns f, u and the output and only needs to
+// know how good a solution is; the handle-based path would have to allocate
+// its coefficient arrays and reduction buffers in asp_setup.
 //
-// The handle-based path allocates its coefficient arrays and reduction
-// buffers in asp_setup.  This entry point needs no handle: it recomputes the
-// stencil weights of Eq. (4) on the device and keeps them, together with the
-// per-block partial sums, in one file-scope device array of fixed size
-// (kScratchBytes below, about 0.7 MB).  Every GPU that loads the library holds
-// that array until the process exits.
+// This entry point needs no handle: it recomputes the stencil weights of
+// Eq. (4) on the device and keeps them, together with the per-block partial
+// sums and a flag for an invalid velocity, in one file-scope device array of
+// fixed size (kScratchBytes below, about 0.7 MB).  Every GPU that loads the
+// library holds that array until the process exits.
 //
 // Host code cannot use the array's name as a device address, so the first call
 // on each device looks the address up with cudaGetSymbolAddress (with that
 // device current) and caches it; that first call should therefore come before
 // any stream capture.  All calls share the one array: calls that overlap on the
 // GPU (different streams, or different host threads without ordering) race and
-// may return wrong values.  Each call rewrites every scratch entry it reads, so
-// nothing has to be cleared between calls.
+// may return wrong values.  Each call rewrites every scratch entry it reads and
+// clears the velocity flag first, so nothing carries over from one call to the
+// next.
 #include <math.h>
 
 #include <mutex>
@@ -46,6 +46,7 @@ struct Scratch {
   double2 cc[kMaxN];                 // s_k s_{k+1/2} / h^2
   double2 cd[kMaxN];                 // -(ca + cc)
   double2 partial[kBlocks][kMaxRhs];  // per block: (sum |r|^2, sum |f|^2)
+  int bad_velocity;                   // set when some c is not positive and finite
 };
 constexpr size_t kScratchBytes = sizeof(Scratch);
 
@@ -70,6 +71,7 @@ __device__ double2 pml_s(double x, int n, int gamma, double C, double omega) {
 
 __global__ void na_coef_kernel(int n, int gamma, double C, double omega, Scratch* S) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) S->bad_velocity = 0;  // this call's flag starts clear
   if (k >= n) return;
   const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
   const double x = (k + 1) * h;
@@ -100,7 +102,9 @@ __global__ void na_residual_kernel(const double* __restrict__ c, double omega, i
     const int i1 = (int)(pt % n), i2 = (int)(pt / n);
     const double2 x = u[e];
     const double2 d1 = S->cd[i1], d2 = S->cd[i2];
-    const double k2 = omega * omega / (c[pt] * c[pt]);
+    const double cv = c[pt];
+    if (!(cv > 0.0) || !isfinite(cv)) S->bad_velocity = 1;
+    const double k2 = omega * omega / (cv * cv);
     const double2 diag = make_double2(d1.x + d2.x + k2, d1.y + d2.y);
     double2 acc = cmul(diag, x);
     double2 acc2 = make_double2(0.0, 0.0);
@@ -131,7 +135,8 @@ __global__ void na_finish_kernel(int nblocks, int nrhs, const Scratch* S, double
     sr += S->partial[b][r].x;
     sf += S->partial[b][r].y;
   }
-  rel[r] = sf > 0.0 ? sqrt(sr / sf) : 0.0;
+  // a velocity that is not positive and finite has no operator: NaN for every right-hand side
+  rel[r] = S->bad_velocity ? __longlong_as_double(0x7ff8000000000000LL) : (sf > 0.0 ? sqrt(sr / sf) : 0.0);
 }
 
 // Device address of g_scratch for the current device (looked up once per device).

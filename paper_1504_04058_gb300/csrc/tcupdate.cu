@@ -26,7 +26,8 @@
 //     instruction, both operands K-major from shared-memory descriptors) into
 //     a 128 x 256 FP32 accumulator in tensor memory; tcgen05.commit releases
 //     each ring stage and finally signals the epilogue;
-//   * four warps read the accumulator with tcgen05.ld and add it into (or, for
+//   * eight epilogue warps (two per TMEM lane quarter, each taking half of the
+//     columns) read the accumulator with tcgen05.ld and add it into (or, for
 //     pivot rows, store it as) C.
 // Every wait is bounded; a timeout records ASP_ERR_TIMEOUT, and the CTA still
 // waits (bounded) for its copies and products in flight and frees its tensor
