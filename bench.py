@@ -38,7 +38,7 @@ WORKLOAD = {"workload": "2d_helmholtz_n1023_layered_omega128pi_pml20_b4_32rhs", 
             "omega": "128*pi", "pml": 20, "b": 4, "nrhs": 32, "velocity": "16 random layers, smoothed 3h",
             "factor_precision": "complex64", "krylov": "FGMRES(40) FP64", "tol": 1e-6,
             "l2": "no flush needed: factors 11.5 GB + transfer maps 4.1 GB exceed the 129 MB L2"}
-PHASES = ["factor", "tmap", "embed", "chain", "fill", "elementwise", "matvec", "krylov", "schur3d"]
+PHASES = ["factor", "tmap", "embed", "chain", "fill", "elementwise", "matvec", "krylov", "schur3d", "tdiag"]
 METRIC_3D = "solves/s (3D n=95, omega=48pi, 1 RHS, to 1e-6 FP64 residual)"
 WORKLOAD_3D = {"workload": "3d_helmholtz_n95_bump_omega48pi_pml8_b4_1rhs", "n": 95, "omega": "48*pi", "pml": 8,
                "b": 4, "nrhs": 1, "velocity": "1 + 0.3 Gaussian bump at the centre",
@@ -152,13 +152,25 @@ def _layer_widths(n, gamma, b, gamma_a=None):
     return m, wM, wR, wL, wT
 
 
-def algorithmic(n, gamma, b, nrhs, esz, gamma_a=None):
+def tc_maps(n, gamma, b, precision="c64", gamma_a=None):
+    """True when the library builds the transfer maps on the tensor cores
+    (complex64 factors, every map subproblem at most 32 columns wide)."""
+    m, wM, wR, wL, wT = _layer_widths(n, gamma, b, gamma_a)
+    return precision == "c64" and m >= 3 and max(wR + wL) <= 32
+
+
+def algorithmic(n, gamma, b, nrhs, esz, gamma_a=None, tc=False):
     """Algorithmic bytes and flops per launch of each phase: a banded solve
     reads its L and U band once, n*w*(2w+1) entries, and does 8*(2w+1) real
     flops per entry row per right-hand side.  A transfer map T_p has n
-    columns; column r's forward pass starts at its own block (n - r steps of
-    w^2 complex MACs) and its backward pass takes all n, so one map costs
-    1.5*n^2*w^2 complex MACs, and it is written once (n*n entries)."""
+    columns and is written once (n*n entries).  Built by solves (tc False),
+    column r's forward pass starts at its own block (n - r steps of w^2
+    complex MACs) and its backward pass takes all n: 1.5*n^2*w^2 complex MACs
+    per map.  Built from the diagonal blocks of the inverse (tc True), each
+    column runs one chain of r block steps from its diagonal block, for the
+    upper and (by symmetry) the lower triangle: n(n-1) w^2 complex MACs per
+    map, plus the diagonal-block recursion (tdiag), two w x w x w complex
+    products per block."""
     m, wM, wR, wL, wT = _layer_widths(n, gamma, b, gamma_a)
     band = lambda ws: sum(n * w * (2 * w + 1) for w in ws)  # noqa: E731
     N = n * n
@@ -166,8 +178,14 @@ def algorithmic(n, gamma, b, nrhs, esz, gamma_a=None):
     out = {}
     out["embed"] = {"bytes": band(wM) * esz + 2 * vec, "flops": 8.0 * nrhs * band(wM)}
     out["fill"] = {"bytes": (band(wR) + band(wL)) * esz + 2 * vec, "flops": 8.0 * nrhs * (band(wR) + band(wL))}
-    out["tmap"] = {"bytes": 2 * band(wT) * esz + 2 * len(wT) * n * n * esz,
-                   "flops": 2 * 8.0 * 1.5 * n * n * sum(w * w for w in wT)}
+    if tc:
+        out["tmap"] = {"bytes": 2 * band(wT) * esz + 2 * len(wT) * n * n * esz + 2 * len(wT) * n * 2 * 32 * esz,
+                       "flops": 2 * 8.0 * n * (n - 1) * sum(w * w for w in wT)}
+        out["tdiag"] = {"bytes": 2 * band(wT) * esz + 2 * len(wT) * n * 2 * 32 * esz,
+                        "flops": 2 * 8.0 * 2 * (n - 1) * sum(w ** 3 for w in wT)}
+    else:
+        out["tmap"] = {"bytes": 2 * band(wT) * esz + 2 * len(wT) * n * n * esz,
+                       "flops": 2 * 8.0 * 1.5 * n * n * sum(w * w for w in wT)}
     out["chain"] = {"bytes": 2 * len(wT) * n * n * esz, "flops": 8.0 * nrhs * 2 * len(wT) * n * n}
     out["factor"] = {"bytes": (band(wM) + band(wR) + band(wL)) * esz,
                      "flops": 8.0 * n * sum(w ** 3 for w in wM + wR + wL)}
@@ -369,11 +387,22 @@ def run_asp(args, rank, world):
                   {"workload": "3d_helmholtz_n47_one_slab_omega12pi_pml6_b37 (profiling case)"})
         metric = METRIC_3D
     else:
-        alg = algorithmic(P.n, P.pml, P.b, P.nrhs, 8, pml_aux)
+        tcm = tc_maps(P.n, P.pml, P.b, args.precision, pml_aux)
+        alg = algorithmic(P.n, P.pml, P.b, P.nrhs, 8, pml_aux, tc=tcm)
         dom = max((p for p in PHASES if p in alg), key=lambda p: phases[p][0])
         tot_ms, nl = phases[dom]
         avg_ms = tot_ms / max(nl, 1)
-        if dom in ("embed", "fill", "tmap", "factor"):
+        if dom == "tmap" and tcm:
+            # tensor-core maps: useful flops (the complex products of the
+            # chains) against the dense TF32 peak; the split-precision scheme
+            # executes three tensor products per useful one
+            tf32_peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * 0.5
+            ach = alg[dom]["flops"] / (avg_ms * 1e-3) / 1e12
+            roof = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                    "frac": ach / tf32_peak, "kernel": "tmap_tc_kernel (transfer maps on tcgen05, split TF32)",
+                    "peak_source": f"bf16_tflops_sustained ({peak_kind}) x 0.5 nominal tf32/bf16 ratio",
+                    "executed_tensor_frac": 3 * ach / tf32_peak}
+        elif dom in ("embed", "fill", "tmap", "factor", "tdiag"):
             ach = alg[dom]["flops"] / (avg_ms * 1e-3) / 1e12
             roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": ach / fp32_peak, "kernel": f"btsolve/btfactor ({dom})",
@@ -382,7 +411,8 @@ def run_asp(args, rank, world):
             ach = alg[dom]["bytes"] / (avg_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / peaks["hbm_gbs"], "kernel": dom, "peak_source": f"hbm_gbs ({peak_kind})"}
-        roof["traffic"] = _traffic_from_profile(dom)
+        # the committed DRAM capture belongs to the layer-solve kernel (btsolve.cuh)
+        roof["traffic"] = None if (dom in ("tmap", "tdiag") and tcm) else _traffic_from_profile(dom)
         roof["avg_launch_ms"] = avg_ms
         roof["hbm_view"] = {"algorithmic_bytes": alg[dom]["bytes"],
                             "GBps": alg[dom]["bytes"] / (avg_ms * 1e-3) / 1e9,
@@ -401,7 +431,7 @@ def run_asp(args, rank, world):
                       variant="thinner auxiliary PML inside the domain (the boundary PML keeps its width)")
     precond_apply = None
     if apply_runs:
-        alg2 = algorithmic(P.n, P.pml, P.b, 1, 8, pml_aux)
+        alg2 = algorithmic(P.n, P.pml, P.b, 1, 8, pml_aux, tc=tcm)
         band_bytes = alg2["factor"]["bytes"]                   # every L and U band read once (complex64)
         design_bytes = band_bytes + alg2["chain"]["bytes"]     # + the transfer maps the sweep chain reads
         precond_apply = []

@@ -188,13 +188,15 @@ long long asp_take_launch_count(asp_handle* h);
  *   6 matvec                         7 FGMRES vector kernels
  *   8 3D tensor-core Schur updates (the rank-256 updates of the slab factor;
  *     their time is also part of phase 0)
+ *   9 diagonal blocks of the sweep subproblems' inverses (complex64 maps built
+ *     on the tensor cores; phase 1 is then the tensor-core map kernel alone)
  * In 3D, phase 0 is the whole slab factor per stream, phase 2 the launch of
  * all M-slab solves and phase 4 the paired sweep launches.
  * asp_phase_times synchronizes the device, writes per-phase total milliseconds
  * and launch counts (HOST arrays of nphases <= ASP_NUM_PHASES entries) and
  * resets the records.  Timing adds two event records per launch; it is off by
  * default. */
-#define ASP_NUM_PHASES 9
+#define ASP_NUM_PHASES 10
 int asp_set_phase_timing(asp_handle* h, int enable);
 int asp_phase_times(asp_handle* h, double* ms, long long* launches, int nphases);
 

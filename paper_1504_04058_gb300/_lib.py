@@ -37,7 +37,7 @@ EXPORTS = [
 ]
 NOALLOC_MAX_N = 4096
 NOALLOC_MAX_RHS = 64
-PHASES = ["factor", "tmap", "embed", "chain", "fill", "elementwise", "matvec", "krylov", "schur3d"]
+PHASES = ["factor", "tmap", "embed", "chain", "fill", "elementwise", "matvec", "krylov", "schur3d", "tdiag"]
 
 
 class asp_params(ctypes.Structure):

@@ -208,6 +208,18 @@ bool supported(const asp_params* p, std::string* why, int sms) {
 
 int fmax_rhs_cap(int prec) { return prec == ASP_PREC_C64 ? 64 : 16; }
 
+// complex64 maps of padded width <= kTmapTcMaxW are built on the tensor cores
+// (tmap_tc.cu) and need no forward-pass scratch of their own.
+bool tc_maps(int dim, int prec, int m, int wmaxRL) {
+  return dim == 2 && prec == ASP_PREC_C64 && m >= 3 && wmaxRL <= kTmapTcMaxW;
+}
+
+// Right-hand sides per scratch slot: the widest solve instance that uses the slot.
+int zslot_cols(int dim, int prec, int m, int wmaxRL) {
+  if (prec == ASP_PREC_C64) return tc_maps(dim, prec, m, wmaxRL) ? 32 : 64;
+  return 16;
+}
+
 Sizes sizes_for3(const asp_params* p, int num_sms) {
   Sizes Z;
   const int n = p->n, gamma = p->pml, ga = p->pml_aux ? p->pml_aux : p->pml, b = p->b;
@@ -275,7 +287,8 @@ Sizes sizes_for(const asp_params* p, int num_sms) {
   const int ldT = (n + 1) & ~1;
   Z.tmap_elems = P.m >= 3 ? (size_t)2 * (P.m - 2) * n * ldT : 0;
   Z.zslots = std::max(1, 4 * num_sms);
-  Z.zslot = (size_t)n * Z.wmax * fmax_rhs_cap(p->factor_prec);
+  Z.zslot = (size_t)n * Z.wmax * zslot_cols(2, p->factor_prec, P.m, Z.wmaxRL);
+  const bool tcm = tc_maps(2, p->factor_prec, P.m, Z.wmaxRL);
   const long long R = p->restart;
   const long long mr = p->max_rhs;
   size_t n2, nd, ni;
@@ -284,6 +297,8 @@ Sizes sizes_for(const asp_params* p, int num_sms) {
   bytes += Z.N * sizeof(double) + 3 * (size_t)n * sizeof(double2);              // k2, ca, cc, cd
   bytes += Z.coef * sizeof(SweepCoef) + Z.nsub * sizeof(SubDesc);
   bytes += Z.W_elems * Z.esz + Z.tmap_elems * Z.esz;
+  if (tcm) bytes += (size_t)2 * (P.m - 2) * (n * 2 * 32 * sizeof(float2) + sizeof(TmMap));  // Gamma columns, map table
+  bytes += (size_t)n * 2 * sizeof(float2);                                        // s1, 1/s1
   bytes += (size_t)Z.N * mr * Z.esz * (3 + (Z.esz == 8 ? 1 : 0));              // uM uR uL (+ r_lo)
   bytes += (size_t)2 * (P.m + 1) * n * ((mr + 1) & ~1) * Z.esz;                   // accR, accL
   bytes += (size_t)Z.zslots * Z.zslot * Z.esz;                                   // forward scratch
@@ -640,7 +655,7 @@ void asp_destroy(asp_handle* hd) {
     if (g.stream) cudaStreamDestroy(g.stream);
     if (g.done) cudaEventDestroy(g.done);
   }
-  void* ptrs[] = {H.k2, H.ca, H.cc, H.cd, H.d_subs, H.d_coef, H.W, H.tmap, H.d_toffR, H.d_toffL, H.r_lo,
+  void* ptrs[] = {H.k2, H.ca, H.cc, H.cd, H.d_subs, H.d_coef, H.W, H.tmap, H.d_toffR, H.d_toffL, H.d_tm, H.gdiag, H.r_lo,
                   H.uM, H.uR, H.uL, H.accR, H.accL, H.zscr, H.bar, H.V, H.Z, H.wv, H.red, H.hess, H.kstate,
                   H.kflags, H.err, H.d_slabs, H.d_slab_lists, H.A3, H.piv3, H.z3, H.tc_area};
   for (void* p : ptrs)
@@ -702,10 +717,13 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   g.hi_edge = (n + 1 - H.gamma) * h;
   g.eta_lo = g.eta_hi = H.gamma * h;
   g.C = p->C;
-  std::vector<double2> ca(n), cc(n), cd(n);
+  std::vector<double2> ca(n), cc(n), cd(n), s1v(n), s1i(n);
   for (int k = 0; k < n; ++k) {
     const double x = (k + 1) * h;
     const double2 sk = g.s(x, omega), sm = g.s(x - 0.5 * h, omega), sp = g.s(x + 0.5 * h, omega);
+    s1v[k] = sk;
+    const double d2 = sk.x * sk.x + sk.y * sk.y;
+    s1i[k] = make_double2(sk.x / d2, -sk.y / d2);
     ca[k] = hscale(hmul(sk, sm), ih2);
     cc[k] = hscale(hmul(sk, sp), ih2);
     cd[k] = hscale(hadd(ca[k], cc[k]), -1.0);
@@ -776,12 +794,20 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
     pr.hi_edge = H.beta[q] * h;  pr.eta_hi = (q == m) ? eta : eta_a;
     H.subM[q] = add(KIND_M, q, P.m_lo[q], P.m_hi[q], pr);
   }
+  // s2(keep) / s2(in) of each sweep subproblem (the map's symmetry factor)
+  std::vector<double2> rhoR(m + 1, make_double2(1, 0)), rhoL(m + 1, make_double2(1, 0));
+  auto sratio = [&](const Profile& pr, int keep_g, int in_g) {
+    const double2 a = pr.s(keep_g * h, omega), b = pr.s(in_g * h, omega);
+    const double d2 = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d2, (a.y * b.x - a.x * b.y) / d2);
+  };
   for (int q = 2; q <= m; ++q) {
     Profile pr;  // sigma_q^R: no layer on the left
     pr.C = p->C;
     pr.hi_on = true;
     pr.hi_edge = H.beta[q] * h; pr.eta_hi = (q == m) ? eta : eta_a;
     H.subR[q] = add(KIND_R, q, H.alpha[q], P.m_hi[q], pr);
+    rhoR[q] = sratio(pr, H.x_hi[q], H.alpha[q]);
   }
   for (int q = 1; q <= m - 1; ++q) {
     Profile pr;  // sigma_q^L: no layer on the right
@@ -789,6 +815,7 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
     pr.lo_on = true;
     pr.lo_edge = H.alpha[q] * h; pr.eta_lo = (q == 1) ? eta : eta_a;
     H.subL[q] = add(KIND_L, q, P.m_lo[q], H.beta[q], pr);
+    rhoL[q] = sratio(pr, H.x_lo[q], H.beta[q]);
   }
   H.W_elems = (size_t)woff;
   // transfer maps T_p^R, T_p^L for p = 2..m-1 (2D only)
@@ -802,6 +829,25 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
     }
   }
   H.tmap_elems = (size_t)toff;
+  if (tc_maps(H.dim, H.prec, m, H.wmaxRL)) {
+    long long goff = 0;
+    for (int q = 2; q <= m - 1; ++q)
+      for (int kind = 0; kind < 2; ++kind) {
+        const SubDesc& S = H.subs[kind == 0 ? H.subR[q] : H.subL[q]];
+        TmMap M{};
+        M.woff = S.woff;
+        M.toff = S.toff;
+        M.goff = goff;
+        goff += (long long)n * 2 * 32;
+        M.w = S.w;
+        M.wp = S.wp;
+        M.jin = kind == 0 ? 0 : S.w - 1;
+        M.keep = kind == 0 ? S.xoff + S.xw - 1 : S.xoff;
+        const double2 rho = kind == 0 ? rhoR[q] : rhoL[q];
+        M.rho = make_float2((float)rho.x, (float)rho.y);
+        H.tm_host.push_back(M);
+      }
+  }
 
   // ---- device allocations
   const size_t esz = Z.esz;
@@ -828,6 +874,10 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
     H.zslots = Z.zslots;
     H.zslot = (long long)Z.zslot;
     dal(&H.zscr, (size_t)Z.zslots * Z.zslot * esz);
+    if (!H.tm_host.empty()) {
+      dal((void**)&H.d_tm, H.tm_host.size() * sizeof(TmMap));
+      dal(&H.gdiag, H.tm_host.size() * (size_t)n * 2 * 32 * sizeof(float2));
+    }
   } else {
     dal((void**)&H.d_slabs, H.slabs.size() * sizeof(Slab));
     dal((void**)&H.d_slab_lists, H.slabs.size() * sizeof(int));
@@ -872,6 +922,7 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   cp(H.d_coef, H.coef.data(), H.coef.size() * sizeof(SweepCoef));
   if (H.dim == 2) {
     cp(H.d_subs, H.subs.data(), H.subs.size() * sizeof(SubDesc));
+    if (!H.tm_host.empty()) cp(H.d_tm, H.tm_host.data(), H.tm_host.size() * sizeof(TmMap));
     cp(H.d_toffR, H.toffR.data(), (m + 1) * sizeof(long long));
     cp(H.d_toffL, H.toffL.data(), (m + 1) * sizeof(long long));
   } else {
@@ -935,6 +986,8 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
       return d;
     };
     if (H.prec == ASP_PREC_C128) {
+      H.fc64.s1 = (const double2*)put(s1v.data(), n * sizeof(double2));
+      H.fc64.s1inv = (const double2*)put(s1i.data(), n * sizeof(double2));
       H.fc64.ca = (const double2*)put(ca.data(), n * sizeof(double2));
       H.fc64.cc = (const double2*)put(cc.data(), n * sizeof(double2));
       H.fc64.cd = (const double2*)put(cd.data(), n * sizeof(double2));
@@ -951,6 +1004,9 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
       std::vector<float> k2f(N);
       for (long long i = 0; i < N; ++i) k2f[i] = (float)k2[i];
       auto caf = f2(ca), ccf = f2(cc), cdf = f2(cd), upf = f2(upv), dnf = f2(dnv), dgf = f2(dgv);
+      auto s1f = f2(s1v), s1if = f2(s1i);
+      H.fc32.s1 = (const float2*)put(s1f.data(), n * sizeof(float2));
+      H.fc32.s1inv = (const float2*)put(s1if.data(), n * sizeof(float2));
       H.fc32.ca = (const float2*)put(caf.data(), n * sizeof(float2));
       H.fc32.cc = (const float2*)put(ccf.data(), n * sizeof(float2));
       H.fc32.cd = (const float2*)put(cdf.data(), n * sizeof(float2));
@@ -998,8 +1054,19 @@ int asp_factor(asp_handle* hd, void* stream) {
   ce = launch_factor(H, m, (int)H.subs.size() - m, s);
   phase_end(H, tb, s);
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString(ce));
-  // transfer maps: columns of T_p^R and T_p^L in chunks of right-hand sides
-  if (H.m >= 3) {
+  // transfer maps: on the tensor cores from the diagonal blocks of the inverse
+  // (complex64, widths <= 32), else columns of T_p^R and T_p^L in chunks of
+  // right-hand sides (CLS_TMAP solves)
+  if (!H.tm_host.empty()) {
+    PhaseTok td = phase_begin(H, PH_TDIAG, s);
+    ce = launch_tmap_diag(H, s);
+    phase_end(H, td, s);
+    if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("diagonal-block launch: ") + cudaGetErrorString(ce));
+    PhaseTok tk = phase_begin(H, PH_TMAP, s);
+    ce = launch_tmap_tc(H, s);
+    phase_end(H, tk, s);
+    if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("transfer-map launch: ") + cudaGetErrorString(ce));
+  } else if (H.m >= 3) {
     const int cap = btsolve_rhs_capacity(H.n, H.wmaxRL, H.prec, true);
     JobCache& jc = cache_of(&H);
     if (!jc.have_tmap) {

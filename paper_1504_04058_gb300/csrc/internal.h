@@ -65,6 +65,8 @@ template <> struct CplxOf<double> { using T = double2; };
 // the sweep-axis weights of every subproblem column (concatenated, SubDesc::prof).
 template <typename R> struct FactorCoefs {
   using C = typename CplxOf<R>::T;
+  const C* s1 = nullptr;     // s at the x1 nodes (boundary PML), and its reciprocal
+  const C* s1inv = nullptr;
   const C* ca = nullptr;
   const C* cc = nullptr;
   const C* cd = nullptr;
@@ -98,6 +100,18 @@ struct SolveParams {
   long long zslot;  // elements per slot
   int zslots;       // number of slots (upper bound on the grid)
   int* err;
+};
+
+// One trace-transfer map built on the tensor cores (tmap_tc.cu): complex64
+// factors, padded subproblem width <= kTmapTcMaxW.
+constexpr int kTmapTcMaxW = 32;
+struct TmMap {
+  long long woff;  // element offset of its subproblem's factor blocks
+  long long toff;  // element offset of the map
+  long long goff;  // element offset of its diagonal-block columns ([n][2][32])
+  int w, wp;       // padded width and block leading dimension of the subproblem
+  int jin, keep;   // boundary-data column and traced column (local)
+  float2 rho;      // s2(keep) / s2(in) of the subproblem's sweep profile
 };
 
 struct ChainParams {
@@ -199,7 +213,7 @@ struct Handle;
 
 enum Phase : int {
   PH_FACTOR = 0, PH_TMAP = 1, PH_EMBED = 2, PH_CHAIN = 3, PH_FILL = 4, PH_SUM = 5, PH_MATVEC = 6,
-  PH_KRYLOV = 7, PH_SCHUR = 8, PH_COUNT = 9
+  PH_KRYLOV = 7, PH_SCHUR = 8, PH_TDIAG = 9, PH_COUNT = 10
 };
 
 // Records CUDA events around launches when phase timing is enabled.
@@ -217,6 +231,8 @@ cudaError_t launch_btsolve_apply(Handle& H, const SolveParams& P, int cls, int c
 cudaError_t launch_btsolve_aux(Handle& H, const SolveParams& P, int cls, int cap, int wmax, cudaStream_t s);
 int btsolve_rhs_capacity(int nrhs, int wmax, int prec, bool tmap);
 cudaError_t launch_chain(Handle& H, const ChainParams& P, cudaStream_t s);
+cudaError_t launch_tmap_diag(Handle& H, cudaStream_t s);
+cudaError_t launch_tmap_tc(Handle& H, cudaStream_t s);
 cudaError_t launch_to_prec(const double2* in, void* out, long long count, int prec, cudaStream_t s);
 // z = a + b (planes >= r_from) + c (planes < l_below), planes of per_col elements
 cudaError_t launch_sum3(const void* a, const void* b, const void* c, double2* z, long long per_col, int ncols,
@@ -271,6 +287,10 @@ struct Handle {
   std::vector<long long> toffR, toffL;
   long long* d_toffR = nullptr;
   long long* d_toffL = nullptr;
+  // maps built on the tensor cores (empty: the maps come from CLS_TMAP solves)
+  std::vector<TmMap> tm_host;
+  TmMap* d_tm = nullptr;
+  void* gdiag = nullptr;  // diagonal-block columns of every such map
   bool factored = false;
 
   // apply workspace (factor precision), sized for max_rhs

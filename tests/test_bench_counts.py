@@ -50,6 +50,26 @@ def test_transfer_map_flops_match_a_count_of_block_steps(bench, n, gamma, b):
 
 
 @pytest.mark.parametrize("n,gamma,b", CASES)
+def test_tensor_core_map_flops_match_a_count_of_chain_steps(bench, n, gamma, b):
+    """Maps from the diagonal blocks of the inverse: a column with data in
+    block r runs r chain steps (blocks r-1 .. 0), once for the upper triangle
+    (data in the boundary column) and once for the lower (data in the traced
+    column), one w x w complex product per step; the diagonal-block recursion
+    takes two w x w x w complex products per block below the last."""
+    m, wM, wR, wL, wT = bench._layer_widths(n, gamma, b)
+    counted = 0
+    counted_diag = 0
+    for w in wT:
+        for _kind in ("R", "L"):
+            for _family in ("upper", "lower"):
+                counted += 8 * sum(r * w * w for r in range(n))
+            counted_diag += 8 * 2 * (n - 1) * w ** 3
+    alg = bench.algorithmic(n, gamma, b, 1, 8, tc=True)
+    assert alg["tmap"]["flops"] == counted
+    assert alg["tdiag"]["flops"] == counted_diag
+
+
+@pytest.mark.parametrize("n,gamma,b", CASES)
 @pytest.mark.parametrize("nrhs", [1, 32])
 def test_layer_solve_flops_match_a_count_of_block_steps(bench, n, gamma, b, nrhs):
     """M-solves and fills: one full solve per subproblem and right-hand side.
