@@ -18,6 +18,12 @@ Readings taken here (each also listed in the design notes):
   remainder r = P - m b.
 * The auxiliary PML width gamma_a may differ from gamma (practical remark 2);
   the boundary PML of X_1 (left) and X_m (right) stays gamma wide.
+* The layers' widths b_1, ..., b_m may differ (practical remark 3: widths are
+  arbitrary, larger where the velocity varies heavily).  With physical widths
+  b_p summing to P, alpha_p = gamma + b_1 + ... + b_{p-1} and
+  beta_p = alpha_p + b_p - 1, and the printed ranges above hold with (p-1)b
+  replaced by b_1 + ... + b_{p-1}; equal widths b with the remainder on the
+  last layer give the formulas as printed.
 """
 from __future__ import annotations
 
@@ -55,25 +61,42 @@ class Partition:
         return 1.0 / (self.n + 1)
 
 
-def make_partition(n: int, gamma: int, b: int, gamma_a: int | None = None) -> Partition:
+def uniform_widths(n: int, gamma: int, b: int) -> list:
+    """m = floor(P/b) layers of b physical columns, the last one absorbing the
+    remainder P - m b (P = n + 2 - 2 gamma)."""
+    P = n + 2 - 2 * gamma
+    m = P // b
+    if m < 1:
+        raise ValueError(f"n={n} too small for gamma={gamma}, b={b}")
+    return [b] * (m - 1) + [b + P - m * b]
+
+
+def make_partition(n: int, gamma: int, b: int, gamma_a: int | None = None, widths=None) -> Partition:
+    """Layers of b physical columns (the last absorbing the remainder), or of
+    the given physical widths b_1..b_m (summing to P = n + 2 - 2 gamma)."""
     if gamma_a is None:
         gamma_a = gamma
     if gamma < 2 or b < 1 or gamma_a < 1:
         raise ValueError("need gamma >= 2, gamma_a >= 1, b >= 1")
     P = n + 2 - 2 * gamma
-    m = P // b
-    if m < 1:
-        raise ValueError(f"n={n} too small for gamma={gamma}, b={b}")
+    if widths is None:
+        widths = uniform_widths(n, gamma, b)
+    widths = [int(x) for x in widths]
+    if min(widths) < 1 or sum(widths) != P:
+        raise ValueError(f"layer widths must be positive and sum to P = {P}")
+    m = len(widths)
     layers = []
+    alpha = gamma
     for p in range(1, m + 1):
-        alpha = gamma + (p - 1) * b
-        beta = gamma + p * b - 1 if p < m else n + 1 - gamma
+        beta = alpha + widths[p - 1] - 1
+        assert p < m or beta == n + 1 - gamma
         x_lo = 1 if p == 1 else alpha
         x_hi = n if p == m else beta
         m_lo = 1 if p == 1 else alpha - gamma_a + 1
         m_hi = n if p == m else beta + gamma_a - 1
         layers.append(Layer(p, x_lo, x_hi, alpha, beta, m_lo, m_hi,
                             alpha, m_hi, m_lo, beta))
+        alpha = beta + 1
     return Partition(n, gamma, gamma_a, b, m, tuple(layers))
 
 

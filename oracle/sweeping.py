@@ -30,10 +30,12 @@ class Preconditioner:
     """Algorithm 1 at construction, Algorithm 2 in :meth:`apply`."""
 
     def __init__(self, dim: int, n: int, omega: float, c: np.ndarray, gamma: int, b: int,
-                 C: float = 20.0, gamma_a: int | None = None, layers=None):
+                 C: float = 20.0, gamma_a: int | None = None, layers=None, widths=None):
         self.dim, self.n, self.omega, self.gamma, self.b, self.C = dim, n, omega, gamma, b, C
         self.c = np.asarray(c, dtype=np.float64)
-        self.part: Partition = make_partition(n, gamma, b, gamma_a)
+        # widths: physical layer widths b_1..b_m (Section 3.1, practical remark 3);
+        # None = b columns per layer, the last absorbing the remainder
+        self.part: Partition = make_partition(n, gamma, b, gamma_a, widths)
         self.T = n ** (dim - 1)
         m = self.part.m
         args = (dim, n, omega, self.c, gamma, C, self.part)

@@ -119,6 +119,27 @@ def test_partition_matches_printed_index_formulas():
         assert got == (int(lo), int(hi)), (kind, p, got)
 
 
+def test_partition_with_arbitrary_widths_matches_hand_evaluated_ranges():
+    """Section 3.1, practical remark 3: layers of arbitrary widths (here 3, 1,
+    4, 2 with a thinner auxiliary PML), ranges evaluated by hand
+    (tests/golden/partition_widths_3142.txt)."""
+    rows = [ln.split() for ln in open(os.path.join(GOLD, "partition_widths_3142.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    part = partition.make_partition(14, 3, 1, gamma_a=2, widths=[3, 1, 4, 2])
+    assert part.m == 4
+    for kind, p, lo, hi in rows:
+        L = part.layers[int(p) - 1]
+        got = {"X": (L.x_lo, L.x_hi), "M": (L.m_lo, L.m_hi), "R": (L.r_lo, L.r_hi),
+               "L": (L.l_lo, L.l_hi)}[kind]
+        assert got == (int(lo), int(hi)), (kind, p, got)
+    # equal widths with the remainder on the last layer reproduce the printed formulas
+    u = partition.make_partition(40, 5, 4)
+    w = partition.make_partition(40, 5, 4, widths=partition.uniform_widths(40, 5, 4))
+    assert u.layers == w.layers
+    with pytest.raises(ValueError):
+        partition.make_partition(14, 3, 1, widths=[3, 1, 4, 1])  # does not sum to P
+
+
 def _aux_fixture():
     """tests/golden/aux_pml_gamma4_ga2_b3.txt: padded grids and sigma*h/C of
     every subproblem at n=18, gamma=4, gamma_a=2, b=3, evaluated by hand from
@@ -341,6 +362,31 @@ def test_accumulated_sweep_equals_naive_superposition(dim, n, gamma, b):
     z1 = pc.apply(P.f)
     z2 = pc.apply_naive(P.f)
     assert np.linalg.norm(z1 - z2) <= 1e-12 * np.linalg.norm(z1)
+
+
+@pytest.mark.parametrize("dim,n,gamma,widths", [(1, 40, 4, [2, 7, 1, 5, 3, 6, 3, 7]), (2, 23, 4, [2, 5, 1, 4, 5]),
+                                                 (3, 11, 3, [1, 3, 3])])
+def test_accumulated_sweep_with_arbitrary_widths_equals_naive_superposition(dim, n, gamma, widths):
+    """The same identity with layers of arbitrary widths (Section 3.1, practical
+    remark 3), including one-column layers, and with the subproblems of such
+    layers solving their boundary value problems."""
+    omega = 2 * math.pi * 2.0
+    assert sum(widths) == n + 2 - 2 * gamma
+    P = W.small_problem(dim, n, omega, gamma, 1, "lens" if dim > 1 else "const", nrhs=2)
+    pc = sweeping.Preconditioner(dim, n, omega, P.c, gamma, 1, P.C, widths=widths)
+    assert pc.m == len(widths)
+    z1 = pc.apply(P.f)
+    z2 = pc.apply_naive(P.f)
+    assert np.linalg.norm(z1 - z2) <= 1e-12 * np.linalg.norm(z1)
+    part = pc.part
+    rng = np.random.default_rng(3)
+    T = n ** (dim - 1)
+    for p, kind in ((2, "R"), (part.m - 1, "L")):
+        F = pc.FR[p] if kind == "R" else pc.FL[p]
+        w = rng.standard_normal(T) + 1j * rng.standard_normal(T)
+        got = (subproblems.G_R if kind == "R" else subproblems.G_L)(F, w, part.h)
+        ref = _bvp_solution(dim, n, omega, P.c, gamma, P.C, part, p, kind, w)
+        assert np.allclose(got, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
 
 
 @pytest.mark.parametrize("dim,n", [(1, 20), (2, 11), (3, 7)])
