@@ -36,10 +36,12 @@
 // Gamma_k e_keep for every k.
 //
 // tmap_tc_kernel runs the chains on the tensor cores.  A tile's state (128
-// columns x w complex) is the real matrix A (128 x 2w, K-major, re and im
-// interleaved along K); -c_k W_k becomes the real matrix B_k^T (2w x 2w) with
-// the 2 x 2 block [[re v, -im v], [im v, re v]] per complex entry, so
-// D = A B_k^T is the next state in the same layout.  Split precision as in the
+// columns x w complex) is the real matrix A (128 x 2w, re and im interleaved
+// along K) and lives in tensor memory, one column per row: the MMAs read it
+// from there and the epilogue writes the next state back with tcgen05.st, so
+// shared memory carries only the small W operand.  -c_k W_k becomes the real
+// matrix B_k^T (2w x 2w) with the 2 x 2 block [[re v, -im v], [im v, re v]] per
+// complex entry, so D = A B_k^T is the next state in the same layout.  Split precision as in the
 // 3D Schur update: x_hi = x with its 13 low mantissa bits cleared, x_lo =
 // x - x_hi, D = A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 (kind::tf32, M = 128,
 // N = 2w rounded up to 16, K = 8 per instruction), which keeps the maps within
@@ -48,14 +50,16 @@
 //   warp 0      TMA producer: W_k and the step's two diagonal-block columns by
 //               1D bulk copies into a ring of W stages (and the TMEM allocation);
 //   warp 1      MMA issuer: per step, both tiles' products into their TMEM
-//               accumulators once B_k and the tile's state are in shared memory;
+//               accumulators once B_k is in shared memory and the tile's state
+//               in tensor memory;
 //   warps 2-5   converter: -c_k W_k into the split B_k^T stage (128-byte
 //               swizzled, as the MMA descriptors read it), and the step's
 //               injected columns and output scale into a small ring;
 //   warps 6-9   epilogue of the family-A tile, warps 10-13 of the family-B
 //               tile: one thread per column reads its accumulator row
 //               (tcgen05.ld), injects Gamma_k e at r = k, writes the map
-//               entries, and stores the split state back for the next step.
+//               entries, and stores the split state back (tcgen05.st) for the
+//               next step.
 // Every wait is bounded; a timeout records ASP_ERR_TIMEOUT and makes every role
 // stop; the issuer then waits (bounded) for its products and the producer for
 // its copies before the tensor memory is freed.
@@ -76,14 +80,17 @@ constexpr int kTT = 128;       // columns per tile (the MMA's M)
 constexpr int kGS = 32;        // complex entries per stored diagonal-block column (>= w)
 constexpr int kThreadsTm = 14 * 32;
 constexpr int kInjRing = 4;    // steps of injected columns held by the converter ring
-constexpr uint32_t kTmemColsTm = 128;  // two accumulators of up to 64 FP32 columns
+// tensor memory per tile: the accumulator D, then the state A_hi and A_lo (up
+// to 64 columns each), tiles 256 columns apart
+constexpr uint32_t kTmemColsTm = 512;
+constexpr uint32_t kTileCols = 256, kAhiCol = 64, kAloCol = 128;
 
 struct TmParams {
   const TmMap* maps;
   int nmaps, ntiles;  // ntiles: 128-column tiles per family (ceil(n / 128))
   int n, ldT;
   int wcap, K8, N16, natoms, wstages;
-  uint32_t a_half, b_half, w_stage;  // bytes: one tile's A_hi, one stage's B_hi, one W stage
+  uint32_t b_half, w_stage;  // bytes: one stage's B_hi, one W stage
   uint32_t idesc;
   float inv_h2;
   const float2* W;
@@ -116,12 +123,13 @@ __device__ __forceinline__ uint64_t sw128(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void mma_tf32_tm(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// D (tensor memory) (+)= A (tensor memory, row m in lane m) B (shared memory).
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+      "r"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 
@@ -153,6 +161,16 @@ __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -196,14 +214,15 @@ struct InjSlot {
   float2 pad;
 };
 
-__global__ void __launch_bounds__(kThreadsTm, 1) tmap_tc_kernel(const __grid_constant__ TmParams P) {
+// At most 80 registers a thread (35,840 a CTA), so that a CTA fits on an SM
+// beside two CTAs of the M-subproblem factor that runs concurrently.
+__global__ void __maxnreg__(80) tmap_tc_kernel(const __grid_constant__ TmParams P) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t sraw = smem_addr(smem_raw);
   const uint32_t sbase = (sraw + 1023u) & ~1023u;
   unsigned char* sgen = smem_raw + (sbase - sraw);
-  // layout: A tiles [2][hi, lo], B stages [2][hi, lo], W stages, then the injection ring
-  const uint32_t offA = 0;
-  const uint32_t offB = offA + 4 * P.a_half;
+  // layout: B stages [2][hi, lo], W stages, then the injection ring
+  const uint32_t offB = 0;
   const uint32_t offW = offB + 4 * P.b_half;
   const uint32_t offI = offW + (uint32_t)P.wstages * P.w_stage;
   InjSlot* inj = reinterpret_cast<InjSlot*>(sgen + offI);
@@ -296,16 +315,19 @@ __global__ void __launch_bounds__(kThreadsTm, 1) tmap_tc_kernel(const __grid_con
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t d = tmem + (uint32_t)(tau * 64);
-            const uint32_t ah = sbase + offA + (uint32_t)(2 * tau) * P.a_half, al = ah + P.a_half;
-            const uint32_t bh = sbase + offB + (uint32_t)(2 * sb) * P.b_half, bl = bh + P.b_half;
+            const uint32_t d = tmem + (uint32_t)tau * kTileCols;
+            const uint32_t ah = d + kAhiCol, al = d + kAloCol;
+            // the descriptors differ only in their start-address field (bits 0-13,
+            // address / 16): step them by offset / 16
+            const uint64_t dbh = sw128(sbase + offB + (uint32_t)(2 * sb) * P.b_half);
+            const uint64_t dbl = dbh + (uint64_t)(P.b_half >> 4);
+            const uint32_t atom16 = (uint32_t)(P.N16 * 128) >> 4;
             for (int kk = 0; kk < P.K8 / 8; ++kk) {
-              const uint32_t atom = (uint32_t)(kk >> 2), ko = (uint32_t)(kk & 3) * 32;
-              const uint32_t aoff = atom * (kTT * 128) + ko;
-              const uint32_t boff = atom * (uint32_t)(P.N16 * 128) + ko;
-              mma_tf32_tm(d, sw128(ah + aoff), sw128(bh + boff), P.idesc, kk > 0 ? 1u : 0u);
-              mma_tf32_tm(d, sw128(ah + aoff), sw128(bl + boff), P.idesc, 1u);
-              mma_tf32_tm(d, sw128(al + aoff), sw128(bh + boff), P.idesc, 1u);
+              const uint64_t boff = (uint64_t)((uint32_t)(kk >> 2) * atom16 + (uint32_t)(kk & 3) * 2);
+              const uint32_t ac = (uint32_t)(kk * 8);  // 8 K columns per instruction
+              mma_tf32_ta(d, ah + ac, dbh + boff, P.idesc, kk > 0 ? 1u : 0u);
+              mma_tf32_ta(d, ah + ac, dbl + boff, P.idesc, 1u);
+              mma_tf32_ta(d, al + ac, dbh + boff, P.idesc, 1u);
             }
             issued = true;
             commit_tm(&dfull[tau]);
@@ -348,8 +370,12 @@ __global__ void __launch_bounds__(kThreadsTm, 1) tmap_tc_kernel(const __grid_con
                                                            2 * kGS * 8);
         unsigned char* bhi = sgen + offB + (uint32_t)(2 * sb) * P.b_half;
         unsigned char* blo = bhi + P.b_half;
-        for (int e = ct; e < wcap * wcap; e += 128) {
-          const int i = e % wcap, jj = e / wcap;
+        // a warp converts 4 x 8 entries (i, jj) at a time: its 32 float2 stores
+        // fall on distinct 8-byte bank pairs of the swizzled rows 2i, 2i+1
+        const int nti = (wcap + 3) >> 2, ntj = (wcap + 7) >> 3;
+        for (int tt = ct >> 5; tt < nti * ntj; tt += 4) {
+          const int i = (tt / ntj) * 4 + (lane >> 3), jj = (tt % ntj) * 8 + (lane & 7);
+          if (i >= wcap || jj >= wcap) continue;
           float2 v = make_float2(0.f, 0.f);
           if (i < w && jj < w) {
             const float2 wv = Wk[jj * wp + i];
@@ -379,9 +405,8 @@ __global__ void __launch_bounds__(kThreadsTm, 1) tmap_tc_kernel(const __grid_con
     const int tau = (warp - 6) >> 2;
     const int q = warp & 3;
     const int m = q * 32 + lane;
-    unsigned char* ahi = sgen + offA + (uint32_t)(2 * tau) * P.a_half;
-    unsigned char* alo = ahi + P.a_half;
-    const uint32_t dcol = tmem + (uint32_t)(tau * 64) + ((uint32_t)(q * 32) << 16);
+    const uint32_t dcol = tmem + (uint32_t)tau * kTileCols + ((uint32_t)(q * 32) << 16);
+    const uint32_t ahi = dcol + kAhiCol, alo = dcol + kAloCol;
     uint32_t dc = 0;
     bool stop = false;
     for (int j = blockIdx.x; j < njobs && !stop; j += gridDim.x) {
@@ -394,14 +419,15 @@ __global__ void __launch_bounds__(kThreadsTm, 1) tmap_tc_kernel(const __grid_con
       if (tau == 1 && valid) s1r = P.s1[r];
       float2* Tm = P.T + M.toff;
       // the state before the first step is zero
-      for (int a = 0; a < P.natoms; ++a)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const uint32_t o = (uint32_t)a * (kTT * 128) + swz(m, 4 * c);
-          *reinterpret_cast<float4*>(ahi + o) = make_float4(0.f, 0.f, 0.f, 0.f);
-          *reinterpret_cast<float4*>(alo + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+      {
+        const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int c = 0; c < P.K8; c += 8) {
+          tmem_st8(ahi + (uint32_t)c, z);
+          tmem_st8(alo + (uint32_t)c, z);
         }
-      fence_async_smem();
+        tmem_wait_st();
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       arrive_tm(&afull[tau]);
       for (int k = J.kmax; k >= 0; --k, ++dc) {
         if (!tm_wait(&dfull[tau], dc & 1u, abort_flag)) {
@@ -410,31 +436,20 @@ __global__ void __launch_bounds__(kThreadsTm, 1) tmap_tc_kernel(const __grid_con
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float d[64];
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (c * 16 < P.N16) tmem_ld16(dcol + (uint32_t)(c * 16), d + c * 16);
-        // the written-out entry, read on its own (no runtime index into d)
+        // the written-out entry first, read on its own (no runtime index into
+        // a register array), with the first 16 accumulator columns
         float sre = tmem_ld1(dcol + (uint32_t)(2 * sel));
         float sim = tmem_ld1(dcol + (uint32_t)(2 * sel + 1));
+        float da[16], db[16];
+        tmem_ld16(dcol, da);
         tmem_wait_ld();
         // tie the loaded registers to the wait, so that no use moves above it
 #pragma unroll
-        for (int i = 0; i < 64; ++i)
-          if (i < P.N16) asm volatile("" : "+f"(d[i]));
+        for (int i = 0; i < 16; ++i) asm volatile("" : "+f"(da[i]));
         asm volatile("" : "+f"(sre), "+f"(sim));
         const InjSlot& S = inj[dc % kInjRing];
         const bool injecting = valid && r == k;
-        float2 out = make_float2(sre, sim);
-        if (injecting) {
-          out = S.col[tau][sel];
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const float2 g = S.col[tau][i];
-            d[2 * i] = g.x;
-            d[2 * i + 1] = g.y;
-          }
-        }
+        const float2 out = injecting ? S.col[tau][sel] : make_float2(sre, sim);
         if (valid) {
           if (tau == 0 && r >= k) {
             Tm[(long long)k * P.ldT + r] = make_float2(-P.inv_h2 * out.x, -P.inv_h2 * out.y);
@@ -445,24 +460,46 @@ __global__ void __launch_bounds__(kThreadsTm, 1) tmap_tc_kernel(const __grid_con
           }
         }
         if (k > 0) {
-          // the next step's state, split, in the 128-byte-swizzled K-major layout
+          // the next step's state, split, one tensor-memory column per float,
+          // 16 columns at a time: the next chunk's load is in flight while
+          // this one is split and stored
           const int K2 = 2 * M.w;
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            if (c * 4 >= P.natoms * 32) break;
-            float h[4], l[4];
+          for (int c = 0; c < 4; ++c) {
+            if (c * 16 >= P.K8) break;
+            float* cur = (c & 1) ? db : da;
+            float* nxt = (c & 1) ? da : db;
+            const bool more = (c + 1) * 16 < P.K8;
+            if (more) tmem_ld16(dcol + (uint32_t)((c + 1) * 16), nxt);
+            if (injecting) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int f = c * 4 + e;
-              const float x = f < K2 ? d[f] : 0.f;
-              h[e] = tf32_hi(x);
-              l[e] = x - h[e];
+              for (int e = 0; e < 8; ++e) {
+                const float2 g = S.col[tau][c * 8 + e];
+                cur[2 * e] = g.x;
+                cur[2 * e + 1] = g.y;
+              }
             }
-            const uint32_t o = (uint32_t)(c >> 3) * (kTT * 128) + swz(m, (c & 7) * 4);
-            *reinterpret_cast<float4*>(ahi + o) = make_float4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<float4*>(alo + o) = make_float4(l[0], l[1], l[2], l[3]);
+#pragma unroll
+            for (int h8 = 0; h8 < 2; ++h8) {
+              if (c * 16 + h8 * 8 >= P.K8) break;
+              float hv[8], lv[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const int f = c * 16 + h8 * 8 + e;
+                const float x = f < K2 ? cur[h8 * 8 + e] : 0.f;
+                hv[e] = tf32_hi(x);
+                lv[e] = x - hv[e];
+              }
+              tmem_st8(ahi + (uint32_t)(c * 16 + h8 * 8), hv);
+              tmem_st8(alo + (uint32_t)(c * 16 + h8 * 8), lv);
+            }
+            if (more) {
+              tmem_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 16; ++i) asm volatile("" : "+f"(nxt[i]));
+            }
           }
-          fence_async_smem();
+          tmem_wait_st();
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           arrive_tm(&afull[tau]);
         }
@@ -516,6 +553,7 @@ __global__ void __launch_bounds__(kGdThreads) gdiag_kernel(const TmMap* __restri
     }
   };
   emit(n - 1);
+  float2 beta_next = n >= 2 ? cmul(cc[n - 2], ca[n - 1]) : make_float2(0.f, 0.f);
   for (int k = n - 2; k >= 0; --k) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) sW[i][j0 + 8 * u] = wr[u];
@@ -534,7 +572,8 @@ __global__ void __launch_bounds__(kGdThreads) gdiag_kernel(const TmMap* __restri
     for (int u = 0; u < 4; ++u) sP[i][j0 + 8 * u] = acc[u];
     __syncthreads();
     // Gamma_k = W_k + beta P W_k
-    const float2 beta = cmul(cc[k], ca[k + 1]);
+    const float2 beta = beta_next;
+    if (k >= 1) beta_next = cmul(cc[k - 1], ca[k]);  // in flight during this step
 #pragma unroll
     for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
     for (int l = 0; l < w; ++l) {
@@ -587,7 +626,6 @@ cudaError_t launch_tmap_tc(Handle& H, cudaStream_t s) {
   P.K8 = (2 * wcap + 7) / 8 * 8;
   P.N16 = (2 * wcap + 15) / 16 * 16;
   P.natoms = (P.K8 + 31) / 32;
-  P.a_half = (uint32_t)P.natoms * kTT * 128;
   P.b_half = (uint32_t)P.natoms * (uint32_t)P.N16 * 128;
   int wpc = 0;
   for (const TmMap& M : H.tm_host) wpc = std::max(wpc, M.w * M.wp * 8);
@@ -606,7 +644,7 @@ cudaError_t launch_tmap_tc(Handle& H, cudaStream_t s) {
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  const size_t fixed = 1024 + 4 * (size_t)P.a_half + 4 * (size_t)P.b_half + kInjRing * sizeof(InjSlot);
+  const size_t fixed = 1024 + 4 * (size_t)P.b_half + kInjRing * sizeof(InjSlot);
   cudaFuncAttributes fa{};
   if ((e = cudaFuncGetAttributes(&fa, (const void*)tmap_tc_kernel)) != cudaSuccess) return e;
   const size_t limit = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
