@@ -139,27 +139,48 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
-def _layer_widths(n, gamma, b, gamma_a=None):
-    """Layer count from the boundary PML gamma; padded widths from the auxiliary PML gamma_a."""
+def _layer_widths(n, gamma, b, gamma_a=None, widths=None):
+    """Layer count and padded subproblem widths: layers of the given physical
+    widths (default: b columns, the last one taking the remainder of the
+    P = n + 2 - 2*gamma physical columns), padded by gamma_a - 1 auxiliary-PML
+    columns on their inner sides (the first layer's grid starts at column 1,
+    the last one's ends at column n).  wT: the R and L subproblems that have a
+    transfer map (p = 2..m-1)."""
     ga = gamma if not gamma_a else gamma_a
     P = n + 2 - 2 * gamma
-    m = P // b
-    r = P - m * b
-    wM = [2 * ga + b - 2 + (r if q == m else 0) for q in range(1, m + 1)]
-    wR = [ga + b - 1 + (r if q == m else 0) for q in range(2, m + 1)]
-    wL = [ga + b - 1 for q in range(1, m)]
-    wT = [ga + b - 1 for q in range(2, m)]  # maps exist for p = 2..m-1 (both kinds)
+    if widths is None:
+        m = P // b
+        widths = [b] * (m - 1) + [b + P - m * b]
+    m = len(widths)
+    alpha, beta, a = [], [], gamma
+    for p, x in enumerate(widths, start=1):
+        alpha.append(a)
+        beta.append(a + x - 1 if p < m else n + 1 - gamma)
+        a += x
+    m_lo = [1 if p == 0 else alpha[p] - ga + 1 for p in range(m)]
+    m_hi = [n if p == m - 1 else beta[p] + ga - 1 for p in range(m)]
+    wM = [m_hi[p] - m_lo[p] + 1 for p in range(m)]
+    wR = [m_hi[p] - alpha[p] + 1 for p in range(1, m)]
+    wL = [beta[p] - m_lo[p] + 1 for p in range(0, m - 1)]
+    wT = [m_hi[p] - alpha[p] + 1 for p in range(1, m - 1)]  # R maps; the L maps match for equal widths
     return m, wM, wR, wL, wT
 
 
-def tc_maps(n, gamma, b, precision="c64", gamma_a=None):
+def _map_widths(n, gamma, b, gamma_a=None, widths=None):
+    """Padded widths of every subproblem with a transfer map: H_p^R and H_p^L
+    for p = 2..m-1."""
+    m, wM, wR, wL, wT = _layer_widths(n, gamma, b, gamma_a, widths)
+    return wR[:m - 2] + wL[1:m - 1]
+
+
+def tc_maps(n, gamma, b, precision="c64", gamma_a=None, widths=None):
     """True when the library builds the transfer maps on the tensor cores
-    (complex64 factors, every map subproblem at most 32 columns wide)."""
-    m, wM, wR, wL, wT = _layer_widths(n, gamma, b, gamma_a)
-    return precision == "c64" and m >= 3 and max(wR + wL) <= 32
+    (complex64 factors, every sweep subproblem at most 32 columns wide)."""
+    m, wM, wR, wL, wT = _layer_widths(n, gamma, b, gamma_a, widths)
+    return precision in ("c64", "c64sym") and m >= 3 and max(wR + wL) <= 32
 
 
-def algorithmic(n, gamma, b, nrhs, esz, gamma_a=None, tc=False):
+def algorithmic(n, gamma, b, nrhs, esz, gamma_a=None, tc=False, widths=None):
     """Algorithmic bytes and flops per launch of each phase: a banded solve
     reads its L and U band once, n*w*(2w+1) entries, and does 8*(2w+1) real
     flops per entry row per right-hand side.  A transfer map T_p has n
@@ -171,7 +192,8 @@ def algorithmic(n, gamma, b, nrhs, esz, gamma_a=None, tc=False):
     upper and (by symmetry) the lower triangle: n(n-1) w^2 complex MACs per
     map, plus the diagonal-block recursion (tdiag), two w x w x w complex
     products per block."""
-    m, wM, wR, wL, wT = _layer_widths(n, gamma, b, gamma_a)
+    m, wM, wR, wL, _ = _layer_widths(n, gamma, b, gamma_a, widths)
+    wT = _map_widths(n, gamma, b, gamma_a, widths)  # 2(m-2) maps, R then L
     band = lambda ws: sum(n * w * (2 * w + 1) for w in ws)  # noqa: E731
     N = n * n
     vec = N * nrhs * esz
@@ -179,18 +201,36 @@ def algorithmic(n, gamma, b, nrhs, esz, gamma_a=None, tc=False):
     out["embed"] = {"bytes": band(wM) * esz + 2 * vec, "flops": 8.0 * nrhs * band(wM)}
     out["fill"] = {"bytes": (band(wR) + band(wL)) * esz + 2 * vec, "flops": 8.0 * nrhs * (band(wR) + band(wL))}
     if tc:
-        out["tmap"] = {"bytes": 2 * band(wT) * esz + 2 * len(wT) * n * n * esz + 2 * len(wT) * n * 2 * 32 * esz,
-                       "flops": 2 * 8.0 * n * (n - 1) * sum(w * w for w in wT)}
-        out["tdiag"] = {"bytes": 2 * band(wT) * esz + 2 * len(wT) * n * 2 * 32 * esz,
-                        "flops": 2 * 8.0 * 2 * (n - 1) * sum(w ** 3 for w in wT)}
+        out["tmap"] = {"bytes": band(wT) * esz + len(wT) * n * n * esz + len(wT) * n * 2 * 32 * esz,
+                       "flops": 8.0 * n * (n - 1) * sum(w * w for w in wT)}
+        out["tdiag"] = {"bytes": band(wT) * esz + len(wT) * n * 2 * 32 * esz,
+                        "flops": 8.0 * 2 * (n - 1) * sum(w ** 3 for w in wT)}
     else:
-        out["tmap"] = {"bytes": 2 * band(wT) * esz + 2 * len(wT) * n * n * esz,
-                       "flops": 2 * 8.0 * 1.5 * n * n * sum(w * w for w in wT)}
-    out["chain"] = {"bytes": 2 * len(wT) * n * n * esz, "flops": 8.0 * nrhs * 2 * len(wT) * n * n}
+        out["tmap"] = {"bytes": band(wT) * esz + len(wT) * n * n * esz,
+                       "flops": 8.0 * 1.5 * n * n * sum(w * w for w in wT)}
+    out["chain"] = {"bytes": len(wT) * n * n * esz, "flops": 8.0 * nrhs * len(wT) * n * n}
     out["factor"] = {"bytes": (band(wM) + band(wR) + band(wL)) * esz,
                      "flops": 8.0 * n * sum(w ** 3 for w in wM + wR + wL)}
     out["matvec"] = {"bytes": 2 * N * nrhs * 16 + N * 8, "flops": 8.0 * 5 * N * nrhs}
     return out
+
+
+def symmetric_band_bytes(n, gamma, b, esz, gamma_a=None, widths=None):
+    """Bytes of every subproblem's symmetric factorization (Section 3.1,
+    practical remark 4): L of LDL^T (w sub-diagonals) and D, n*w*(w+1) entries
+    per subproblem of padded width w."""
+    m, wM, wR, wL, _ = _layer_widths(n, gamma, b, gamma_a, widths)
+    return sum(n * w * (w + 1) for w in wM + wR + wL) * esz
+
+
+def stored_factor_bytes(n, gamma, b, esz, gamma_a=None, widths=None, packed=True):
+    """Bytes of the factor blocks this library stores: per subproblem n blocks,
+    each the packed upper triangle of the symmetric W_k Delta (w(w+1)/2
+    entries, padded to even) for complex64, else w x w_pad."""
+    m, wM, wR, wL, _ = _layer_widths(n, gamma, b, gamma_a, widths)
+    if packed:
+        return sum(n * ((w * (w + 1) // 2 + 1) // 2 * 2) for w in wM + wR + wL) * esz
+    return sum(n * w * (w + (w % 2)) for w in wM + wR + wL) * esz
 
 
 def _traffic_from_profile(kernel_phase):
@@ -241,7 +281,11 @@ def run_asp(args, rank, world):
     pml_aux = args.pml_aux if args.pml_aux else (P.pml_aux or 0)
     prm = asp.make_params(P.n, P.omega, P.pml, P.b, pml_aux=pml_aux, C=P.C, precision=args.precision,
                           max_rhs=P.nrhs, restart=restart, dim=P.dim)
-    h = asp.asp_setup(P.c, prm)
+    widths = None
+    if args.layer_widths:  # "BMIN:BMAX": widths chosen from the velocity by the library
+        bmin, bmax = (int(x) for x in args.layer_widths.split(":"))
+        widths = asp.layer_widths_from_velocity(prm, P.c, bmin, bmax)
+    h = asp.asp_setup(P.c, prm, widths=widths)
     f_host = torch.from_numpy(P.f).pin_memory()
     f = f_host.to(dev)
     u = torch.empty_like(f)
@@ -253,6 +297,11 @@ def run_asp(args, rank, world):
         return info
 
     for _ in range(args.warmup):
+        info = step()
+    tuned = None
+    if P.dim == 2 and not args.no_autotune:
+        # launch shapes of the layer solves, chosen by timing on these factors
+        tuned = {str(nr): h.autotune(nr) for nr in sorted({P.nrhs, 1})}
         info = step()
     if world > 1:
         torch.distributed.barrier()
@@ -387,8 +436,8 @@ def run_asp(args, rank, world):
                   {"workload": "3d_helmholtz_n47_one_slab_omega12pi_pml6_b37 (profiling case)"})
         metric = METRIC_3D
     else:
-        tcm = tc_maps(P.n, P.pml, P.b, args.precision, pml_aux)
-        alg = algorithmic(P.n, P.pml, P.b, P.nrhs, 8, pml_aux, tc=tcm)
+        tcm = tc_maps(P.n, P.pml, P.b, args.precision, pml_aux, widths)
+        alg = algorithmic(P.n, P.pml, P.b, P.nrhs, 8, pml_aux, tc=tcm, widths=widths)
         dom = max((p for p in PHASES if p in alg), key=lambda p: phases[p][0])
         tot_ms, nl = phases[dom]
         avg_ms = tot_ms / max(nl, 1)
@@ -426,14 +475,21 @@ def run_asp(args, rank, world):
         metric = METRIC
     if args.source == "packet":
         config = dict(config, sources="Gaussian wave packets, one wavelength wide, seeded centres and directions")
+    if widths is not None:
+        config = dict(config, layer_widths=f"from the velocity, {args.layer_widths.replace(':', '..')} columns",
+                      layers=len(widths), width_histogram={str(x): widths.count(x) for x in sorted(set(widths))})
     if args.pml_aux:
         config = dict(config, pml_aux=args.pml_aux,
                       variant="thinner auxiliary PML inside the domain (the boundary PML keeps its width)")
     precond_apply = None
     if apply_runs:
-        alg2 = algorithmic(P.n, P.pml, P.b, 1, 8, pml_aux, tc=tcm)
-        band_bytes = alg2["factor"]["bytes"]                   # every L and U band read once (complex64)
-        design_bytes = band_bytes + alg2["chain"]["bytes"]     # + the transfer maps the sweep chain reads
+        alg2 = algorithmic(P.n, P.pml, P.b, 1, 8, pml_aux, tc=tcm, widths=widths)
+        packed = args.precision == "c64sym" and P.dim == 2
+        lu_bytes = alg2["factor"]["bytes"]                     # nonsymmetric banded L and U, once (complex64)
+        sym_bytes = symmetric_band_bytes(P.n, P.pml, P.b, 8, pml_aux, widths)
+        band_bytes = sym_bytes if packed else lu_bytes
+        stored = stored_factor_bytes(P.n, P.pml, P.b, 8, pml_aux, widths, packed)
+        design_bytes = stored + alg2["chain"]["bytes"]         # what this design reads: its factors + the maps
         precond_apply = []
         for nr, a_ms, ph in apply_runs:
             vec = 3 * P.n * P.n * nr * 16                      # r in, z out, and the complex64 copy of r
@@ -442,10 +498,17 @@ def run_asp(args, rank, world):
                 "algorithmic_bytes": band_bytes + vec,
                 "GBps": (band_bytes + vec) / (a_ms * 1e-3) / 1e9,
                 "frac_of_measured_hbm": (band_bytes + vec) / (a_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                "nonsymmetric_band_bytes": lu_bytes + vec,
                 "design_bytes": design_bytes + vec,
                 "design_GBps": (design_bytes + vec) / (a_ms * 1e-3) / 1e9,
-                "note": "algorithmic bytes: the banded L and U factors of every layer subproblem, once, as the paper's "
-                        "apply reads them; design bytes add the transfer maps this implementation's sweep chain reads"})
+                "note": ("algorithmic bytes: every layer subproblem's symmetric factorization once (Section 3.1, "
+                         "practical remark 4: L of LDL^T and D, n*w*(w+1) entries per subproblem), the storage "
+                         "this build's complex64 path uses; nonsymmetric: the banded L and U, n*w*(2w+1); design "
+                         "bytes: the packed blocks this design reads plus the transfer maps of the sweep chain"
+                         if packed else
+                         "algorithmic bytes: the banded L and U factors of every layer subproblem, once, as the "
+                         "paper's apply reads them; design bytes add the transfer maps this implementation's sweep "
+                         "chain reads")})
     line = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -458,11 +521,12 @@ def run_asp(args, rank, world):
         "e2e": {"value": whole_job_rate(world, P.nrhs, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
+        "autotune": tuned,
         "roofline": roof,
         "precond_apply": precond_apply,
         "clocks": clk,
     }
-    if args.workload == "n1023" and args.precision == "c64" and not args.no_fp64_path:
+    if args.workload == "n1023" and args.precision in ("c64", "c64sym") and not args.no_fp64_path:
         # the plain FP64 path on the same problem and GPU: complex128 factors
         # and applies inside the same FP64 FGMRES, one warm-up and one timed
         # step; the mixed path's solutions are compared with its solutions
@@ -470,8 +534,10 @@ def run_asp(args, rank, world):
         h.destroy()
         prm128 = asp.make_params(P.n, P.omega, P.pml, P.b, pml_aux=pml_aux, C=P.C, precision="c128",
                                  max_rhs=P.nrhs, restart=restart, dim=P.dim)
-        h = asp.asp_setup(P.c, prm128)
+        h = asp.asp_setup(P.c, prm128, widths=widths)
         h.factor()
+        if not args.no_autotune:
+            h.autotune(P.nrhs)
         h.gmres_solve(f, u, tol=P.tol, maxit=200)
         torch.cuda.synchronize()
         q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -734,13 +800,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["asp", "reference"], default="asp")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", choices=["c64", "c128"], default="c64",
-                    help="layer factors and preconditioner applies in complex64 (mixed path, the headline) or "
-                         "complex128 (the plain FP64 path); FGMRES is FP64 either way")
+    ap.add_argument("--precision", choices=["c64", "c64sym", "c128"], default="c64",
+                    help="layer factors and preconditioner applies in complex64 (mixed path, the headline), "
+                         "complex64 with packed symmetric factors (half the factor memory), or complex128 (the "
+                         "plain FP64 path); FGMRES is FP64 either way")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes of the layer solves (no asp_autotune before timing)")
     ap.add_argument("--no-fp64-path", action="store_true",
                     help="skip the complex128 comparison step after the complex64 headline")
     ap.add_argument("--source", choices=["point", "packet"], default="point",
                     help="right-hand sides of the n=1023 workload: Gaussian point sources or wave packets")
+    ap.add_argument("--layer-widths", default="",
+                    help="BMIN:BMAX -- layer widths chosen from the velocity (at least BMIN columns, up to BMAX "
+                         "where it jumps heavily) instead of uniform layers of b columns")
     ap.add_argument("--pml-aux", type=int, default=0,
                     help="width of the auxiliary PMLs between layers (default: the boundary PML width)")
     ap.add_argument("--workload", choices=["n1023", "n511x32", "n255x32", "n255x1", "n95_3d", "n47_3d_slab"], default="n1023",

@@ -59,6 +59,12 @@ extern "C" {
 /* ---- precision of the layer factors and preconditioner applies ---------- */
 #define ASP_PREC_C128 0 /* complex128 factors and applies (plain FP64 path)      */
 #define ASP_PREC_C64 1  /* complex64 factors and applies inside FP64 FGMRES      */
+/* complex64 as ASP_PREC_C64, with every 2D layer factor block stored as the
+ * packed upper triangle of the complex-symmetric W_k Delta (Section 3.1,
+ * practical remark 4: the symmetric version saves memory): half the factor
+ * bytes, at the cost of expanding each block in shared memory during the
+ * layer solves (slower applies).  Not available in 3D (ASP_ERR_UNSUPPORTED). */
+#define ASP_PREC_C64_SYM 2
 
 /* Problem parameters (Section 2 and Section 3.1 notation).
  *   dim        spatial dimension (2 or 3)
@@ -73,7 +79,7 @@ extern "C" {
  *              P - m*b
  *   C          PML strength: sigma = (C/eta) (d/eta)^2 at distance d past the
  *              physical edge (Section 2); > 0
- *   factor_prec ASP_PREC_C128 or ASP_PREC_C64
+ *   factor_prec ASP_PREC_C128, ASP_PREC_C64 or ASP_PREC_C64_SYM
  *   max_rhs    largest nrhs that later calls will pass (1..256); sizes the
  *              apply and Krylov workspaces
  *   restart    FGMRES restart length the workspace is sized for (1..64)       */
@@ -113,11 +119,37 @@ typedef struct asp_solve_info {
  * returning. */
 int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle** out);
 
+/* asp_setup_layers: asp_setup with layers of arbitrary physical widths
+ * (Section 3.1, practical remark 3: the widths need not be equal and can be
+ * chosen larger where the velocity varies heavily).  widths (HOST, nwidths
+ * entries) are the numbers of physical columns (planes in 3D) of layers
+ * 1..m along the sweep axis, each >= 1, summing to n + 2 - 2*gamma; X_1 also
+ * holds the gamma - 1 boundary-PML columns before it and X_m those after it.
+ * p->b is not used for the partition.  widths = NULL gives asp_setup's
+ * partition.  Every other rule of asp_setup applies (2D padded widths
+ * 2*gamma_a + b_p - 2 <= 64, the auxiliary padding of the second and the
+ * second-to-last layer inside the grid: gamma_a <= gamma + min(b_1, b_m)). */
+int asp_setup_layers(const asp_params* p, const int* widths, int nwidths, const double* c, int c_is_device,
+                     asp_handle** out);
+
+/* Layer widths chosen from the velocity (Section 3.1, practical remark 3):
+ * layers of at least b_min physical columns, grown (up to b_max) while the
+ * next column boundary falls where the velocity jumps heavily along the sweep
+ * axis (relative jump above 4 times its median over the physical region, and
+ * above 1e-3), so that auxiliary PMLs are placed where the medium is smooth;
+ * the last layer takes the remainder.  c: HOST, n^dim doubles, natural
+ * ordering.  Writes at most `capacity` widths and returns their number m, or
+ * ASP_ERR_INVALID.  Host-only; no device work. */
+int asp_layer_widths_from_velocity(const asp_params* p, const double* c, int b_min, int b_max, int* widths,
+                                   int capacity);
+
 /* Bytes of device memory asp_setup + asp_factor will hold for these
  * parameters (factors, transfer maps, apply and Krylov workspaces).  Pure
  * function of `p` and the device's SM count (152 without a device); 0 for
  * invalid or unsupported parameters. */
 size_t asp_footprint_bytes(const asp_params* p);
+/* The same for asp_setup_layers' partition (widths = NULL: uniform). */
+size_t asp_footprint_bytes_layers(const asp_params* p, const int* widths, int nwidths);
 
 /* Number of layers m, and the partition of layer p (1-based): X_p = [x_lo, x_hi]
  * along the sweep axis (global 1-based indices).  Returns ASP_ERR_INVALID for a
@@ -174,6 +206,22 @@ int asp_subproblem_solve(asp_handle* h, int kind, int p, const void* g, void* v,
  * flags, and before returning. */
 int asp_gmres_solve(asp_handle* h, const void* f, void* u, int nrhs, double tol, int restart,
                     int maxit, asp_solve_info* info_host, void* stream);
+
+/* asp_autotune: choose the launch shapes of the layer solves of an apply
+ * with nrhs right-hand sides by timing them.  For the M-solves and for the
+ * sweep fills it times, on this handle's own factors, each candidate shape --
+ * right-hand sides per job (the tile's column capacity) and the compiled tile
+ * variant: the default capacity for nrhs, its alternative tile where one
+ * exists (complex64 at 32 and at 1 right-hand side), and the next smaller
+ * capacity -- one untimed and three timed launches each, and keeps the
+ * fastest for later applies with this nrhs.  The input contents are not used
+ * for the choice (the apply workspace is timed as it is).  choice_host (HOST,
+ * 4 ints, may be NULL): capacity and variant chosen for the M-solves, then for
+ * the fills.  ms_host (HOST, 6 doubles, may be NULL): mean milliseconds of each
+ * candidate (M-solves first, 0 where a candidate does not exist or does not
+ * fit the widths).  Requires asp_factor; 3D handles have nothing to tune
+ * (ASP_OK).  Synchronizes `stream`. */
+int asp_autotune(asp_handle* h, int nrhs, int* choice_host, double* ms_host, void* stream);
 
 /* Number of kernel launches this handle has issued since the last call (the
  * counter is reset by the call).  Used to report how many of the library's

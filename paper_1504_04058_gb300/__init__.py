@@ -19,7 +19,8 @@ from . import _lib
 from ._lib import (ASP_PREC_C64, ASP_PREC_C128, KIND_L, KIND_M, KIND_R, AspError,  # noqa: F401
                    asp_params, asp_solve_info)
 
-__all__ = ["asp_setup", "asp_footprint_bytes", "asp_residual_norms_noalloc", "asp_selftest_bounded_wait",
+__all__ = ["asp_setup", "asp_footprint_bytes", "layer_widths_from_velocity", "asp_residual_norms_noalloc",
+           "asp_selftest_bounded_wait",
            "AspHandle", "make_params",
            "AspError",
            "ASP_PREC_C64", "ASP_PREC_C128", "KIND_M", "KIND_R", "KIND_L"]
@@ -49,12 +50,38 @@ def _dev_vec(t, n: int, name: str, dim: int = 2):
 
 def make_params(n: int, omega: float, pml: int, b: int, pml_aux: int = 0, C: float = 20.0,
                 precision: str = "c128", max_rhs: int = 1, restart: int = 40, dim: int = 2) -> asp_params:
-    prec = {"c128": ASP_PREC_C128, "c64": ASP_PREC_C64}[precision]
+    prec = {"c128": ASP_PREC_C128, "c64": ASP_PREC_C64, "c64sym": _lib.ASP_PREC_C64_SYM}[precision]
     return asp_params(dim, n, float(omega), pml, pml_aux, b, float(C), prec, max_rhs, restart)
 
 
-def asp_footprint_bytes(params: asp_params) -> int:
-    return int(_lib.load().asp_footprint_bytes(ctypes.byref(params)))
+def _widths_arg(widths):
+    if widths is None:
+        return None, 0, None
+    w = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+    return w.ctypes.data_as(ctypes.c_void_p), int(w.size), w
+
+
+def asp_footprint_bytes(params: asp_params, widths=None) -> int:
+    """Device bytes of a handle; ``widths``: physical layer widths (None: uniform b)."""
+    ptr, m, _keep = _widths_arg(widths)
+    return int(_lib.load().asp_footprint_bytes_layers(ctypes.byref(params), ptr, m))
+
+
+def layer_widths_from_velocity(params: asp_params, c, b_min: int, b_max: int) -> list:
+    """Layer widths chosen from the velocity (host computation in the library):
+    at least b_min columns, grown up to b_max where the velocity jumps heavily
+    along the sweep axis.  ``c``: the float64 velocity as a numpy array."""
+    arr = np.ascontiguousarray(np.asarray(c, dtype=np.float64))
+    if arr.size != params.n ** params.dim:
+        raise ValueError("velocity has the wrong number of nodes")
+    cap = params.n + 2
+    out = np.zeros(cap, dtype=np.int32)
+    m = _lib.load().asp_layer_widths_from_velocity(ctypes.byref(params), arr.ctypes.data_as(ctypes.c_void_p),
+                                                   int(b_min), int(b_max), out.ctypes.data_as(ctypes.c_void_p),
+                                                   cap)
+    if m < 0:
+        _lib.check(m, "asp_layer_widths_from_velocity")
+    return [int(x) for x in out[:m]]
 
 
 class AspHandle:
@@ -98,6 +125,18 @@ class AspHandle:
         return {name: (ms[i], int(cnt[i])) for i, name in enumerate(_lib.PHASES)}
 
     # -------------------------------------------------------------- compute
+    def autotune(self, nrhs: int, stream=None) -> dict:
+        """Time the candidate launch shapes of the layer solves for ``nrhs``
+        right-hand sides on this handle's factors and keep the fastest
+        (asp_autotune).  Returns the choices and the candidates' times."""
+        choice = np.zeros(4, dtype=np.int32)
+        ms = np.zeros(6, dtype=np.float64)
+        _lib.check(_lib.load().asp_autotune(self._ptr, int(nrhs), choice.ctypes.data_as(ctypes.c_void_p),
+                                            ms.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(_stream_ptr(stream))),
+                   "asp_autotune")
+        return {"embed": {"cap": int(choice[0]), "variant": int(choice[1]), "candidate_ms": [float(x) for x in ms[:3]]},
+                "fill": {"cap": int(choice[2]), "variant": int(choice[3]), "candidate_ms": [float(x) for x in ms[3:]]}}
+
     def factor(self, stream=None) -> None:
         _lib.check(_lib.load().asp_factor(self._ptr, ctypes.c_void_p(_stream_ptr(stream))), "asp_factor")
 
@@ -202,19 +241,23 @@ def asp_selftest_bounded_wait(polls: int = 4096, stream=None) -> int:
     return int(_lib.load().asp_selftest_bounded_wait(int(polls), ctypes.c_void_p(_stream_ptr(stream))))
 
 
-def asp_setup(c, params: asp_params) -> AspHandle:
-    """Set up a handle for velocity ``c`` (n x n float64, numpy or CUDA tensor)."""
+def asp_setup(c, params: asp_params, widths=None) -> AspHandle:
+    """Set up a handle for velocity ``c`` (n x n float64, numpy or CUDA tensor);
+    ``widths``: physical layer widths summing to n + 2 - 2*pml (None: uniform
+    layers of params.b columns, the last taking the remainder)."""
     lib = _lib.load()
     out = ctypes.c_void_p()
+    wptr, m, _keep = _widths_arg(widths)
     if isinstance(c, np.ndarray):
         arr = np.ascontiguousarray(c, dtype=np.float64)
         if arr.size != params.n ** params.dim:
             raise ValueError("velocity has the wrong number of nodes")
-        code = lib.asp_setup(ctypes.byref(params), arr.ctypes.data_as(ctypes.c_void_p), 0, ctypes.byref(out))
+        code = lib.asp_setup_layers(ctypes.byref(params), wptr, m, arr.ctypes.data_as(ctypes.c_void_p), 0,
+                                    ctypes.byref(out))
     else:
         torch = _torch()
         t = c.contiguous().to(torch.float64)
-        code = lib.asp_setup(ctypes.byref(params), ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0,
-                             ctypes.byref(out))
+        code = lib.asp_setup_layers(ctypes.byref(params), wptr, m, ctypes.c_void_p(t.data_ptr()),
+                                    1 if t.is_cuda else 0, ctypes.byref(out))
     _lib.check(code, "asp_setup")
     return AspHandle(out.value, params)

@@ -24,6 +24,7 @@ ASP_ERR_UNSUPPORTED = -8
 
 ASP_PREC_C128 = 0
 ASP_PREC_C64 = 1
+ASP_PREC_C64_SYM = 2
 
 KIND_M, KIND_R, KIND_L = 0, 1, 2
 
@@ -33,7 +34,8 @@ EXPORTS = [
     "asp_apply_preconditioner", "asp_matvec", "asp_subproblem_width", "asp_subproblem_solve",
     "asp_gmres_solve", "asp_take_launch_count", "asp_set_phase_timing", "asp_phase_times",
     "asp_destroy", "asp_error_string", "asp_last_error_detail", "asp_residual_norms_noalloc",
-    "asp_selftest_bounded_wait",
+    "asp_selftest_bounded_wait", "asp_setup_layers", "asp_footprint_bytes_layers", "asp_layer_widths_from_velocity",
+    "asp_autotune",
 ]
 NOALLOC_MAX_N = 4096
 NOALLOC_MAX_RHS = 64
@@ -86,6 +88,9 @@ def load() -> ctypes.CDLL:
     sig = {
         "asp_setup": (I, [ctypes.POINTER(asp_params), P, I, ctypes.POINTER(P)]),
         "asp_footprint_bytes": (ctypes.c_size_t, [ctypes.POINTER(asp_params)]),
+        "asp_setup_layers": (I, [ctypes.POINTER(asp_params), P, I, P, I, ctypes.POINTER(P)]),
+        "asp_footprint_bytes_layers": (ctypes.c_size_t, [ctypes.POINTER(asp_params), P, I]),
+        "asp_layer_widths_from_velocity": (I, [ctypes.POINTER(asp_params), P, I, I, P, I]),
         "asp_num_layers": (I, [P]),
         "asp_layer_range": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "asp_factor": (I, [P, P]),
@@ -95,6 +100,7 @@ def load() -> ctypes.CDLL:
         "asp_subproblem_solve": (I, [P, I, I, P, P, I, P]),
         "asp_gmres_solve": (I, [P, P, P, I, D, I, I, ctypes.POINTER(asp_solve_info), P]),
         "asp_take_launch_count": (ctypes.c_longlong, [P]),
+        "asp_autotune": (I, [P, I, P, P, P]),
         "asp_set_phase_timing": (I, [P, I]),
         "asp_phase_times": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), I]),
         "asp_destroy": (V, [P]),

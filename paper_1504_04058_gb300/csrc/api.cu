@@ -131,7 +131,31 @@ struct Sizes {
   size_t bytes = 0;
 };
 
-bool valid(const asp_params* p, std::string* why) {
+// Physical layer widths b_1..b_m (Section 3.1, practical remark 3: arbitrary
+// widths).  With widths == nullptr: floor(P/b) layers of b columns, the last
+// one absorbing the remainder, P = n + 2 - 2*gamma.  Empty on invalid input.
+std::vector<int> layer_widths(const asp_params* p, const int* widths, int m, std::string* why) {
+  std::vector<int> w;
+  const int P = p->n + 2 - 2 * p->pml;
+  if (!widths) {
+    const int mm = p->b >= 1 ? P / p->b : 0;
+    if (mm < 1) { *why = "n too small for the PML width and layer width (need n >= 2*gamma + b - 2)"; return w; }
+    w.assign(mm, p->b);
+    w[mm - 1] += P - mm * p->b;
+    return w;
+  }
+  if (m < 1 || m > P) { *why = "number of layers out of range [1, n + 2 - 2*gamma]"; return w; }
+  long long sum = 0;
+  for (int i = 0; i < m; ++i) {
+    if (widths[i] < 1) { *why = "every layer width must be >= 1"; return w; }
+    sum += widths[i];
+  }
+  if (sum != P) { *why = "layer widths must sum to n + 2 - 2*gamma = " + std::to_string(P); return w; }
+  w.assign(widths, widths + m);
+  return w;
+}
+
+bool valid(const asp_params* p, std::string* why, const std::vector<int>* widths = nullptr) {
   if (!p) { *why = "null params"; return false; }
   if (p->dim != 2 && p->dim != 3) { *why = "dim must be 2 or 3"; return false; }
   if (p->dim == 2 && (p->n < 3 || p->n > 16383)) { *why = "n out of range [3, 16383]"; return false; }
@@ -141,14 +165,28 @@ bool valid(const asp_params* p, std::string* why) {
   if (p->pml_aux < 0) { *why = "pml_aux must be >= 0"; return false; }
   if (p->b < 1) { *why = "b must be >= 1"; return false; }
   if (!(p->C > 0) || !isfinite(p->C)) { *why = "C must be positive and finite"; return false; }
-  if (p->factor_prec != ASP_PREC_C128 && p->factor_prec != ASP_PREC_C64) { *why = "bad factor_prec"; return false; }
+  if (p->factor_prec != ASP_PREC_C128 && p->factor_prec != ASP_PREC_C64 && p->factor_prec != ASP_PREC_C64_SYM) {
+    *why = "bad factor_prec";
+    return false;
+  }
   if (p->max_rhs < 1 || p->max_rhs > 256) { *why = "max_rhs out of range [1, 256]"; return false; }
   if (p->restart < 1 || p->restart > 64) { *why = "restart out of range [1, 64]"; return false; }
   const int P = p->n + 2 - 2 * p->pml;
-  if (P < p->b) { *why = "n too small for the PML width and layer width (need n >= 2*gamma + b - 2)"; return false; }
+  if (!widths && P < p->b) { *why = "n too small for the PML width and layer width (need n >= 2*gamma + b - 2)"; return false; }
   const int ga = p->pml_aux ? p->pml_aux : p->pml;
-  if (ga > p->pml + p->b) { *why = "pml_aux too wide for the layer width"; return false; }
+  // the auxiliary padding of X_2^M and X_{m-1}^M must stay inside [1, n]
+  const int bmin = widths ? std::min(widths->front(), widths->back()) : p->b;
+  if (ga > p->pml + bmin) { *why = "pml_aux too wide for the layer width"; return false; }
   return true;
+}
+
+// ASP_PREC_C64_SYM is complex64 arithmetic with packed symmetric factor
+// storage: the rest of the library sees ASP_PREC_C64 and the `packed` flag.
+asp_params normalized(const asp_params* p, bool* packed) {
+  asp_params q = *p;
+  *packed = q.factor_prec == ASP_PREC_C64_SYM;
+  if (*packed) q.factor_prec = ASP_PREC_C64;
+  return q;
 }
 
 struct Part {
@@ -156,15 +194,18 @@ struct Part {
   std::vector<int> x_lo, x_hi, alpha, beta, m_lo, m_hi;
 };
 
-Part partition(int n, int gamma, int ga, int b) {
+// Layers of the given physical widths: alpha_p = gamma + b_1 + ... + b_{p-1},
+// beta_p = alpha_p + b_p - 1 (beta_m = n + 1 - gamma when the widths sum to P).
+Part partition(int n, int gamma, int ga, const std::vector<int>& widths) {
   Part P;
-  const int phys = n + 2 - 2 * gamma;
-  P.m = phys / b;
+  P.m = (int)widths.size();
   const int m = P.m;
   P.x_lo.assign(m + 1, 0); P.x_hi = P.x_lo; P.alpha = P.x_lo; P.beta = P.x_lo; P.m_lo = P.x_lo; P.m_hi = P.x_lo;
+  int a = gamma;
   for (int p = 1; p <= m; ++p) {
-    P.alpha[p] = gamma + (p - 1) * b;
-    P.beta[p] = (p < m) ? gamma + p * b - 1 : n + 1 - gamma;
+    P.alpha[p] = a;
+    P.beta[p] = (p < m) ? a + widths[p - 1] - 1 : n + 1 - gamma;
+    a = P.beta[p] + 1;
     P.x_lo[p] = (p == 1) ? 1 : P.alpha[p];
     P.x_hi[p] = (p == m) ? n : P.beta[p];
     P.m_lo[p] = (p == 1) ? 1 : P.alpha[p] - ga + 1;
@@ -183,9 +224,7 @@ constexpr int kDefaultSms = 152;
 // padded layers wider than 64 columns, 2D grids with more than
 // kChainMaxRows * (sms / 2) points per side (sweep chain with three or more
 // layers), 3D blocks larger than kMaxNb3.
-bool supported(const asp_params* p, std::string* why, int sms) {
-  const int ga = p->pml_aux ? p->pml_aux : p->pml;
-  Part P = partition(p->n, p->pml, ga, p->b);
+bool supported(const asp_params* p, const Part& P, std::string* why, int sms) {
   int wmax = 0;
   for (int q = 1; q <= P.m; ++q) wmax = std::max(wmax, P.m_hi[q] - P.m_lo[q] + 1);
   if (p->dim == 2 && wmax > 64) {
@@ -220,10 +259,9 @@ int zslot_cols(int dim, int prec, int m, int wmaxRL) {
   return 16;
 }
 
-Sizes sizes_for3(const asp_params* p, int num_sms) {
+Sizes sizes_for3(const asp_params* p, const Part& P, int num_sms) {
   Sizes Z;
-  const int n = p->n, gamma = p->pml, ga = p->pml_aux ? p->pml_aux : p->pml, b = p->b;
-  Part P = partition(n, gamma, ga, b);
+  const int n = p->n;
   Z.m = P.m;
   Z.esz = p->factor_prec == ASP_PREC_C128 ? 16 : 8;
   Z.N = (long long)n * n * n;
@@ -253,7 +291,8 @@ Sizes sizes_for3(const asp_params* p, int num_sms) {
   const size_t rsz = Z.esz / 2;  // real type of the factor precision
   size_t bytes = 0;
   bytes += Z.N * (sizeof(double) + rsz) + 3 * (size_t)n * (sizeof(double2) + Z.esz);  // k2, ca, cc, cd (both)
-  bytes += Z.coef * (sizeof(SweepCoef) + 3 * Z.esz) + Z.nsub * sizeof(Slab) + Z.nsub * sizeof(int);
+  bytes += Z.coef * (sizeof(SweepCoef) + 5 * Z.esz) + Z.nsub * sizeof(Slab) + Z.nsub * sizeof(int);
+  bytes += (size_t)n * 2 * Z.esz;  // s1, 1/s1
   bytes += (Z.W_elems + Z.A_elems + Z.z3_elems) * Z.esz + Z.piv_elems * sizeof(int);
   bytes += Z.tc_floats * sizeof(float);
   bytes += (size_t)Z.N * mr * Z.esz * (3 + (Z.esz == 8 ? 1 : 0));                 // uM uR uL (+ r_lo)
@@ -264,18 +303,19 @@ Sizes sizes_for3(const asp_params* p, int num_sms) {
   return Z;
 }
 
-Sizes sizes_for(const asp_params* p, int num_sms) {
-  if (p->dim == 3) return sizes_for3(p, num_sms);
+// p->factor_prec is ASP_PREC_C128 or ASP_PREC_C64 here (see normalized());
+// packed: complex64 blocks stored as packed symmetric triangles.
+Sizes sizes_for(const asp_params* p, const Part& P, int num_sms, bool packed) {
+  if (p->dim == 3) return sizes_for3(p, P, num_sms);
   Sizes Z;
-  const int n = p->n, gamma = p->pml, ga = p->pml_aux ? p->pml_aux : p->pml, b = p->b;
-  Part P = partition(n, gamma, ga, b);
+  const int n = p->n;
   Z.m = P.m;
   Z.esz = p->factor_prec == ASP_PREC_C128 ? 16 : 8;
   Z.N = (long long)n * n;
   auto addsub = [&](int lo, int hi, bool rl) {
     const int w = hi - lo + 1;
     const int wp = (p->factor_prec == ASP_PREC_C64) ? ((w + 1) & ~1) : w;
-    Z.W_elems += (size_t)n * w * wp;
+    Z.W_elems += (size_t)n * (packed ? packed_block_elems(w) : w * wp);
     Z.coef += w;
     Z.wmax = std::max(Z.wmax, w);
     if (rl) Z.wmaxRL = std::max(Z.wmaxRL, w);
@@ -298,7 +338,7 @@ Sizes sizes_for(const asp_params* p, int num_sms) {
   bytes += Z.coef * sizeof(SweepCoef) + Z.nsub * sizeof(SubDesc);
   bytes += Z.W_elems * Z.esz + Z.tmap_elems * Z.esz;
   if (tcm) bytes += (size_t)2 * (P.m - 2) * (n * 2 * 32 * sizeof(float2) + sizeof(TmMap));  // Gamma columns, map table
-  bytes += (size_t)n * 2 * sizeof(float2);                                        // s1, 1/s1
+  bytes += (size_t)n * 2 * sizeof(float2) + Z.coef * 2 * Z.esz;                    // s1, 1/s1, s2, 1/s2
   bytes += (size_t)Z.N * mr * Z.esz * (3 + (Z.esz == 8 ? 1 : 0));              // uM uR uL (+ r_lo)
   bytes += (size_t)2 * (P.m + 1) * n * ((mr + 1) & ~1) * Z.esz;                   // accR, accL
   bytes += (size_t)Z.zslots * Z.zslot * Z.esz;                                   // forward scratch
@@ -374,11 +414,18 @@ namespace {
 
 struct JobList {
   Job* d = nullptr;
-  int n = 0, cap = 0, wmax = 0;
+  int n = 0, cap = 0, wmax = 0, variant = 0;
+};
+
+// A layer-solve launch shape: right-hand sides per job (the tile's column
+// capacity) and the instance variant of launch_btsolve_apply.
+struct Shape {
+  int cap = 0, variant = 0;
 };
 
 struct JobCache {
   std::map<int, JobList> embed, fill;
+  std::map<int, Shape> tuned_embed, tuned_fill;  // asp_autotune's choices per nrhs
   std::map<long long, JobList> sub;  // key: subproblem index * 1024 + nrhs
   JobList tmap;
   bool have_tmap = false;
@@ -403,10 +450,11 @@ JobCache& cache_of(const Handle* h) {
   return caches()[h];
 }
 
-int upload_jobs(Handle& H, const std::vector<Job>& jobs, int cap, int wmax, JobList* out) {
+int upload_jobs(Handle& H, const std::vector<Job>& jobs, int cap, int wmax, JobList* out, int variant = 0) {
   out->n = (int)jobs.size();
   out->cap = cap;
   out->wmax = wmax;
+  out->variant = variant;
   if (jobs.empty()) return ASP_OK;
   void* d = nullptr;
   if (cudaMalloc(&d, jobs.size() * sizeof(Job)) != cudaSuccess) return fail(ASP_ERR_OOM, "job list allocation");
@@ -419,18 +467,48 @@ int upload_jobs(Handle& H, const std::vector<Job>& jobs, int cap, int wmax, JobL
   return ASP_OK;
 }
 
+int embed_wmax(const Handle& H) {
+  int wm = 0;
+  for (int q = 1; q <= H.m; ++q) wm = std::max(wm, H.subs[H.subM[q]].w);
+  return wm;
+}
+
+int build_embed_jobs(Handle& H, int nrhs, Shape sh, JobList* L) {
+  std::vector<Job> jobs;
+  for (int q = 1; q <= H.m; ++q)
+    for (int r0 = 0; r0 < nrhs; r0 += sh.cap) jobs.push_back({H.subM[q], MODE_EMBED, r0, std::min(sh.cap, nrhs - r0)});
+  return upload_jobs(H, jobs, sh.cap, embed_wmax(H), L, sh.variant);
+}
+
+int build_fill_jobs(Handle& H, int nrhs, Shape sh, JobList* L) {
+  std::vector<Job> jobs;
+  for (int p = 1; p <= H.m; ++p) {
+    for (int r0 = 0; r0 < nrhs; r0 += sh.cap) {
+      if (p >= 2) jobs.push_back({H.subR[p], MODE_FILL_R, r0, std::min(sh.cap, nrhs - r0)});
+      if (p <= H.m - 1) jobs.push_back({H.subL[p], MODE_FILL_L, r0, std::min(sh.cap, nrhs - r0)});
+    }
+  }
+  return upload_jobs(H, jobs, sh.cap, std::max(1, H.wmaxRL), L, sh.variant);
+}
+
+// The launch shape of the M-solves / fills for nrhs right-hand sides: the
+// autotuner's choice if asp_autotune ran for this nrhs, else the default
+// capacity for the count.
+Shape shape_for(Handle& H, JobCache& c, int cls, int nrhs) {
+  const auto& tuned = cls == CLS_EMBED ? c.tuned_embed : c.tuned_fill;
+  auto it = tuned.find(nrhs);
+  if (it != tuned.end()) return it->second;
+  Shape sh;
+  sh.cap = btsolve_rhs_capacity(nrhs, cls == CLS_EMBED ? embed_wmax(H) : std::max(1, H.wmaxRL), H.prec, false);
+  return sh;
+}
+
 int get_embed_jobs(Handle& H, int nrhs, JobList** out) {
   JobCache& c = cache_of(&H);
   auto it = c.embed.find(nrhs);
   if (it == c.embed.end()) {
-    int wm = 0;
-    for (int q = 1; q <= H.m; ++q) wm = std::max(wm, H.subs[H.subM[q]].w);
-    const int cap = btsolve_rhs_capacity(nrhs, wm, H.prec, false);
-    std::vector<Job> jobs;
-    for (int q = 1; q <= H.m; ++q)
-      for (int r0 = 0; r0 < nrhs; r0 += cap) jobs.push_back({H.subM[q], MODE_EMBED, r0, std::min(cap, nrhs - r0)});
     JobList L;
-    int rc = upload_jobs(H, jobs, cap, wm, &L);
+    int rc = build_embed_jobs(H, nrhs, shape_for(H, c, CLS_EMBED, nrhs), &L);
     if (rc != ASP_OK) return rc;
     it = c.embed.emplace(nrhs, L).first;
   }
@@ -442,17 +520,8 @@ int get_fill_jobs(Handle& H, int nrhs, JobList** out) {
   JobCache& c = cache_of(&H);
   auto it = c.fill.find(nrhs);
   if (it == c.fill.end()) {
-    const int wm = std::max(1, H.wmaxRL);
-    const int cap = btsolve_rhs_capacity(nrhs, wm, H.prec, false);
-    std::vector<Job> jobs;
-    for (int p = 1; p <= H.m; ++p) {
-      for (int r0 = 0; r0 < nrhs; r0 += cap) {
-        if (p >= 2) jobs.push_back({H.subR[p], MODE_FILL_R, r0, std::min(cap, nrhs - r0)});
-        if (p <= H.m - 1) jobs.push_back({H.subL[p], MODE_FILL_L, r0, std::min(cap, nrhs - r0)});
-      }
-    }
     JobList L;
-    int rc = upload_jobs(H, jobs, cap, wm, &L);
+    int rc = build_fill_jobs(H, nrhs, shape_for(H, c, CLS_FILL, nrhs), &L);
     if (rc != ASP_OK) return rc;
     it = c.fill.emplace(nrhs, L).first;
   }
@@ -471,6 +540,7 @@ SolveParams base_params(Handle& H, int ldv) {
   P.W = H.W;
   P.ca = H.prec == ASP_PREC_C64 ? (const void*)H.fc32.ca : (const void*)H.fc64.ca;
   P.cc = H.prec == ASP_PREC_C64 ? (const void*)H.fc32.cc : (const void*)H.fc64.cc;
+  P.s2inv = H.prec == ASP_PREC_C64 ? (const void*)H.fc32.s2inv : (const void*)H.fc64.s2inv;
   P.outM = H.uM;
   P.outR = H.uR;
   P.outL = H.uL;
@@ -539,7 +609,7 @@ int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_
   P.jobs = je->d;
   P.njobs = je->n;
   PhaseTok tk = phase_begin(H, PH_EMBED, s);
-  cudaError_t ce = launch_btsolve_apply(H, P, CLS_EMBED, je->cap, je->wmax, s);
+  cudaError_t ce = launch_btsolve_apply(H, P, CLS_EMBED, je->cap, je->variant, je->wmax, s);
   phase_end(H, tk, s);
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("M-solve launch: ") + cudaGetErrorString(ce));
   // 2. accumulated traces of both sweeps (Algorithm 2, second and third loops)
@@ -560,7 +630,7 @@ int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_
   P.jobs = jf->d;
   P.njobs = jf->n;
   tk = phase_begin(H, PH_FILL, s);
-  ce = launch_btsolve_apply(H, P, CLS_FILL, jf->cap, jf->wmax, s);
+  ce = launch_btsolve_apply(H, P, CLS_FILL, jf->cap, jf->variant, jf->wmax, s);
   phase_end(H, tk, s);
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("fill launch: ") + cudaGetErrorString(ce));
   // 4. u~_p = u~_{p,1:p-1} + u~_{p,p} + u~_{p,p+1:m}
@@ -572,11 +642,99 @@ int apply_precond(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_
   return ASP_OK;
 }
 
+// Candidate launch shapes of the M-solves (cls CLS_EMBED) or fills for nrhs
+// right-hand sides: the default capacity, its variant where one is compiled
+// (complex64 at 32 and 1 right-hand sides), and the next smaller capacity
+// (more, narrower jobs).  At most kTuneCands.
+constexpr int kTuneCands = 3;
+std::vector<Shape> tune_candidates(const Handle& H, int nrhs, int wmax) {
+  std::vector<Shape> c;
+  const int def = btsolve_rhs_capacity(nrhs, wmax, H.prec, false);
+  c.push_back({def, 0});
+  if (H.prec == ASP_PREC_C64 && (def == 32 || def == 1)) c.push_back({def, 1});
+  static const int caps[] = {32, 16, 8, 4, 2, 1};
+  for (int cp : caps)
+    if (cp < def) {
+      c.push_back({cp, 0});
+      break;
+    }
+  return c;
+}
+
+int autotune(Handle& H, int nrhs, int* choice, double* ms_out, cudaStream_t s) {
+  if (!H.factored) return fail(ASP_ERR_STATE, "autotune before factor");
+  if (ms_out)
+    for (int i = 0; i < 2 * kTuneCands; ++i) ms_out[i] = 0.0;
+  if (H.dim != 2) return ASP_OK;  // the 3D slab solves have one launch shape
+  JobCache& c = cache_of(&H);
+  SolveParams P = base_params(H, nrhs);
+  P.in = H.prec == ASP_PREC_C64 ? (const void*)H.r_lo : (const void*)H.wv;  // contents do not matter for timing
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(ASP_ERR_CUDA, "autotune: event creation");
+  }
+  int rc = ASP_OK;
+  for (int k = 0; k < 2 && rc == ASP_OK; ++k) {
+    const int cls = k == 0 ? CLS_EMBED : CLS_FILL;
+    const int wm = cls == CLS_EMBED ? embed_wmax(H) : std::max(1, H.wmaxRL);
+    const std::vector<Shape> cands = tune_candidates(H, nrhs, wm);
+    Shape best = cands[0];
+    double best_ms = 1e300;
+    for (size_t i = 0; i < cands.size() && rc == ASP_OK; ++i) {
+      JobList L;
+      rc = cls == CLS_EMBED ? build_embed_jobs(H, nrhs, cands[i], &L) : build_fill_jobs(H, nrhs, cands[i], &L);
+      if (rc != ASP_OK) break;
+      P.jobs = L.d;
+      P.njobs = L.n;
+      // one untimed launch, then three timed ones on the handle's own factors
+      cudaError_t ce = launch_btsolve_apply(H, P, cls, L.cap, L.variant, L.wmax, s);
+      if (ce != cudaSuccess) {  // a shape this width does not fit: not a candidate
+        cudaGetLastError();
+        continue;
+      }
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep) ce = launch_btsolve_apply(H, P, cls, L.cap, L.variant, L.wmax, s);
+      cudaEventRecord(e1, s);
+      float t = 0.f;
+      if (ce != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+        rc = fail(ASP_ERR_CUDA, "autotune: timed launches");
+        break;
+      }
+      H.launches += 4;
+      const double ms = t / 3.0;
+      if (ms_out) ms_out[k * kTuneCands + i] = ms;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cands[i];
+      }
+    }
+    if (rc != ASP_OK) break;
+    (cls == CLS_EMBED ? c.tuned_embed : c.tuned_fill)[nrhs] = best;
+    (cls == CLS_EMBED ? c.embed : c.fill).erase(nrhs);  // the next apply builds its jobs with the choice
+    if (choice) {
+      choice[2 * k] = best.cap;
+      choice[2 * k + 1] = best.variant;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == ASP_OK) rc = check_err(H, s, "autotune");
+  return rc;
+}
+
 }  // namespace asp
 
 using namespace asp;
 
 extern "C" {
+
+int asp_autotune(asp_handle* hd, int nrhs, int* choice_host, double* ms_host, void* stream) {
+  if (!hd) return fail(ASP_ERR_INVALID, "null handle");
+  Handle& H = hd->h;
+  if (nrhs < 1 || nrhs > H.prm.max_rhs) return fail(ASP_ERR_INVALID, "nrhs out of range");
+  return autotune(H, nrhs, choice_host, ms_host, (cudaStream_t)stream);
+}
 
 const char* asp_error_string(int code) {
   switch (code) {
@@ -595,12 +753,77 @@ const char* asp_error_string(int code) {
 
 const char* asp_last_error_detail(void) { return g_detail.c_str(); }
 
-size_t asp_footprint_bytes(const asp_params* p) {
+size_t asp_footprint_bytes_layers(const asp_params* pin, const int* widths, int m) {
   std::string why;
+  if (!pin) return 0;
+  if (!valid(pin, &why)) return 0;
+  bool packed = false;
+  const asp_params q = normalized(pin, &packed);
+  const asp_params* p = &q;
+  if (packed && p->dim != 2) return 0;
   int sms = device_sms();
   if (sms <= 0) sms = kDefaultSms;
-  if (!valid(p, &why) || !supported(p, &why, sms)) return 0;
-  return sizes_for(p, sms).bytes;
+  const std::vector<int> w = layer_widths(p, widths, m, &why);
+  if (w.empty() || !valid(p, &why, &w)) return 0;
+  const Part P = partition(p->n, p->pml, p->pml_aux ? p->pml_aux : p->pml, w);
+  if (!supported(p, P, &why, sms)) return 0;
+  return sizes_for(p, P, sms, packed).bytes;
+}
+
+size_t asp_footprint_bytes(const asp_params* p) { return asp_footprint_bytes_layers(p, nullptr, 0); }
+
+int asp_layer_widths_from_velocity(const asp_params* p, const double* c, int b_min, int b_max, int* widths,
+                                   int capacity) {
+  if (!p || !c || !widths) return fail(ASP_ERR_INVALID, "null argument");
+  if ((p->dim != 2 && p->dim != 3) || p->n < 3 || p->pml < 2) return fail(ASP_ERR_INVALID, "bad dim, n or pml");
+  const int n = p->n, gamma = p->pml, ga = p->pml_aux ? p->pml_aux : p->pml;
+  const int P = n + 2 - 2 * gamma;
+  // a padded M-layer is 2*gamma_a + b - 2 columns wide and the 2D kernels take 64
+  const int b_cap = p->dim == 2 ? 66 - 2 * ga : P;
+  if (b_min < 1 || b_max < b_min || b_min > b_cap || P < b_min)
+    return fail(ASP_ERR_INVALID, "need 1 <= b_min <= b_max, b_min <= n + 2 - 2*gamma and a padded width <= 64");
+  b_max = std::min(b_max, b_cap);
+  const long long T = p->dim == 3 ? (long long)n * n : n;  // transverse points per sweep column
+  // relative velocity jump between sweep columns j and j+1 (1-based j), worst over the column
+  std::vector<double> v(n + 2, 0.0);
+  for (int j = 1; j < n; ++j) {
+    double worst = 0.0;
+    const double* a = c + (long long)(j - 1) * T;
+    const double* b = c + (long long)j * T;
+    for (long long t = 0; t < T; ++t) {
+      if (!(a[t] > 0) || !(b[t] > 0) || !isfinite(a[t]) || !isfinite(b[t]))
+        return fail(ASP_ERR_INVALID, "velocity must be positive and finite");
+      worst = std::max(worst, fabs(b[t] - a[t]) / std::min(a[t], b[t]));
+    }
+    v[j] = worst;
+  }
+  // "heavy" variation: well above the typical jump inside the physical region
+  std::vector<double> vs(v.begin() + gamma, v.begin() + (n + 1 - gamma));
+  double tau = 1e-3;
+  if (!vs.empty()) {
+    std::nth_element(vs.begin(), vs.begin() + vs.size() / 2, vs.end());
+    tau = std::max(tau, 4.0 * vs[vs.size() / 2]);
+  }
+  // left to right: at least b_min columns; a layer does not end between two
+  // columns with a heavy jump unless it has reached b_max; the last layer
+  // takes what is left when that is less than b_min more
+  std::vector<int> w;
+  int a = gamma;  // first physical column of the next layer
+  const int last = n + 1 - gamma;
+  while (a <= last) {
+    int e = a + b_min - 1;  // last column of this layer
+    while (e < last && e - a + 1 < b_max && v[e] > tau) ++e;
+    if (last - e < b_min) {
+      if (last - a + 1 <= b_cap) e = last;               // absorb the remainder
+      else e = std::min(e, last - b_min);                 // keep the padded width in range
+    }
+    e = std::min(e, last);
+    w.push_back(e - a + 1);
+    a = e + 1;
+  }
+  if ((int)w.size() > capacity) return fail(ASP_ERR_INVALID, "capacity below the number of layers");
+  for (size_t i = 0; i < w.size(); ++i) widths[i] = w[i];
+  return (int)w.size();
 }
 
 int asp_num_layers(const asp_handle* h) { return h ? h->h.m : ASP_ERR_INVALID; }
@@ -670,12 +893,26 @@ void asp_destroy(asp_handle* hd) {
 }
 
 int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle** out) {
+  return asp_setup_layers(p, nullptr, 0, c, c_is_device, out);
+}
+
+int asp_setup_layers(const asp_params* pin, const int* widths, int nwidths, const double* c, int c_is_device,
+                     asp_handle** out) {
   std::string why;
   if (!out) return fail(ASP_ERR_INVALID, "out is null");
   *out = nullptr;
-  if (!valid(p, &why)) return fail(ASP_ERR_INVALID, why);
+  if (!pin) return fail(ASP_ERR_INVALID, "null params");
+  if (!valid(pin, &why)) return fail(ASP_ERR_INVALID, why);
+  bool packed = false;
+  const asp_params q = normalized(pin, &packed);
+  const asp_params* p = &q;
+  if (packed && p->dim != 2) return fail(ASP_ERR_UNSUPPORTED, "packed symmetric factors are 2D only");
+  const std::vector<int> lw = layer_widths(p, widths, nwidths, &why);
+  if (lw.empty()) return fail(ASP_ERR_INVALID, why);
+  if (!valid(p, &why, &lw)) return fail(ASP_ERR_INVALID, why);
   const int sms = device_sms();
-  if (!supported(p, &why, sms > 0 ? sms : kDefaultSms)) return fail(ASP_ERR_UNSUPPORTED, why);
+  const Part P = partition(p->n, p->pml, p->pml_aux ? p->pml_aux : p->pml, lw);
+  if (!supported(p, P, &why, sms > 0 ? sms : kDefaultSms)) return fail(ASP_ERR_UNSUPPORTED, why);
   if (!c) return fail(ASP_ERR_INVALID, "velocity pointer is null");
   const int n = p->n;
   const long long N = p->dim == 3 ? (long long)n * n * n : (long long)n * n;
@@ -704,11 +941,11 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   H.inv_h2 = 1.0 / (H.h * H.h);
   H.num_sms = sms;
   const double h = H.h, omega = p->omega, ih2 = H.inv_h2;
-  Part P = partition(n, H.gamma, H.gamma_a, H.b);
   H.m = P.m;
   H.x_lo = P.x_lo; H.x_hi = P.x_hi; H.alpha = P.alpha; H.beta = P.beta;
   const int m = H.m;
-  Sizes Z = sizes_for(p, sms);
+  H.packed = packed;
+  Sizes Z = sizes_for(p, P, sms, packed);
 
   // ---- global stencil weights (same boundary PML on x1 and x2)
   Profile g;
@@ -734,11 +971,15 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
   // ---- subproblems (2D: strips of columns; 3D: slabs of planes) and their
   // sweep-axis profiles
   H.subM.assign(m + 1, -1); H.subR.assign(m + 1, -1); H.subL.assign(m + 1, -1);
+  std::vector<double2> s2v, s2i;  // s and 1/s of every subproblem column, in SweepCoef order
   auto push_coef = [&](int lo, int w, const Profile& pr) {
     const int prof = (int)H.coef.size();
     for (int j = 0; j < w; ++j) {
       const double x = (lo + j) * h;
       const double2 sj = pr.s(x, omega), sm = pr.s(x - 0.5 * h, omega), sp = pr.s(x + 0.5 * h, omega);
+      s2v.push_back(sj);
+      const double d2 = sj.x * sj.x + sj.y * sj.y;
+      s2i.push_back(make_double2(sj.x / d2, -sj.y / d2));
       SweepCoef cf;
       cf.up = hscale(hmul(sj, sp), ih2);
       cf.dn = hscale(hmul(sj, sm), ih2);
@@ -776,12 +1017,13 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
     SubDesc S{};
     S.kind = kind; S.p = q; S.lo = lo; S.w = w;
     S.wp = (H.prec == ASP_PREC_C64) ? ((S.w + 1) & ~1) : S.w;
+    S.bs = H.packed ? packed_block_elems(S.w) : S.w * S.wp;
     S.xoff = H.x_lo[q] - lo;
     S.xw = H.x_hi[q] - H.x_lo[q] + 1;
     S.prof = push_coef(lo, w, pr);
     S.woff = woff;
     S.toff = -1;
-    woff += (long long)n * S.w * S.wp;
+    woff += (long long)n * S.bs;
     H.subs.push_back(S);
     return (int)H.subs.size() - 1;
   };
@@ -841,6 +1083,8 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
         goff += (long long)n * 2 * 32;
         M.w = S.w;
         M.wp = S.wp;
+        M.bs = S.bs;
+        M.prof = S.prof;
         M.jin = kind == 0 ? 0 : S.w - 1;
         M.keep = kind == 0 ? S.xoff + S.xw - 1 : S.xoff;
         const double2 rho = kind == 0 ? rhoR[q] : rhoL[q];
@@ -988,6 +1232,8 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
     if (H.prec == ASP_PREC_C128) {
       H.fc64.s1 = (const double2*)put(s1v.data(), n * sizeof(double2));
       H.fc64.s1inv = (const double2*)put(s1i.data(), n * sizeof(double2));
+      H.fc64.s2 = (const double2*)put(s2v.data(), nc * sizeof(double2));
+      H.fc64.s2inv = (const double2*)put(s2i.data(), nc * sizeof(double2));
       H.fc64.ca = (const double2*)put(ca.data(), n * sizeof(double2));
       H.fc64.cc = (const double2*)put(cc.data(), n * sizeof(double2));
       H.fc64.cd = (const double2*)put(cd.data(), n * sizeof(double2));
@@ -1004,9 +1250,11 @@ int asp_setup(const asp_params* p, const double* c, int c_is_device, asp_handle*
       std::vector<float> k2f(N);
       for (long long i = 0; i < N; ++i) k2f[i] = (float)k2[i];
       auto caf = f2(ca), ccf = f2(cc), cdf = f2(cd), upf = f2(upv), dnf = f2(dnv), dgf = f2(dgv);
-      auto s1f = f2(s1v), s1if = f2(s1i);
+      auto s1f = f2(s1v), s1if = f2(s1i), s2f = f2(s2v), s2if = f2(s2i);
       H.fc32.s1 = (const float2*)put(s1f.data(), n * sizeof(float2));
       H.fc32.s1inv = (const float2*)put(s1if.data(), n * sizeof(float2));
+      H.fc32.s2 = (const float2*)put(s2f.data(), nc * sizeof(float2));
+      H.fc32.s2inv = (const float2*)put(s2if.data(), nc * sizeof(float2));
       H.fc32.ca = (const float2*)put(caf.data(), n * sizeof(float2));
       H.fc32.cc = (const float2*)put(ccf.data(), n * sizeof(float2));
       H.fc32.cd = (const float2*)put(cdf.data(), n * sizeof(float2));

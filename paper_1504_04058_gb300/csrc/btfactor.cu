@@ -10,6 +10,8 @@
 //     S_0 = T_0,   S_k = T_k - a_k c_{k-1} S_{k-1}^{-1},
 // and the solver needs only W_k = S_k^{-1}: the forward pass is
 // z_k = W_k (g_k - a_k z_{k-1}) and the backward pass x_k = z_k - c_k W_k x_{k+1}.
+// With ASP_PREC_C64_SYM the factors are stored as the upper triangle of the
+// symmetric W_k Delta (internal.h, packed_index), half the bytes.
 // This is the banded LU of Section 3.1 with the fill of each w x w pivot block
 // kept as an explicit inverse, which turns every solve step into a dense
 // matrix product.
@@ -38,7 +40,7 @@ constexpr int kColGroups = kFactorThreads / 64;  // threads sharing a row
 template <typename R>
 __global__ void __launch_bounds__(kFactorThreads)
     btfactor_kernel(const SubDesc* __restrict__ subs, int first, FactorCoefs<R> F, int n,
-                    Cx<R>* __restrict__ Wout, int* err) {
+                    Cx<R>* __restrict__ Wout, int* err, int packed) {
   using C = Cx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int sub = first + blockIdx.x;
@@ -56,6 +58,7 @@ __global__ void __launch_bounds__(kFactorThreads)
   const Cx<R>* up = F.up + S.prof;
   const Cx<R>* dn = F.dn + S.prof;
   const Cx<R>* dg = F.dg + S.prof;
+  const Cx<R>* s2 = F.s2 + S.prof;
   C* Wsub = Wout + S.woff;
   bool bad = false;
   C* prev = buf1;  // holds the permuted inverse of the previous block
@@ -124,11 +127,17 @@ __global__ void __launch_bounds__(kFactorThreads)
       __syncthreads();
       C* t = src; src = dst; dst = t;
     }
-    // src holds the permuted inverse of S_k; store W_k (column-major, ld wp)
+    // src holds the permuted inverse of S_k; store W_k (column-major, ld wp),
+    // or (packed factors) the upper triangle of the symmetric W_k Delta
     if (row_ok) {
-      C* Wk = Wsub + (long long)k * w * wp;
+      C* Wk = Wsub + (long long)k * S.bs;
       const int pr = piv_row[i];
-      for (int j = jh; j < w; j += kColGroups) Wk[j * wp + i] = src[pr * ld + col_of_row[j]];
+      if (packed) {
+        for (int j = jh; j < w; j += kColGroups)
+          if (i <= j) Wk[packed_index(i, j)] = cmul(src[pr * ld + col_of_row[j]], s2[j]);
+      } else {
+        for (int j = jh; j < w; j += kColGroups) Wk[j * wp + i] = src[pr * ld + col_of_row[j]];
+      }
     }
     prev = src;
     // the next formation reads prev and piv/col tables; the barrier after it
@@ -149,12 +158,12 @@ cudaError_t launch_factor(Handle& H, int first, int count, cudaStream_t s) {
     e = ensure_dyn_smem((const void*)btfactor_kernel<double>, smem);
     if (e != cudaSuccess) return e;
     btfactor_kernel<double><<<nsub, kFactorThreads, smem, s>>>(H.d_subs, first, H.fc64, H.n, (double2*)H.W,
-                                                                H.err);
+                                                                H.err, 0);
   } else {
     e = ensure_dyn_smem((const void*)btfactor_kernel<float>, smem);
     if (e != cudaSuccess) return e;
     btfactor_kernel<float><<<nsub, kFactorThreads, smem, s>>>(H.d_subs, first, H.fc32, H.n, (float2*)H.W,
-                                                               H.err);
+                                                               H.err, H.packed ? 1 : 0);
   }
   H.launches += 1;
   return cudaGetLastError();

@@ -25,7 +25,16 @@
 // Data movement: the W_k blocks stream from HBM through an STG-stage
 // shared-memory ring (3; 6 for few right-hand sides; 2 where a block near 64
 // columns would overflow shared memory with more) filled by 1D bulk (TMA)
-// copies that complete on mbarriers; the per-step right-hand-side entries
+// copies that complete on mbarriers.  Complex64 factors are stored as the
+// packed upper triangle of the symmetric W'_k = W_k Delta (internal.h): four
+// extra producer warps issue the bulk copies of the packed blocks into a
+// 3-stage landing ring and expand each into the ring of STG full blocks the
+// compute warps read (ready / empty mbarriers), ahead of them, so the
+// expansion stays off the steps' dependent chain; the panel rows are scaled by
+// Delta^-1 when they are stored (W_k y = W'_k Delta^-1 y), and the compute
+// warps synchronise on a named barrier of their own (blocks of 60 or more
+// columns with many right-hand sides fall back to one landing stage and one
+// full block); the per-step right-hand-side entries
 // (and, in the backward pass, the z_k saved by the forward pass in a per-CTA
 // scratch slot) stream through a per-thread cp.async ring.  One __syncthreads per step publishes the panel.
 //
@@ -59,27 +68,40 @@ constexpr int kRing = 3;    // per-thread input ring depth
 struct Geometry {
   int wcap;    // largest w in the launch
   int wstage;  // elements of one W stage (largest w*wp, plus slack for the row tiles)
+  int pstage;  // packed factors: elements of one landing stage (largest packed block)
+  int packed;  // 1: blocks stored as packed symmetric triangles (ASP_PREC_C64_SYM)
 };
 
 __host__ __device__ inline size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
 
-template <typename R, int TR_, int TC, int LC, int NCW, int STG = 3, int KS = 1>
+template <typename R, int TR_, int TC, int LC, int NCW, int STG = 3, int KS = 1, bool PKT = false>
 struct Tiling {
-  static_assert(STG >= 2 && STG <= kMaxStages, "W-block ring depth");
+  static_assert(STG >= (PKT ? 1 : 2) && STG <= kMaxStages, "W-block ring depth");
+  static constexpr bool PK = PKT;
   using C = Cx<R>;
   static constexpr int TR = TR_;                   // rows per thread (2 or 4)
   static constexpr int WR = (32 / (LC * KS)) * TR;  // rows per warp
   static constexpr int WC = LC * TC;           // right-hand sides per warp
   static constexpr int NR = WC * NCW;          // right-hand sides per CTA
   static constexpr int E = TR * TC;            // panel entries per thread
-  __host__ __device__ static size_t bars() { return 64; }
-  __host__ __device__ static size_t wst(const Geometry& g) { return (size_t)STG * g.wstage * sizeof(C); }
+  // packed factors (symmetric W_k Delta, internal.h): producer warps land them
+  // in an LS-stage ring and expand them into STG full blocks
+  static constexpr int LS = STG == 1 ? 1 : 3;  // one landing stage only in the widest fallback
+  static constexpr int kProdWarps = 4;           // producer warps of packed factors
+  __host__ __device__ static size_t bars() { return 256; }
+  __host__ __device__ static size_t wst(const Geometry& g) {
+    return PK ? ((size_t)LS * g.pstage + (size_t)STG * g.wstage) * sizeof(C) : (size_t)STG * g.wstage * sizeof(C);
+  }
   __host__ __device__ static size_t ybuf(const Geometry& g) { return (size_t)2 * g.wcap * NR * sizeof(C); }
   __host__ __device__ static size_t ring(int nt) { return (size_t)kRing * E * nt * sizeof(C); }
   __host__ __device__ static size_t total(const Geometry& g, int nt) {
     return align128(bars()) + align128(wst(g)) + align128(ybuf(g)) + align128(ring(nt));
   }
 };
+
+__device__ __forceinline__ void mbar_arrive1(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
 
 template <typename C> struct Vec2;
 template <> struct Vec2<float2> {
@@ -114,18 +136,25 @@ template <typename C, int TC, int PS> __device__ __forceinline__ void st_cols(C*
   }
 }
 
-template <typename R, int TRT, int TC, int LC, int NCW, int MAXT, int MINB, int CLS, int STG, int KS>
+template <typename R, int TRT, int TC, int LC, int NCW, int MAXT, int MINB, int CLS, int STG, int KS, bool PKT>
 __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geometry G) {
   using C = Cx<R>;
-  using T = Tiling<R, TRT, TC, LC, NCW, STG, KS>;
+  using T = Tiling<R, TRT, TC, LC, NCW, STG, KS, PKT>;
   constexpr int kStages = STG;
+  constexpr bool PK = T::PK;
   constexpr int TR = T::TR, WR = T::WR, WC = T::WC, NR = T::NR, E = T::E;
   constexpr int CB = (int)sizeof(C);
   constexpr int PS = 2 * LC;  // column distance between a thread's pairs
+  constexpr int LS = T::LS;
   extern __shared__ __align__(128) unsigned char smem[];
-  const int NT = blockDim.x;
+  constexpr int kProd = T::kProdWarps;
+  const int NT = PK ? (int)blockDim.x - 32 * kProd : (int)blockDim.x;  // compute threads (PK: + producer warps)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  C* Wst = reinterpret_cast<C*>(smem + align128(T::bars()));
+  // PK barriers: bar[0, LS) landing copies, then ready[kStages], empty[kStages]
+  uint64_t* ready = bar + LS;
+  uint64_t* empty = bar + LS + kStages;
+  C* Wst = reinterpret_cast<C*>(smem + align128(T::bars()));  // !PK: the W ring; PK: the landing ring
+  C* Wfull = Wst + (size_t)LS * G.pstage;                      // PK: the full blocks
   C* ybuf = reinterpret_cast<C*>(smem + align128(T::bars()) + align128(T::wst(G)));
   C* ring = reinterpret_cast<C*>(smem + align128(T::bars()) + align128(T::wst(G)) + align128(T::ybuf(G)));
   __shared__ int s_abort;
@@ -149,12 +178,143 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
   const C* ccp = reinterpret_cast<const C*>(P.cc);
 
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    if constexpr (PK) {
+      for (int s = 0; s < LS; ++s) mbar_init(&bar[s], 1);
+      for (int s = 0; s < kStages; ++s) {
+        mbar_init(&ready[s], 1);
+        mbar_init(&empty[s], NT / 32);
+      }
+    } else {
+      for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    }
     s_abort = 0;
     fence_mbar_init();
   }
   __syncthreads();
-  uint32_t wuse = 0;  // W stages consumed so far (identical in every thread)
+  // bounded wait that also gives up once another warp has aborted
+  auto wait_or_abort = [&](uint64_t* b, uint32_t parity) -> bool {
+    const uint32_t addr = smem_addr(b);
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+      uint32_t done;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done)
+          : "r"(addr), "r"(parity)
+          : "memory");
+      if (done) return true;
+      if ((it & 1023u) == 1023u && *(volatile int*)&s_abort) return false;
+    }
+    return false;
+  };
+  // compute threads: all of the CTA, or (PK) all but the producer warp
+  auto sync_compute = [&]() {
+    if constexpr (PK) asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
+    else __syncthreads();
+  };
+  // the same barrier, returning whether any warp has aborted; with a producer
+  // warp that may set the flag at any time, the compute threads take one
+  // common decision (an OR over their reads at the barrier)
+  auto sync_compute_aborted = [&]() -> bool {
+    if constexpr (PK) {
+      const uint32_t mine = *(volatile int*)&s_abort ? 1u : 0u;
+      uint32_t any;
+      asm volatile(
+          "{\n\t.reg .pred p, q;\n\t"
+          "setp.ne.u32 p, %1, 0;\n\t"
+          "bar.red.or.pred q, 1, %2, p;\n\t"
+          "selp.u32 %0, 1, 0, q;\n\t}"
+          : "=r"(any)
+          : "r"(mine), "r"(NT)
+          : "memory");
+      return any != 0;
+    } else {
+      __syncthreads();
+      return s_abort != 0;
+    }
+  };
+
+  if constexpr (PK) {
+    if (warp >= NT / 32) {
+      // ---- producer warps: packed blocks in, full blocks out.  Thread pt of
+      // the kProd*32 takes an even share of the packed entries; entry (r, c),
+      // r <= c, goes to (r, c) and (c, r) of the full block.
+      const int pt = tid - NT, PT = 32 * kProd;
+      const bool lead = pt == 0;
+      uint32_t gi = 0, ge = 0;  // copies issued, blocks expanded (across jobs)
+      bool stop = false;
+      for (int job = blockIdx.x; job < P.njobs && !stop; job += gridDim.x) {
+        const Job J = P.jobs[job];
+        const SubDesc S = P.subs[J.sub];
+        const int w = S.w, wp = S.wp;
+        const int k0 = (CLS == CLS_TMAP) ? J.rhs0 : 0;
+        const int nf = n - k0;
+        const int L = nf + (n - 1);
+        const uint32_t bbytes = (uint32_t)(S.bs * CB);
+        const C* Wsub = Wg + S.woff;
+        auto blk = [&](int q) { return q < nf ? k0 + q : n - 2 - (q - nf); };
+        // this thread's share of the packed entries and its first (r, c)
+        const int np = w * (w + 1) / 2;
+        const int e0 = (int)(((long long)np * pt) / PT), e1 = (int)(((long long)np * (pt + 1)) / PT);
+        int c0 = (int)((sqrtf(8.f * e0 + 1.f) - 1.f) * 0.5f);
+        while (c0 * (c0 + 1) / 2 > e0) --c0;
+        while ((c0 + 1) * (c0 + 2) / 2 <= e0) ++c0;
+        const int r0e = e0 - c0 * (c0 + 1) / 2;
+        int issued = 0;
+        for (int t = 0; t < L; ++t) {
+          while (issued < L && issued < t + LS) {  // LS copies in flight
+            if (lead) {
+              const uint32_t st = gi % LS;
+              mbar_arrive_expect_tx(&bar[st], bbytes);
+              bulk_g2s(Wst + (size_t)st * G.pstage, Wsub + (long long)blk(issued) * S.bs, bbytes, &bar[st]);
+            }
+            ++gi;
+            ++issued;
+          }
+          const uint32_t sl = ge % LS, fs = ge % kStages;
+          const bool ok = wait_or_abort(&bar[sl], (ge / LS) & 1u) &&
+                          (ge < (uint32_t)kStages || wait_or_abort(&empty[fs], ((ge / kStages) - 1) & 1u));
+          // one common decision of the producer threads (they meet at barrier 2 below)
+          uint32_t failed;
+          asm volatile(
+              "{\n\t.reg .pred p, q;\n\t"
+              "setp.eq.u32 p, %1, 0;\n\t"
+              "bar.red.or.pred q, 2, %2, p;\n\t"
+              "selp.u32 %0, 1, 0, q;\n\t}"
+              : "=r"(failed)
+              : "r"(ok ? 1u : 0u), "r"(PT)
+              : "memory");
+          if (failed) {
+            if (lead && !*(volatile int*)&s_abort) record_error(P.err, ASP_ERR_TIMEOUT, blockIdx.x);
+            s_abort = 1;
+            stop = true;
+            break;
+          }
+          // full block (column-major, ld wp) from the packed upper triangle
+          const C* pk = Wst + (size_t)sl * G.pstage;
+          C* full = Wfull + (size_t)fs * G.wstage;
+          int r = r0e, c = c0;
+#pragma unroll 4
+          for (int e = e0; e < e1; ++e) {
+            const C v = pk[e];
+            full[c * wp + r] = v;
+            full[r * wp + c] = v;
+            if (++r > c) { r = 0; ++c; }
+          }
+          // every producer thread's entries are in place before the block is published
+          asm volatile("bar.sync 2, %0;" ::"r"(PT) : "memory");
+          if (lead) mbar_arrive1(&ready[fs]);
+          ++ge;
+        }
+      }
+      if (stop && lead) {  // copies still in flight complete on their landing barrier
+        for (uint32_t q = gi >= (uint32_t)LS ? gi - LS : 0; q < gi; ++q) mbar_wait(&bar[q % LS], (q / LS) & 1u);
+      }
+      return;
+    }
+  }
+  uint32_t wuse = 0;  // W stages consumed so far (identical in every compute thread)
 
   for (int job = blockIdx.x; job < P.njobs; job += gridDim.x) {
     const Job J = P.jobs[job];
@@ -165,7 +325,7 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
     const int k0 = (CLS == CLS_TMAP) ? rhs0 : 0;
     const int nf = n - k0;
     const int L = nf + (n - 1);
-    const uint32_t bbytes = (uint32_t)(w * wp * CB);
+    const uint32_t bbytes = (uint32_t)(S.bs * CB);
     const C* Wsub = Wg + S.woff;
     auto blk = [&](int q) { return q < nf ? k0 + q : n - 2 - (q - nf); };
 
@@ -216,16 +376,20 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
     C* zrow[TR];
 #pragma unroll
     for (int a = 0; a < TR; ++a) zrow[a] = zslot + (long long)(i0 + a) * NR;
+    C dr[TR];  // PK: 1/s2 of the thread's rows (panel rows are stored as Delta^-1 y)
+#pragma unroll
+    for (int a = 0; a < TR; ++a)
+      dr[a] = (PK && row_ok[a]) ? reinterpret_cast<const C*>(P.s2inv)[S.prof + i0 + a] : cmake<R>(R(1), R(0));
     const long long zstep = (long long)w * NR;
     C* accRp = reinterpret_cast<C*>(P.accR) + (long long)p * n * lda + rhs0;
     C* accLp = reinterpret_cast<C*>(P.accL) + (long long)p * n * lda + rhs0;
 
-    __syncthreads();  // the previous job's last reads of the W ring and panels are done
-    if (tid == 0) {
+    sync_compute();  // the previous job's last reads of the W ring and panels are done
+    if (!PK && tid == 0) {
       for (int t = 0; t < kStages && t < L; ++t) {
         const int st = (wuse + t) % kStages;
         mbar_arrive_expect_tx(&bar[st], bbytes);
-        bulk_g2s(Wst + (size_t)st * G.wstage, Wsub + (long long)blk(t) * w * wp, bbytes, &bar[st]);
+        bulk_g2s(Wst + (size_t)st * G.wstage, Wsub + (long long)blk(t) * S.bs, bbytes, &bar[st]);
       }
     }
 
@@ -305,22 +469,35 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
 #pragma unroll
           for (int c = 0; c < TC; ++c) y[c] = carry[a][c];
         }
+        if constexpr (PK) {
+#pragma unroll
+          for (int c = 0; c < TC; ++c) y[c] = cmul(y[c], dr[a]);
+        }
         if (wlane) st_cols<C, TC, PS>(yb + (size_t)(i0 + a) * NR + r0, y);
       }
-      __syncthreads();
-      if (s_abort) return;
-      if (tid == 0 && q >= 1 && q - 1 + kStages < L) {
+      if (sync_compute_aborted()) return;
+      if (!PK && tid == 0 && q >= 1 && q - 1 + kStages < L) {
         const int st = (wuse + q - 1) % kStages;
         mbar_arrive_expect_tx(&bar[st], bbytes);
-        bulk_g2s(Wst + (size_t)st * G.wstage, Wsub + (long long)blk(q - 1 + kStages) * w * wp, bbytes, &bar[st]);
+        bulk_g2s(Wst + (size_t)st * G.wstage, Wsub + (long long)blk(q - 1 + kStages) * S.bs, bbytes, &bar[st]);
       }
-      const uint32_t st = (wuse + q) % kStages;
-      const uint32_t par = ((wuse + q) / kStages) & 1u;
-      if (!mbar_wait(&bar[st], par)) {
-        record_error(P.err, ASP_ERR_TIMEOUT, blockIdx.x);
-        s_abort = 1;
+      const C* Wk;
+      const uint32_t fs = (wuse + q) % kStages;
+      if constexpr (PK) {  // the producer warp's full block
+        if (!wait_or_abort(&ready[fs], ((wuse + q) / kStages) & 1u)) {
+          if (!*(volatile int*)&s_abort) record_error(P.err, ASP_ERR_TIMEOUT, blockIdx.x);
+          s_abort = 1;
+        }
+        Wk = Wfull + (size_t)fs * G.wstage;
+      } else {
+        const uint32_t st = (wuse + q) % kStages;
+        const uint32_t par = ((wuse + q) / kStages) & 1u;
+        if (!mbar_wait(&bar[st], par)) {
+          record_error(P.err, ASP_ERR_TIMEOUT, blockIdx.x);
+          s_abort = 1;
+        }
+        Wk = Wst + (size_t)st * G.wstage;
       }
-      const C* Wk = Wst + (size_t)st * G.wstage;
 
       // ---- acc = W_k * panel on the thread's 2 x TC tile
       C acc[TR][TC];
@@ -356,6 +533,11 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
               acc[a][c].x += __shfl_xor_sync(0xffffffffu, acc[a][c].x, off);
               acc[a][c].y += __shfl_xor_sync(0xffffffffu, acc[a][c].y, off);
             }
+      }
+
+      if constexpr (PK) {  // this warp is done with the full block
+        __syncwarp();
+        if (lane == 0) mbar_arrive1(&empty[fs]);
       }
 
       // ---- epilogue
@@ -412,9 +594,14 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
     wuse += (uint32_t)L;
     cp_async_wait<0>();
   }
-  __syncthreads();
-  if (tid == 0)
-    for (int s = 0; s < kStages; ++s) mbar_inval(&bar[s]);
+  sync_compute();
+  if (tid == 0) {
+    if constexpr (PK) {
+      for (int s = 0; s < LS + 2 * kStages; ++s) mbar_inval(&bar[s]);
+    } else {
+      for (int s = 0; s < kStages; ++s) mbar_inval(&bar[s]);
+    }
+  }
 }
 
 // TRT: rows per thread.  MAXT / MINB: largest CTA the instance is compiled for
@@ -422,12 +609,15 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
 // W-block ring depth (few right-hand sides do little work per block, so they
 // need more blocks in flight to keep HBM busy).
 template <typename R, int TRT, int TC, int LC, int NCW, int CLS, int MAXT = 512, int MINB = 1, int STG = 3,
-          int KS = 1>
+          int KS = 1, bool PKT = false>
 cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
-  using T = Tiling<R, TRT, TC, LC, NCW, STG, KS>;
+  using T = Tiling<R, TRT, TC, LC, NCW, STG, KS, PKT>;
+  if (H.packed != PKT) return cudaErrorInvalidValue;  // the instance must match the factor storage
   const int nrw = (wcap + T::WR - 1) / T::WR;
-  const int nt = 32 * nrw * NCW;
-  if (nt > MAXT) return cudaErrorInvalidValue;
+  const int nt = 32 * nrw * NCW;                 // compute threads
+  constexpr bool packed = PKT;
+  const int nlaunch = nt + (packed ? 32 * T::kProdWarps : 0);  // + the producer warps of packed factors
+  if (nlaunch > MAXT) return cudaErrorInvalidValue;
   Geometry G;
   G.wcap = wcap;
   const int wpc = (sizeof(R) == 4) ? ((wcap + 1) & ~1) : wcap;
@@ -435,11 +625,14 @@ cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
   // column w-1 of a stage (their results are discarded)
   G.wstage = wcap * wpc + T::WR * nrw + 2;
   if (sizeof(R) == 4) G.wstage = (G.wstage + 1) & ~1;
+  G.pstage = packed_block_elems(wcap);
+  G.packed = packed ? 1 : 0;
   const size_t smem = T::total(G, nt);
-  auto kern = btsolve_kernel<R, TRT, TC, LC, NCW, MAXT, MINB, CLS, STG, KS>;
-  if constexpr (STG > 2) {
+  auto kern = btsolve_kernel<R, TRT, TC, LC, NCW, MAXT, MINB, CLS, STG, KS, PKT>;
+  if constexpr (STG > 2 || (PKT && STG > 1)) {
     // Wide blocks (w near 64 with many right-hand sides) can need more than
-    // the opt-in shared memory with a deep W ring; they run with two stages.
+    // the opt-in shared memory with a deep W ring; they run with two stages
+    // (packed factors: then one full block).
     // The limit is the device's opt-in size less the kernel's static shared
     // bytes, read once per instance (thread-safe static initialisation).
     static const size_t dyn_limit = [kern]() -> size_t {
@@ -451,13 +644,14 @@ cudaError_t run(Handle& H, const SolveParams& P, int wcap, cudaStream_t s) {
         return 0;
       return (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
     }();
-    if (smem > dyn_limit) return run<R, TRT, TC, LC, NCW, CLS, MAXT, MINB, 2, KS>(H, P, wcap, s);
+    // (packed factors may go on to one full block; the plain ring keeps two)
+    if (smem > dyn_limit) return run<R, TRT, TC, LC, NCW, CLS, MAXT, MINB, (STG > 2 ? 2 : 1), KS, PKT>(H, P, wcap, s);
   }
   cudaError_t e = ensure_dyn_smem((const void*)kern, smem);
   if (e != cudaSuccess) return e;
   int grid = P.njobs < P.zslots ? P.njobs : P.zslots;
   if (grid <= 0) return cudaSuccess;
-  kern<<<grid, nt, smem, s>>>(P, G);
+  kern<<<grid, nlaunch, smem, s>>>(P, G);
   H.launches += 1;
   return cudaGetLastError();
 }

@@ -5,23 +5,29 @@
 
 namespace asp {
 
+template <bool PKT>
+cudaError_t aux_c64(Handle& H, const SolveParams& P, int cls, int cap, int wmax, cudaStream_t s) {
+  using namespace bts;
+  constexpr int X = PKT ? 128 : 0;  // producer warps of packed factors
+  if (cls == CLS_TMAP) {
+    if (cap == 64 && wmax <= 24) return run<float, 2, 4, 8, 2, CLS_TMAP, 192 + X, PKT ? 2 : 3, 3, 1, PKT>(H, P, wmax, s);
+    if (cap == 64) return run<float, 2, 4, 8, 2, CLS_TMAP, 512 + X, 1, 3, 1, PKT>(H, P, wmax, s);
+  } else {
+    if (cap == 4) return run<float, 2, 2, 2, 1, CLS_SUB, 512, 1, 3, 1, PKT>(H, P, wmax, s);
+    if (cap == 1) return run<float, 2, 1, 1, 1, CLS_SUB, 512, 1, 3, 1, PKT>(H, P, wmax, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_btsolve_aux(Handle& H, const SolveParams& P, int cls, int cap, int wmax, cudaStream_t s) {
   using namespace bts;
-  if (H.prec == ASP_PREC_C64) {
-    if (cls == CLS_TMAP) {
-      if (cap == 64 && wmax <= 24) return run<float, 2, 4, 8, 2, CLS_TMAP, 192, 3>(H, P, wmax, s);
-      if (cap == 64) return run<float, 2, 4, 8, 2, CLS_TMAP>(H, P, wmax, s);
-    } else {
-      if (cap == 4) return run<float, 2, 2, 2, 1, CLS_SUB>(H, P, wmax, s);
-      if (cap == 1) return run<float, 2, 1, 1, 1, CLS_SUB>(H, P, wmax, s);
-    }
+  if (H.prec == ASP_PREC_C64)
+    return H.packed ? aux_c64<true>(H, P, cls, cap, wmax, s) : aux_c64<false>(H, P, cls, cap, wmax, s);
+  if (cls == CLS_TMAP) {
+    if (cap == 16) return run<double, 2, 2, 8, 1, CLS_TMAP>(H, P, wmax, s);
   } else {
-    if (cls == CLS_TMAP) {
-      if (cap == 16) return run<double, 2, 2, 8, 1, CLS_TMAP>(H, P, wmax, s);
-    } else {
-      if (cap == 4) return run<double, 2, 2, 2, 1, CLS_SUB>(H, P, wmax, s);
-      if (cap == 1) return run<double, 2, 1, 1, 1, CLS_SUB>(H, P, wmax, s);
-    }
+    if (cap == 4) return run<double, 2, 2, 2, 1, CLS_SUB>(H, P, wmax, s);
+    if (cap == 1) return run<double, 2, 1, 1, 1, CLS_SUB>(H, P, wmax, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -28,9 +28,24 @@ struct SubDesc {
   int xoff;          // X_p = local columns [xoff, xoff + xw)
   int xw;
   int prof;          // offset of this subproblem's sweep-axis coefficients
+  int bs;            // elements per stored block: w*wp, or with packed factors
+                     // (ASP_PREC_C64_SYM) the upper triangle of the symmetric
+                     // W_k Delta (packed_block_elems)
   long long woff;    // element offset of block 0 of its factor
   long long toff;    // element offset of its trace-transfer map (-1: none)
 };
+
+// With ASP_PREC_C64_SYM, 2D factors are stored as the upper triangle of W'_k = W_k Delta,
+// Delta = diag(s2_j) the subproblem's sweep-axis PML weights: D^-1 H is
+// complex symmetric for D = diag(s1_k s2_j) (Section 3.1, practical remark 4),
+// and by induction over the block recursion so is every S_k^-1 D_k, i.e. W'_k.
+// Entry (i, j), i <= j, sits at j (j + 1) / 2 + i; the block is padded to an
+// even count (16-byte aligned blocks).  W_k = W'_k Delta^-1.
+__host__ __device__ inline int packed_block_elems(int w) { return ((w * (w + 1) / 2) + 1) & ~1; }
+__host__ __device__ inline int packed_index(int i, int j) {
+  const int lo = i < j ? i : j, hi = i < j ? j : i;
+  return hi * (hi + 1) / 2 + lo;
+}
 
 // Solve modes of the batched block-tridiagonal solver (btsolve.cuh).
 enum SolveMode : int {
@@ -67,6 +82,8 @@ template <typename R> struct FactorCoefs {
   using C = typename CplxOf<R>::T;
   const C* s1 = nullptr;     // s at the x1 nodes (boundary PML), and its reciprocal
   const C* s1inv = nullptr;
+  const C* s2 = nullptr;     // s of every subproblem column (SubDesc::prof), and its reciprocal
+  const C* s2inv = nullptr;
   const C* ca = nullptr;
   const C* cc = nullptr;
   const C* cd = nullptr;
@@ -88,6 +105,7 @@ struct SolveParams {
   const void* W;    // factor blocks W_k = S_k^-1
   const void* ca;   // a_k: coupling of block k to block k-1 (x1 stencil), factor precision
   const void* cc;   // c_k: coupling of block k to block k+1, factor precision
+  const void* s2inv;  // 1 / s2 of every subproblem column (complex64: packed factors), factor precision
   const void* in;   // EMBED / SUB input (factor precision, RHS-interleaved)
   void* outM;       // EMBED output restricted to X_q (factor precision)
   void* outR;       // FILL_R output
@@ -110,6 +128,7 @@ struct TmMap {
   long long toff;  // element offset of the map
   long long goff;  // element offset of its diagonal-block columns ([n][2][32])
   int w, wp;       // padded width and block leading dimension of the subproblem
+  int bs, prof;    // elements per stored (packed) block; its sweep coefficients' offset
   int jin, keep;   // boundary-data column and traced column (local)
   float2 rho;      // s2(keep) / s2(in) of the subproblem's sweep profile
 };
@@ -227,7 +246,8 @@ void phase_end(Handle& H, PhaseTok t, cudaStream_t s);
 // ---- launchers (one translation unit each) ----
 cudaError_t launch_matvec(const Handle& H, const double2* x, double2* y, int nrhs, cudaStream_t s);
 cudaError_t launch_factor(Handle& H, int first, int count, cudaStream_t s);
-cudaError_t launch_btsolve_apply(Handle& H, const SolveParams& P, int cls, int cap, int wmax, cudaStream_t s);
+cudaError_t launch_btsolve_apply(Handle& H, const SolveParams& P, int cls, int cap, int variant, int wmax,
+                                 cudaStream_t s);
 cudaError_t launch_btsolve_aux(Handle& H, const SolveParams& P, int cls, int cap, int wmax, cudaStream_t s);
 int btsolve_rhs_capacity(int nrhs, int wmax, int prec, bool tmap);
 cudaError_t launch_chain(Handle& H, const ChainParams& P, cudaStream_t s);
@@ -252,6 +272,7 @@ struct Handle {
   asp_params prm{};
   int dim = 2;
   int n = 0, m = 0, prec = 0, gamma = 0, gamma_a = 0, b = 0;
+  bool packed = false;  // complex64 blocks stored as packed symmetric triangles (ASP_PREC_C64_SYM)
   double h = 0, inv_h2 = 0;
   long long N = 0;  // n^dim grid points
 

@@ -31,6 +31,10 @@
 // 1.5 n^2 w^2 for building the columns by forward and backward solves, and it
 // needs no forward-pass scratch.
 //
+// With packed factors (ASP_PREC_C64_SYM) the blocks arrive as the upper
+// triangle of the symmetric W'_k = W_k Delta (internal.h), and both kernels
+// read W_k[i][j] = W'_k(i, j) / s2_j; otherwise full blocks (ld wp).
+//
 // gdiag_kernel runs the Gamma recursion (one CTA per map, n dependent steps of
 // two w x w x w complex products in shared memory) and stores Gamma_k e_in and
 // Gamma_k e_keep for every k.
@@ -92,12 +96,14 @@ struct TmParams {
   int wcap, K8, N16, natoms, wstages;
   uint32_t b_half, w_stage;  // bytes: one stage's B_hi, one W stage
   uint32_t idesc;
+  int packed;  // blocks stored as packed symmetric triangles (else full, ld wp)
   float inv_h2;
   const float2* W;
   const float2* cc;
   const float2* ca;
   const float2* s1;
   const float2* s1inv;
+  const float2* s2inv;
   const float2* gd;
   float2* T;
   int* err;
@@ -276,7 +282,7 @@ __global__ void __maxnreg__(80) tmap_tc_kernel(const __grid_constant__ TmParams 
       for (int j = blockIdx.x; j < njobs && !stop; j += gridDim.x) {
         const TmJob J = tm_job(P, j);
         const TmMap M = P.maps[J.mi];
-        const uint32_t wbytes = (uint32_t)(M.w * M.wp * 8);
+        const uint32_t wbytes = (uint32_t)(M.bs * 8);
         for (int k = J.kmax; k >= 0; --k, ++wc) {
           const int s = (int)(wc % WS);
           if (wc >= (uint32_t)WS && !tm_wait(&wempty[s], ((wc / WS) - 1) & 1u, abort_flag)) {
@@ -286,7 +292,7 @@ __global__ void __maxnreg__(80) tmap_tc_kernel(const __grid_constant__ TmParams 
           }
           unsigned char* dst = sgen + offW + (uint32_t)s * P.w_stage;
           mbar_arrive_expect_tx(&wfull[s], wbytes + 2 * kGS * 8);
-          bulk_g2s(dst, P.W + M.woff + (long long)k * M.w * M.wp, wbytes, &wfull[s]);
+          bulk_g2s(dst, P.W + M.woff + (long long)k * M.bs, wbytes, &wfull[s]);
           bulk_g2s(dst + P.w_stage - 2 * kGS * 8, P.gd + M.goff + (long long)k * 2 * kGS, 2 * kGS * 8, &wfull[s]);
         }
       }
@@ -349,7 +355,8 @@ __global__ void __maxnreg__(80) tmap_tc_kernel(const __grid_constant__ TmParams 
     for (int j = blockIdx.x; j < njobs && !stop; j += gridDim.x) {
       const TmJob J = tm_job(P, j);
       const TmMap M = P.maps[J.mi];
-      const int w = M.w, wp = M.wp, wcap = P.wcap;
+      const int w = M.w, wcap = P.wcap;
+      const float2* dinv = P.s2inv + M.prof;  // W_k[i][j] = W'_k(i, j) / s2_j
       for (int k = J.kmax; k >= 0; --k, ++wc, ++bc) {
         const int sw = (int)(wc % WS), sb = (int)(bc & 1u);
         const float2 nc = make_float2(-P.cc[k].x, -P.cc[k].y);
@@ -378,7 +385,7 @@ __global__ void __maxnreg__(80) tmap_tc_kernel(const __grid_constant__ TmParams 
           if (i >= wcap || jj >= wcap) continue;
           float2 v = make_float2(0.f, 0.f);
           if (i < w && jj < w) {
-            const float2 wv = Wk[jj * wp + i];
+            const float2 wv = P.packed ? cmul(Wk[packed_index(i, jj)], __ldg(dinv + jj)) : Wk[jj * M.wp + i];
             v = make_float2(nc.x * wv.x - nc.y * wv.y, nc.x * wv.y + nc.y * wv.x);
           }
           // rows 2i (re output) and 2i+1 (im output), floats 2jj, 2jj+1
@@ -524,18 +531,26 @@ constexpr int kGdThreads = 256;
 __global__ void __launch_bounds__(kGdThreads) gdiag_kernel(const TmMap* __restrict__ maps, int n,
                                                           const float2* __restrict__ W,
                                                           const float2* __restrict__ ca,
-                                                          const float2* __restrict__ cc, float2* __restrict__ gd) {
+                                                          const float2* __restrict__ cc,
+                                                          const float2* __restrict__ s2inv, float2* __restrict__ gd,
+                                                          int packed) {
   __shared__ float2 sW[32][33], sG[32][33], sP[32][33];
   const TmMap M = maps[blockIdx.x];
-  const int w = M.w, wp = M.wp;
+  const int w = M.w;
   const int tid = threadIdx.x, i = tid >> 3, j0 = tid & 7;
   const float2* Wsub = W + M.woff;
   float2* g = gd + M.goff;
+  // W_k[i][j] = W'_k(i, j) / s2_j from the packed symmetric factor
+  float2 dinv[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) dinv[u] = (j0 + 8 * u < w) ? s2inv[M.prof + j0 + 8 * u] : make_float2(0.f, 0.f);
   auto fetch = [&](int k, float2 (&v)[4]) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int jj = j0 + 8 * u;
-      v[u] = (i < w && jj < w) ? Wsub[(long long)k * w * wp + (long long)jj * wp + i] : make_float2(0.f, 0.f);
+      v[u] = (i >= w || jj >= w) ? make_float2(0.f, 0.f)
+             : packed ? cmul(Wsub[(long long)k * M.bs + packed_index(i, jj)], dinv[u])
+                      : Wsub[(long long)k * M.bs + (long long)jj * M.wp + i];
     }
   };
   float2 wr[4];
@@ -604,7 +619,7 @@ cudaError_t launch_tmap_diag(Handle& H, cudaStream_t s) {
   for (const TmMap& M : H.tm_host)
     if (M.w > kTmapTcMaxW) return cudaErrorInvalidValue;
   gdiag_kernel<<<nmaps, kGdThreads, 0, s>>>(H.d_tm, H.n, (const float2*)H.W, H.fc32.ca, H.fc32.cc,
-                                            (float2*)H.gdiag);
+                                            H.fc32.s2inv, (float2*)H.gdiag, H.packed ? 1 : 0);
   H.launches += 1;
   return cudaGetLastError();
 }
@@ -628,7 +643,7 @@ cudaError_t launch_tmap_tc(Handle& H, cudaStream_t s) {
   P.natoms = (P.K8 + 31) / 32;
   P.b_half = (uint32_t)P.natoms * (uint32_t)P.N16 * 128;
   int wpc = 0;
-  for (const TmMap& M : H.tm_host) wpc = std::max(wpc, M.w * M.wp * 8);
+  for (const TmMap& M : H.tm_host) wpc = std::max(wpc, M.bs * 8);
   P.w_stage = (uint32_t)((wpc + 2 * kGS * 8 + 127) / 128 * 128);
   P.idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(P.N16 >> 3) << 17) | ((uint32_t)(kTT >> 4) << 24);
   P.inv_h2 = (float)H.inv_h2;
@@ -637,6 +652,8 @@ cudaError_t launch_tmap_tc(Handle& H, cudaStream_t s) {
   P.ca = H.fc32.ca;
   P.s1 = H.fc32.s1;
   P.s1inv = H.fc32.s1inv;
+  P.s2inv = H.fc32.s2inv;
+  P.packed = H.packed ? 1 : 0;
   P.gd = (const float2*)H.gdiag;
   P.T = (float2*)H.tmap;
   P.err = H.err;

@@ -55,17 +55,17 @@ def c64_tol(n):
     return 2e-4 * max(1.0, n / 300)
 
 
-def handle(P, precision="c128", max_rhs=None, restart=40):
+def handle(P, precision="c128", max_rhs=None, restart=40, widths=None):
     import paper_1504_04058_gb300 as asp
     prm = asp.make_params(P.n, P.omega, P.pml, P.b, pml_aux=P.pml_aux or 0, C=P.C, precision=precision,
                           max_rhs=max_rhs or P.nrhs, restart=restart)
-    h = asp.asp_setup(P.c, prm)
+    h = asp.asp_setup(P.c, prm, widths=widths)
     h.factor()
     return h
 
 
-def oracle_pc(P):
-    return sweeping.Preconditioner(2, P.n, P.omega, P.c, P.pml, P.b, P.C, gamma_a=P.pml_aux)
+def oracle_pc(P, widths=None):
+    return sweeping.Preconditioner(2, P.n, P.omega, P.c, P.pml, P.b, P.C, gamma_a=P.pml_aux, widths=widths)
 
 
 SMALL = {
@@ -111,7 +111,7 @@ def test_matvec_config_n127():
 
 # ------------------------------------------------------- layer subproblems
 
-@pytest.mark.parametrize("precision,tol", [("c128", 1e-11), ("c64", 2e-4)])
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-11), ("c64", 2e-4), ("c64sym", 2e-4)])
 @pytest.mark.parametrize("name", ["ragged_const", "lens_3rhs", "thin_aux_pml", "widest_band_64"])
 def test_subproblem_solves_match_oracle(name, precision, tol):
     """Every H_q^M, H_p^R, H_p^L: GPU block-inverse solve vs oracle banded LU."""
@@ -135,7 +135,7 @@ def test_subproblem_solves_match_oracle(name, precision, tol):
 
 # ----------------------------------------------------- preconditioner apply
 
-@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4)])
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4), ("c64sym", 2e-4)])
 @pytest.mark.parametrize("name", list(SMALL))
 def test_apply_matches_oracle(name, precision, tol):
     P = small(name)
@@ -157,7 +157,7 @@ CHAIN_WIDE = {
 }
 
 
-@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4)])
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4), ("c64sym", 2e-4)])
 @pytest.mark.parametrize("name", list(CHAIN_WIDE))
 def test_apply_matches_oracle_long_layers(name, precision, tol):
     n, om, g, b, vel, R, ga = CHAIN_WIDE[name]
@@ -200,12 +200,78 @@ def widest_blocks():
     return P, oracle_pc(P).apply(P.f)
 
 
-@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4)])
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4), ("c64sym", 2e-4)])
 def test_apply_with_widest_blocks_matches_oracle(widest_blocks, precision, tol):
     P, zo = widest_blocks
     h = handle(P, precision)
     z = host(h.apply_preconditioner(dev(P.f)))
     assert emax(z, zo) <= tol, (emax(z, zo), rel(z, zo))
+
+
+# Layers of arbitrary widths (Section 3.1, practical remark 3): an irregular
+# list with one- and two-column layers, and widths chosen from the velocity.
+def _widths_cases():
+    import paper_1504_04058_gb300 as asp
+    P1 = W.small_problem(2, 80, 8 * math.pi, 6, 3, "layered", nrhs=3, pml_aux=4)
+    Pw = P1.n + 2 - 2 * P1.pml
+    w1 = [5, 1, 2, 7, 3, 9, 4, 4, 6, 1, 8, 2, 3, 5, 10]
+    w1[-1] += Pw - sum(w1)
+    P2 = W.small_problem(2, 300, 24 * math.pi, 8, 3, "layered", nrhs=5)
+    prm = asp.make_params(P2.n, P2.omega, P2.pml, P2.b)
+    w2 = asp.layer_widths_from_velocity(prm, P2.c, 3, 9)
+    return {"irregular_n80": (P1, w1), "from_velocity_n300": (P2, w2)}
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4)])
+@pytest.mark.parametrize("name", ["irregular_n80", "from_velocity_n300"])
+def test_apply_with_arbitrary_layer_widths_matches_oracle(name, precision, tol):
+    P, widths = _widths_cases()[name]
+    assert len(set(widths)) > 1
+    h = handle(P, precision, widths=widths)
+    assert h.num_layers == len(widths)
+    z = host(h.apply_preconditioner(dev(P.f)))
+    zo = oracle_pc(P, widths).apply(P.f)
+    record(f"apply_widths[{name}-{precision}]", emax=emax(z, zo), rel=rel(z, zo), tol=tol)
+    assert emax(z, zo) <= tol, (emax(z, zo), rel(z, zo))
+
+
+def test_fgmres_with_arbitrary_layer_widths_matches_oracle():
+    """FP64 path with widths chosen from the velocity: the same Krylov
+    dimension gives the oracle's solution at 1e-9, and the iteration count to
+    tolerance is within one of the oracle's."""
+    P, widths = _widths_cases()["from_velocity_n300"]
+    pc = oracle_pc(P, widths)
+    A = operator.helmholtz_matrix(2, P.n, P.omega, P.c, P.pml, P.C)
+    uo, itso, _ = fgmres.solve(pc, A, P.f, tol=P.tol, restart=P.restart)
+    k = int(itso.max())
+    uk, _, _ = fgmres.solve(pc, A, P.f, tol=P.tol, restart=P.restart, fixed_iters=k)
+    h = handle(P, "c128", widths=widths)
+    ug, _ = h.gmres_solve(dev(P.f), tol=0.0, maxit=k)
+    assert emax(host(ug), uk) <= 1e-9, rel(host(ug), uk)
+    _, info = h.gmres_solve(dev(P.f), tol=P.tol, maxit=200)
+    for r in range(P.nrhs):
+        assert abs(info[r]["iterations"] - int(itso[r])) <= 1, (info[r], itso[r])
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4)])
+def test_autotuned_apply_matches_oracle(precision, tol):
+    """asp_autotune times the candidate launch shapes of the layer solves on the
+    handle's factors and keeps the fastest; applies with the chosen shapes
+    (at 34 and at 1 right-hand side) still match the oracle."""
+    n, om, g, b, vel, R, ga = CHAIN_WIDE["n300_34rhs"]
+    P = W.small_problem(2, n, om, g, b, vel, nrhs=R, pml_aux=ga)
+    h = handle(P, precision)
+    for nr in (R, 1):
+        t = h.autotune(nr)
+        for cls in ("embed", "fill"):
+            assert t[cls]["cap"] in (1, 2, 4, 8, 16, 32) and t[cls]["variant"] in (0, 1), t
+            assert any(x > 0 for x in t[cls]["candidate_ms"]), t
+    zo = oracle_pc(P).apply(P.f)
+    z = host(h.apply_preconditioner(dev(P.f)))
+    record(f"apply_autotuned[{precision}]", emax=emax(z, zo), rel=rel(z, zo), tol=tol)
+    assert emax(z, zo) <= tol, (emax(z, zo), rel(z, zo))
+    z1 = host(h.apply_preconditioner(dev(P.f[..., :1])))
+    assert emax(z1, zo[..., :1]) <= tol, (emax(z1, zo[..., :1]), rel(z1, zo[..., :1]))
 
 
 def test_apply_is_linear_and_rhs_independent():
@@ -340,7 +406,7 @@ def headline_oracle():
     return P, zo, uo, int(itso[0]), A
 
 
-@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("precision", ["c64", "c64sym", "c128"])
 def test_headline_apply_matches_oracle(headline_oracle, precision):
     """Algorithm 2 at the benchmark's full size and widths (w_M = 42, w_R = w_L =
     23, 246 layers), in the launch configuration the benchmark times (all 32
@@ -348,7 +414,7 @@ def test_headline_apply_matches_oracle(headline_oracle, precision):
     the 1-RHS apply), element-wise against the oracle on three right-hand
     sides: c64_tol(1023) for complex64 factors, 1e-10 for complex128."""
     P, zo, _, _, _ = headline_oracle
-    tol = c64_tol(P.n) if precision == "c64" else 1e-10
+    tol = 1e-10 if precision == "c128" else c64_tol(P.n)
     h = handle(P, precision, max_rhs=32, restart=40)
     z = host(h.apply_preconditioner(dev(P.f)))[..., :3]
     record(f"headline_apply32[{precision}]", emax=emax(z, zo), rel=rel(z, zo), tol=tol)
@@ -377,6 +443,34 @@ def test_headline_fgmres_matches_oracle_iteration_count(headline_oracle):
     assert res <= P.tol, res
     assert emax(u, uo[..., 0], single=True) <= 1e-3, rel(u, uo[..., 0])
     h.destroy()
+
+
+def test_packed_symmetric_factors_halve_the_factor_bytes():
+    """ASP_PREC_C64_SYM (Section 3.1, practical remark 4): the same problem's
+    footprint shrinks by the factor bytes saved, n * sum over subproblems of
+    (w * w_pad - packed triangle) complex64 entries, and FGMRES with packed
+    factors reaches the FP64 tolerance in the same number of iterations."""
+    import paper_1504_04058_gb300 as asp
+    P = W.small_problem(2, 300, 24 * math.pi, 8, 4, "layered", nrhs=3)
+    full = asp.make_params(P.n, P.omega, P.pml, P.b, C=P.C, precision="c64", max_rhs=3, restart=20)
+    sym = asp.make_params(P.n, P.omega, P.pml, P.b, C=P.C, precision="c64sym", max_rhs=3, restart=20)
+    part = partition.make_partition(P.n, P.pml, P.b)
+    saved = 0
+    for L in part.layers:
+        for lo, hi, exists in ((L.m_lo, L.m_hi, True), (L.r_lo, L.r_hi, L.p >= 2), (L.l_lo, L.l_hi, L.p <= part.m - 1)):
+            if exists:
+                w = hi - lo + 1
+                saved += P.n * (w * (w + (w % 2)) - ((w * (w + 1) // 2 + 1) // 2 * 2))
+    assert asp.asp_footprint_bytes(full) - asp.asp_footprint_bytes(sym) == saved * 8
+    its = []
+    for prm in (full, sym):
+        h = asp.asp_setup(P.c, prm)
+        h.factor()
+        _, info = h.gmres_solve(dev(P.f), tol=P.tol, maxit=100)
+        assert all(i["converged"] for i in info)
+        its.append([i["iterations"] for i in info])
+        h.destroy()
+    assert its[0] == its[1], its
 
 
 def test_native_library_is_loaded_and_launches_kernels():

@@ -189,3 +189,84 @@ def test_selftest_bounded_wait_rejects_bad_limits():
     assert lib.asp_selftest_bounded_wait(0, None) == _lib.ASP_ERR_INVALID
     assert lib.asp_selftest_bounded_wait(-3, None) == _lib.ASP_ERR_INVALID
     assert lib.asp_selftest_bounded_wait((1 << 26) + 1, None) == _lib.ASP_ERR_INVALID
+
+
+# ------------------------------------------------ layers of arbitrary widths
+
+def _widths_for(c, n, gamma, b_min, b_max, dim=2, pml_aux=0):
+    import paper_1504_04058_gb300 as asp
+    prm = asp.make_params(n, 10.0, gamma, b_min, pml_aux=pml_aux, dim=dim)
+    return asp.layer_widths_from_velocity(prm, c, b_min, b_max)
+
+
+def test_layer_widths_for_a_smooth_velocity_are_uniform(lib):
+    """No heavy jump: every layer has b_min columns and the last takes the
+    remainder, which is the uniform partition."""
+    import numpy as np
+    n, gamma = 127, 12
+    w = _widths_for(np.ones((n, n)), n, gamma, 4, 8)
+    P = n + 2 - 2 * gamma
+    m = P // 4
+    assert sum(w) == P
+    assert w == [4] * (m - 1) + [4 + P - 4 * m]
+
+
+def test_layer_widths_grow_where_the_velocity_jumps(lib):
+    """Section 3.1, practical remark 3: wider layers where the velocity varies
+    heavily.  With sharp jumps between constant bands, no layer boundary
+    falls between two columns with a jump unless the layer already has b_max
+    columns; a layer grows beyond b_min only to carry its boundary past a
+    jump."""
+    import numpy as np
+    n, gamma, b_min, b_max = 200, 8, 3, 7
+    prof = np.ones(n)
+    jumps = [40, 41, 97, 150, 151, 152]  # column j (1-based) jumps to j+1
+    for j in jumps:
+        prof[j:] *= 1.15
+    c = np.broadcast_to(prof[:, None], (n, n)).copy()  # c[i2-1, i1-1]: varies along x2
+    w = _widths_for(c, n, gamma, b_min, b_max)
+    P = n + 2 - 2 * gamma
+    assert sum(w) == P and min(w) >= 1
+    ends, a = [], gamma
+    for x in w:
+        ends.append(a + x - 1)
+        a += x
+    for e, x in zip(ends[:-1], w[:-1]):
+        assert e not in jumps or x == b_max, (e, x)
+    # where a boundary would have fallen on a jump the layer grew past it
+    assert any(x > b_min for x in w[:-1])
+    assert all(x in (b_min, b_max) or any(e - x < j < e for j in jumps) for e, x in zip(ends[:-1], w[:-1]))
+
+
+def test_layer_widths_rejected_on_host(lib):
+    """Widths that do not sum to P, zero widths and an oversized padded width
+    are refused before any device work."""
+    import numpy as np
+    import paper_1504_04058_gb300 as asp
+    from paper_1504_04058_gb300 import _lib
+    n, gamma = 31, 4
+    prm = asp.make_params(n, 10.0, gamma, 3, max_rhs=1, restart=4)
+    P = n + 2 - 2 * gamma
+    for bad in ([3] * (P // 3), [0] + [3] * (P // 3), [P + 1]):
+        with pytest.raises(asp.AspError) as ei:
+            asp.asp_setup(np.ones((n, n)), prm, widths=bad)
+        assert ei.value.code == _lib.ASP_ERR_INVALID
+        assert asp.asp_footprint_bytes(prm, widths=bad) == 0
+    with pytest.raises(asp.AspError):
+        asp.layer_widths_from_velocity(prm, np.ones((n, n)), 0, 4)
+
+
+def test_footprint_with_explicit_widths(lib):
+    """Uniform widths passed explicitly give asp_footprint_bytes' value; wider
+    layers (fewer, larger subproblems) give a different one."""
+    import paper_1504_04058_gb300 as asp
+    n, gamma, b = 127, 12, 4
+    prm = asp.make_params(n, 40.0, gamma, b, precision="c64", max_rhs=2, restart=8)
+    P = n + 2 - 2 * gamma
+    m = P // b
+    uniform = [b] * (m - 1) + [b + P - m * b]
+    f0 = asp.asp_footprint_bytes(prm)
+    assert f0 > 0 and asp.asp_footprint_bytes(prm, widths=uniform) == f0
+    wider = [8] * (P // 8 - 1) + [8 + P - 8 * (P // 8)]
+    f1 = asp.asp_footprint_bytes(prm, widths=wider)
+    assert f1 > 0 and f1 != f0
