@@ -66,6 +66,26 @@ def algorithmic3d(n, gamma, b):
             "schur_flops": n * schur}
 
 
+def algorithmic3d_nd(n, gamma, b):
+    """Work of the nested-dissection slab factor (Section 4), from the library's
+    host plan of the n x n column grid: per slab, the fronts' Gauss-Jordan steps
+    (s steps over an ns x ns front: s*ns^2 complex multiply-adds, 8 real flops
+    each) and the stored factor entries ([X; L] and P), read once each by an
+    apply's forward and backward passes in complex64."""
+    import ctypes
+    from paper_1504_04058_gb300 import _lib
+    lib = _lib.load()
+    m, wM, wR, wL, _ = _layer_widths(n, gamma, b)
+    flops = 0.0
+    entries = 0.0
+    for w in wM + wR + wL:
+        st = (ctypes.c_longlong * 9)()
+        _lib.check(lib.asp_nd_plan_check(n, w, st, 9), "asp_nd_plan_check")
+        entries += st[3]
+        flops += 8.0 * st[8]
+    return {"factor_flops": flops, "factor_bytes": 8.0 * entries, "apply_bytes": 8.0 * entries}
+
+
 def dist_max(x: float, device=None) -> float:
     """Maximum of a per-rank value over all ranks (the step time the job is
     judged by); the value itself when there is no process group."""
@@ -280,7 +300,8 @@ def run_asp(args, rank, world):
         restart = 16
     pml_aux = args.pml_aux if args.pml_aux else (P.pml_aux or 0)
     prm = asp.make_params(P.n, P.omega, P.pml, P.b, pml_aux=pml_aux, C=P.C, precision=args.precision,
-                          max_rhs=P.nrhs, restart=restart, dim=P.dim)
+                          max_rhs=P.nrhs, restart=restart, dim=P.dim,
+                          slab_solver=args.slab_solver if P.dim == 3 else "block")
     widths = None
     if args.layer_widths:  # "BMIN:BMAX": widths chosen from the velocity by the library
         bmin, bmax = (int(x) for x in args.layer_widths.split(":"))
@@ -411,7 +432,27 @@ def run_asp(args, rank, world):
     fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # TFLOP/s at max clock
     phase_ms = {p: round(phases[p][0] / args.steps, 3) for p in PHASES}
     value = whole_job_rate(world, P.nrhs, ms)
-    if P.dim == 3:
+    if P.dim == 3 and args.slab_solver == "nd":
+        alg3 = algorithmic3d_nd(P.n, P.pml, P.b)
+        fl = alg3["factor_flops"] / (factor_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": fl, "peak": fp32_peak, "unit": "TFLOP/s", "frac": fl / fp32_peak,
+                "kernel": "nested-dissection slab factor (assembly, extend-add, blocked Gauss-Jordan on the fronts' "
+                          "fully summed columns, CUDA cores; all launches of the factor)",
+                "peak_source": "SMs x 128 FP32 lanes x 2 flops x max SM clock (derived)",
+                "traffic": None, "factor_ms": factor_ms, "algorithmic_flops": alg3["factor_flops"],
+                "factor_bytes": alg3["factor_bytes"]}
+        apply_ms = (phases["embed"][0] + phases["fill"][0]) / max(phases["embed"][1], 1)
+        roof["hbm_view"] = {"kernel": "3D slab solves of one apply (nested-dissection fronts)",
+                            "algorithmic_bytes": alg3["apply_bytes"], "ms_per_apply": apply_ms,
+                            "GBps": alg3["apply_bytes"] / (apply_ms * 1e-3) / 1e9,
+                            "frac_of_measured_hbm": alg3["apply_bytes"] / (apply_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+        config = (dict(WORKLOAD_3D, parallelism=f"replicas x{world}", slab_solver="nested dissection",
+                       l2="no flush needed: slab factors exceed the 129 MB L2")
+                  if args.workload == "n95_3d" else
+                  {"workload": "3d_helmholtz_n47_one_slab_omega12pi_pml6_b37 (profiling case)",
+                   "slab_solver": "nested dissection"})
+        metric = METRIC_3D
+    elif P.dim == 3:
         alg3 = algorithmic3d(P.n, P.pml, P.b)
         # dominant kernel: the tensor-core rank-256 Schur update (tcgen05, split TF32)
         tf32_peak = peaks["bf16_tflops"] * 0.5  # nominal dense tf32 : bf16 ratio (1.1 : 2.25 PFLOP/s)
@@ -838,6 +879,8 @@ def main():
     ap.add_argument("--layer-widths", default="",
                     help="BMIN:BMAX -- layer widths chosen from the velocity (at least BMIN columns, up to BMAX "
                          "where it jumps heavily) instead of uniform layers of b columns")
+    ap.add_argument("--slab-solver", choices=["block", "nd"], default="block",
+                    help="3D workloads: block elimination over the x2 planes, or nested dissection (Section 4)")
     ap.add_argument("--pml-aux", type=int, default=0,
                     help="width of the auxiliary PMLs between layers (default: the boundary PML width)")
     ap.add_argument("--workload", choices=["n1023", "n511x32", "n255x32", "n255x1", "n95_3d", "n47_3d_slab"], default="n1023",

@@ -66,6 +66,17 @@ extern "C" {
  * layer solves (slower applies).  Not available in 3D (ASP_ERR_UNSUPPORTED). */
 #define ASP_PREC_C64_SYM 2
 
+/* ---- solver of the 3D slab subproblems ---------------------------------- */
+/* block elimination over the x2 planes: n dense blocks of n*w unknowns per
+ * slab, each inverted (Gauss-Jordan, tensor-core updates for complex64)      */
+#define ASP_SLAB_BLOCK 0
+/* nested dissection (Section 4, Algorithms 3 and 4): the unknowns of a slab
+ * grouped along x3 into columns, the n x n grid of columns ordered by nested
+ * dissection, a multifrontal factorization with dense fronts (partial
+ * Gauss-Jordan with pivoting inside the fully summed rows); fewer flops and
+ * factor bytes than ASP_SLAB_BLOCK.  3D only.                                  */
+#define ASP_SLAB_ND 1
+
 /* Problem parameters (Section 2 and Section 3.1 notation).
  *   dim        spatial dimension (2 or 3)
  *   n          interior nodes per axis; h = 1/(n+1)
@@ -82,7 +93,8 @@ extern "C" {
  *   factor_prec ASP_PREC_C128, ASP_PREC_C64 or ASP_PREC_C64_SYM
  *   max_rhs    largest nrhs that later calls will pass (1..256); sizes the
  *              apply and Krylov workspaces
- *   restart    FGMRES restart length the workspace is sized for (1..64)       */
+ *   restart    FGMRES restart length the workspace is sized for (1..64)
+ *   slab_solver ASP_SLAB_BLOCK (0, the default) or ASP_SLAB_ND; 3D only       */
 typedef struct asp_params {
   int dim;
   int n;
@@ -94,6 +106,7 @@ typedef struct asp_params {
   int factor_prec;
   int max_rhs;
   int restart;
+  int slab_solver;
 } asp_params;
 
 typedef struct asp_handle asp_handle;
@@ -142,6 +155,18 @@ int asp_setup_layers(const asp_params* p, const int* widths, int nwidths, const 
  * ASP_ERR_INVALID.  Host-only; no device work. */
 int asp_layer_widths_from_velocity(const asp_params* p, const double* c, int b_min, int b_max, int* widths,
                                    int capacity);
+
+/* Host-only check of the nested-dissection plan (ASP_SLAB_ND) of an n x n
+ * grid of columns with w planes each (Section 4: unknowns grouped along x3,
+ * nested dissection of the column grid).  Fills up to `nstats` (<= 9) of:
+ * [0] tree nodes, [1] largest depth, [2] largest front (unknowns), [3] factor
+ * entries ([X; L] and P of every front), [4] stencil entries the fronts
+ * assemble, [5] nonzeros of the slab's 7-point operator, [6] couplings
+ * assembled more than once, [7] couplings never assembled, [8] complex
+ * multiply-adds of the fronts' Gauss-Jordan steps.  A valid plan has
+ * [4] == [5] and [6] == [7] == 0.  Returns ASP_ERR_INVALID for n < 1 or w < 1.
+ * No device work. */
+int asp_nd_plan_check(int n, int w, long long* stats, int nstats);
 
 /* Bytes of device memory asp_setup + asp_factor will hold for these
  * parameters (factors, transfer maps, apply and Krylov workspaces).  Pure

@@ -22,6 +22,9 @@ Modules and what they follow:
   each factored once by banded LU in the quasi-1D ordering (Algorithm 1).
 * :mod:`oracle.sweeping`   -- Algorithm 2 (accumulated boundary values, O(m)
   subproblem solves) and the naive O(m^2) superposition of Section 2.1.
+* :mod:`oracle.nested_dissection` -- Section 4's solver of the 3D slab
+  subproblems: unknowns grouped along x3, nested dissection of the column grid,
+  dense frontal matrices (pinned against a sparse direct solve).
 * :mod:`oracle.fgmres`     -- right-preconditioned flexible GMRES with restart,
   zero initial guess, modified Gram-Schmidt and Givens rotations (the Krylov
   solver of Section 3.2).

@@ -49,9 +49,13 @@ def _dev_vec(t, n: int, name: str, dim: int = 2):
 
 
 def make_params(n: int, omega: float, pml: int, b: int, pml_aux: int = 0, C: float = 20.0,
-                precision: str = "c128", max_rhs: int = 1, restart: int = 40, dim: int = 2) -> asp_params:
+                precision: str = "c128", max_rhs: int = 1, restart: int = 40, dim: int = 2,
+                slab_solver: str = "block") -> asp_params:
+    """``slab_solver`` (3D only): "block" (block elimination over the x2 planes)
+    or "nd" (nested dissection of the slab's column grid, Section 4)."""
     prec = {"c128": ASP_PREC_C128, "c64": ASP_PREC_C64, "c64sym": _lib.ASP_PREC_C64_SYM}[precision]
-    return asp_params(dim, n, float(omega), pml, pml_aux, b, float(C), prec, max_rhs, restart)
+    solver = {"block": _lib.ASP_SLAB_BLOCK, "nd": _lib.ASP_SLAB_ND}[slab_solver]
+    return asp_params(dim, n, float(omega), pml, pml_aux, b, float(C), prec, max_rhs, restart, solver)
 
 
 def _widths_arg(widths):

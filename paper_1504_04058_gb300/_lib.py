@@ -25,6 +25,8 @@ ASP_ERR_UNSUPPORTED = -8
 ASP_PREC_C128 = 0
 ASP_PREC_C64 = 1
 ASP_PREC_C64_SYM = 2
+ASP_SLAB_BLOCK = 0
+ASP_SLAB_ND = 1
 
 KIND_M, KIND_R, KIND_L = 0, 1, 2
 
@@ -35,7 +37,7 @@ EXPORTS = [
     "asp_gmres_solve", "asp_take_launch_count", "asp_set_phase_timing", "asp_phase_times",
     "asp_destroy", "asp_error_string", "asp_last_error_detail", "asp_residual_norms_noalloc",
     "asp_selftest_bounded_wait", "asp_setup_layers", "asp_footprint_bytes_layers", "asp_layer_widths_from_velocity",
-    "asp_autotune",
+    "asp_autotune", "asp_nd_plan_check",
 ]
 NOALLOC_MAX_N = 4096
 NOALLOC_MAX_RHS = 64
@@ -54,6 +56,7 @@ class asp_params(ctypes.Structure):
         ("factor_prec", ctypes.c_int),
         ("max_rhs", ctypes.c_int),
         ("restart", ctypes.c_int),
+        ("slab_solver", ctypes.c_int),
     ]
 
 
@@ -101,6 +104,7 @@ def load() -> ctypes.CDLL:
         "asp_gmres_solve": (I, [P, P, P, I, D, I, I, ctypes.POINTER(asp_solve_info), P]),
         "asp_take_launch_count": (ctypes.c_longlong, [P]),
         "asp_autotune": (I, [P, I, P, P, P]),
+        "asp_nd_plan_check": (I, [I, I, P, I]),
         "asp_set_phase_timing": (I, [P, I]),
         "asp_phase_times": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), I]),
         "asp_destroy": (V, [P]),

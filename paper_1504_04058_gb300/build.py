@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
 SOURCES = ["api.cu", "btfactor.cu", "btsolve_apply.cu", "btsolve_aux.cu", "chain.cu", "krylov.cu", "noalloc.cu",
-           "factor3d.cu", "solve3d.cu", "tcupdate.cu", "tmap_tc.cu"]
+           "factor3d.cu", "solve3d.cu", "tcupdate.cu", "tmap_tc.cu", "nd3d.cu"]
 
 
 def nvcc() -> str:

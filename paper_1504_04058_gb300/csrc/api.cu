@@ -171,6 +171,8 @@ bool valid(const asp_params* p, std::string* why, const std::vector<int>* widths
   }
   if (p->max_rhs < 1 || p->max_rhs > 256) { *why = "max_rhs out of range [1, 256]"; return false; }
   if (p->restart < 1 || p->restart > 64) { *why = "restart out of range [1, 64]"; return false; }
+  if (p->slab_solver != ASP_SLAB_BLOCK && p->slab_solver != ASP_SLAB_ND) { *why = "bad slab_solver"; return false; }
+  if (p->slab_solver == ASP_SLAB_ND && p->dim != 3) { *why = "slab_solver ASP_SLAB_ND is 3D only"; return false; }
   const int P = p->n + 2 - 2 * p->pml;
   if (!widths && P < p->b) { *why = "n too small for the PML width and layer width (need n >= 2*gamma + b - 2)"; return false; }
   const int ga = p->pml_aux ? p->pml_aux : p->pml;
@@ -238,9 +240,23 @@ bool supported(const asp_params* p, const Part& P, std::string* why, int sms) {
            " map rows per CTA on half of the SMs)";
     return false;
   }
-  if (p->dim == 3 && (long long)p->n * wmax > kMaxNb3) {
+  if (p->dim == 3 && p->slab_solver == ASP_SLAB_BLOCK && (long long)p->n * wmax > kMaxNb3) {
     *why = "3D block size n * (padded slab width) exceeds " + std::to_string(kMaxNb3);
     return false;
+  }
+  if (p->dim == 3 && p->slab_solver == ASP_SLAB_ND) {
+    // the nested-dissection solve stages a front's vector (4 right-hand sides) in shared memory
+    NdTree T;
+    std::string w2;
+    if (!nd_build_tree(p->n, T, &w2)) { *why = w2; return false; }
+    int ncmax = 0;
+    for (int t = 0; t < T.nn; ++t) ncmax = std::max(ncmax, T.nc(t));
+    const long long esz = p->factor_prec == ASP_PREC_C128 ? 16 : 8;
+    if ((long long)ncmax * wmax * 4 * esz > 200 * 1024) {
+      *why = "nested-dissection front of " + std::to_string((long long)ncmax * wmax) +
+             " unknowns exceeds the solve's shared-memory stage";
+      return false;
+    }
   }
   return true;
 }
@@ -281,10 +297,35 @@ Sizes sizes_for3(const asp_params* p, const Part& P, int num_sms) {
   };
   long long tc_rows_M = 0, tc_rows_RL = 0;
   auto padr = [&](int lo, int hi) { return (long long)((n * (hi - lo + 1) + 127) / 128 * 128); };
-  for (int q = 1; q <= P.m; ++q) { addslab(P.m_lo[q], P.m_hi[q], false); tc_rows_M += padr(P.m_lo[q], P.m_hi[q]); }
-  for (int q = 2; q <= P.m; ++q) { addslab(P.alpha[q], P.m_hi[q], true); tc_rows_RL += padr(P.alpha[q], P.m_hi[q]); }
-  for (int q = 1; q <= P.m - 1; ++q) { addslab(P.m_lo[q], P.beta[q], true); tc_rows_RL += padr(P.m_lo[q], P.beta[q]); }
-  if (p->factor_prec == ASP_PREC_C64) Z.tc_floats = tc_group_floats(tc_rows_M) + tc_group_floats(tc_rows_RL);
+  std::vector<int> sw, sk;  // slab widths and kinds in slab order
+  for (int q = 1; q <= P.m; ++q) {
+    addslab(P.m_lo[q], P.m_hi[q], false); tc_rows_M += padr(P.m_lo[q], P.m_hi[q]);
+    sw.push_back(P.m_hi[q] - P.m_lo[q] + 1); sk.push_back(KIND_M);
+  }
+  for (int q = 2; q <= P.m; ++q) {
+    addslab(P.alpha[q], P.m_hi[q], true); tc_rows_RL += padr(P.alpha[q], P.m_hi[q]);
+    sw.push_back(P.m_hi[q] - P.alpha[q] + 1); sk.push_back(KIND_R);
+  }
+  for (int q = 1; q <= P.m - 1; ++q) {
+    addslab(P.m_lo[q], P.beta[q], true); tc_rows_RL += padr(P.m_lo[q], P.beta[q]);
+    sw.push_back(P.beta[q] - P.m_lo[q] + 1); sk.push_back(KIND_L);
+  }
+  size_t nd_extra = 0;
+  if (p->slab_solver == ASP_SLAB_ND) {
+    // nested dissection: its factors, work and pivots replace the block path's;
+    // no tensor-core operand area
+    NdTree T;
+    std::string why;
+    nd_build_tree(n, T, &why);
+    const NdSizes ND = nd_sizes(T, sw, sk, (int)mr, (int)Z.esz, nullptr);
+    Z.W_elems = (size_t)ND.factor_elems;
+    Z.A_elems = (size_t)ND.work_elems;
+    Z.piv_elems = (size_t)ND.piv_ints;
+    nd_extra = (size_t)ND.zu_elems * Z.esz + (size_t)ND.nfronts * (sizeof(NdFront) + sizeof(Slab) + sizeof(int)) +
+               (T.node.size() + T.cols.size() + T.cmap.size() + T.nn) * sizeof(int);
+  } else if (p->factor_prec == ASP_PREC_C64) {
+    Z.tc_floats = tc_group_floats(tc_rows_M) + tc_group_floats(tc_rows_RL);
+  }
   const long long R = p->restart;
   size_t n2, nd, ni;
   const size_t kst = krylov_state_bytes(p->restart, p->max_rhs, &n2, &nd, &ni);
@@ -295,6 +336,7 @@ Sizes sizes_for3(const asp_params* p, const Part& P, int num_sms) {
   bytes += (size_t)n * 2 * Z.esz;  // s1, 1/s1
   bytes += (Z.W_elems + Z.A_elems + Z.z3_elems) * Z.esz + Z.piv_elems * sizeof(int);
   bytes += Z.tc_floats * sizeof(float);
+  bytes += nd_extra;
   bytes += (size_t)Z.N * mr * Z.esz * (3 + (Z.esz == 8 ? 1 : 0));                 // uM uR uL (+ r_lo)
   bytes += (size_t)(2 * R + 2) * Z.N * mr * sizeof(double2);                        // V, Z, work
   bytes += (size_t)num_sms * 4 * 9 * mr * sizeof(double2);                          // dot partials
@@ -873,6 +915,7 @@ void asp_destroy(asp_handle* hd) {
     caches().erase(&H);
   }
   release_jobs3(&H);
+  nd_release(H);
   for (auto& g : H.fgroups) {
     tc_group_release(g.tc);
     if (g.stream) cudaStreamDestroy(g.stream);
@@ -945,6 +988,7 @@ int asp_setup_layers(const asp_params* pin, const int* widths, int nwidths, cons
   H.x_lo = P.x_lo; H.x_hi = P.x_hi; H.alpha = P.alpha; H.beta = P.beta;
   const int m = H.m;
   H.packed = packed;
+  H.nd = p->dim == 3 && p->slab_solver == ASP_SLAB_ND;
   Sizes Z = sizes_for(p, P, sms, packed);
 
   // ---- global stencil weights (same boundary PML on x1 and x2)
@@ -1006,7 +1050,9 @@ int asp_setup_layers(const asp_params* pin, const int* widths, int nwidths, cons
       if (kind == KIND_R) { S.src_plane = H.x_hi[q - 1] - 1; S.src_sweep = (q - 1 >= 2) ? 1 : 0; }
       if (kind == KIND_L) { S.src_plane = H.x_lo[q + 1] - 1; S.src_sweep = (q + 1 <= m - 1) ? 1 : 0; }
       S.woff = woff; woff += (long long)n * S.nb * S.ld;
+      S.np = S.nb;
       S.aoff = aoff; aoff += slab_work_elems(S.nb, S.ld);
+      S.zbo = 2LL * S.nb * S.ld;
       S.poff = poff; poff += 3LL * S.nb;
       S.zoff = zoff; zoff += (long long)n * S.nb * p->max_rhs;
       if (kind == KIND_M) H.nbmaxM = std::max(H.nbmaxM, S.nb);
@@ -1060,6 +1106,11 @@ int asp_setup_layers(const asp_params* pin, const int* widths, int nwidths, cons
     rhoL[q] = sratio(pr, H.x_lo[q], H.beta[q]);
   }
   H.W_elems = (size_t)woff;
+  if (H.nd) {  // nd_setup plans and allocates the factors, work and pivots
+    H.W_elems = 0;
+    aoff = 0;
+    poff = 0;
+  }
   // transfer maps T_p^R, T_p^L for p = 2..m-1 (2D only)
   H.toffR.assign(m + 1, 0); H.toffL.assign(m + 1, 0);
   H.ldT = (n + 1) & ~1;
@@ -1128,7 +1179,7 @@ int asp_setup_layers(const asp_params* pin, const int* widths, int nwidths, cons
     dal(&H.A3, (size_t)aoff * esz);
     dal((void**)&H.piv3, (size_t)poff * sizeof(int));
     dal(&H.z3, (size_t)zoff * esz);
-    if (H.prec == ASP_PREC_C64) dal((void**)&H.tc_area, Z.tc_floats * sizeof(float));
+    if (H.prec == ASP_PREC_C64 && !H.nd) dal((void**)&H.tc_area, Z.tc_floats * sizeof(float));
   }
   if (H.prec == ASP_PREC_C64) dal(&H.r_lo, (size_t)N * mr * esz);
   dal(&H.uM, (size_t)N * mr * esz);
@@ -1196,7 +1247,15 @@ int asp_setup_layers(const asp_params* pin, const int* widths, int nwidths, cons
         if (up && cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess) up = false;
       }
     }
-    if (up && H.prec == ASP_PREC_C64) {
+    if (up && H.nd) {
+      const int rc = nd_setup(H);
+      if (rc != ASP_OK) {
+        const std::string why = asp_last_error_detail();
+        asp_destroy(hd);
+        return fail(rc, why);
+      }
+    }
+    if (up && H.prec == ASP_PREC_C64 && !H.nd) {
       // operand rows of the tensor-core update, per factor group in list order
       long long off = 0;
       int rc = ASP_OK;
@@ -1281,7 +1340,7 @@ int asp_factor(asp_handle* hd, void* stream) {
   Handle& H = hd->h;
   cudaStream_t s = (cudaStream_t)stream;
   if (H.dim == 3) {
-    int rc3 = factor3d(H, s);
+    int rc3 = H.nd ? nd_factor(H, s) : factor3d(H, s);
     if (rc3 != ASP_OK) return rc3;
     rc3 = check_err(H, s, "factor");
     if (rc3 != ASP_OK) return rc3;

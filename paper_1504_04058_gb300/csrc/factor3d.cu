@@ -63,11 +63,11 @@ template <typename R> __device__ __forceinline__ Cx<R>* work(const Slab3Params& 
 }
 // outer block's pivot rows, kKO x ld
 template <typename R> __device__ __forceinline__ Cx<R>* zbig(const Slab3Params& P, const Slab& S) {
-  return reinterpret_cast<Cx<R>*>(P.A) + S.aoff + 2LL * S.nb * S.ld;
+  return reinterpret_cast<Cx<R>*>(P.A) + S.aoff + S.zbo;
 }
 // inner panel's pivot rows inside the outer block, kPW x kKO
 template <typename R> __device__ __forceinline__ Cx<R>* zpan(const Slab3Params& P, const Slab& S) {
-  return reinterpret_cast<Cx<R>*>(P.A) + S.aoff + 2LL * S.nb * S.ld + (long long)kKO * S.ld;
+  return reinterpret_cast<Cx<R>*>(P.A) + S.aoff + S.zbo + (long long)kKO * S.ld;
 }
 
 // ------------------------------------------------------------ form / store
@@ -141,9 +141,9 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
   const int CL = (int)cluster.num_blocks();
   const int sidx = P.list[blockIdx.y];
   const Slab S = P.slabs[sidx];
-  const int nb = S.nb, ld = S.ld;
-  if (c0 >= nb) return;  // the whole cluster leaves together
-  const int pw = min(kPW, nb - c0);
+  const int nb = S.nb, ld = S.ld, np = S.np;
+  if (c0 >= np) return;  // the whole cluster leaves together
+  const int pw = min(kPW, np - c0);
   const int rpc = (nb + CL - 1) / CL;
   const int row0 = q * rpc;
   const int nrows = max(0, min(nb, row0 + rpc) - row0);
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
     R best = R(-1);
     int bi = INT_MAX;
     for (int l = wlo + lane; l < whi; l += 32) {
-      if (rstep[l] < 0) {
+      if (rstep[l] < 0 && row0 + l < np) {  // pivots come from the first np rows only
         const C v = Ps[l * kLDP + t];
         const R a = v.x * v.x + v.y * v.y;
         if (a > best) { best = a; bi = row0 + l; }  // rows ascend along a lane: ties keep the first
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_kernel(Slab3Params P, 
   // pivot rows inside the outer block, outside the panel (untouched here), for
   // the inner update; rows t = q, q + CL, ... on this CTA
   {
-    const int C1 = min(C0 + kKO, nb);
+    const int C1 = min(C0 + kKO, np);
     Cx<R>* zp = zpan<R>(P, S);
     for (int t = q; t < pw; t += CL) {
       const Cx<R>* src = A + (long long)pivs[t] * ld;
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(256) gather_kernel(Slab3Params P, int C0, int 
   const Slab S = P.slabs[P.list[blockIdx.y]];
   const int nb = S.nb, ld = S.ld;
   const int t = blockIdx.x;
-  if (C0 >= nb || t >= min(kKO, nb - C0)) return;
+  if (C0 >= S.np || t >= min(kKO, S.np - C0)) return;
   const int* piv_row = P.piv + S.poff;
   const int r = min(max(piv_row[C0 + t], 0), nb - 1);
   const Cx<R>* src = work<R>(P, S, buf) + (long long)r * ld;
@@ -319,12 +319,12 @@ template <typename R>
 __global__ void __launch_bounds__(kUpdThreads) update_kernel(Slab3Params P, int C0, int c0, int buf, int big) {
   using C = Cx<R>;
   const Slab S = P.slabs[P.list[blockIdx.z]];
-  const int nb = S.nb, ld = S.ld;
+  const int nb = S.nb, ld = S.ld, np = S.np;
   const int a0 = big ? C0 : c0;
-  if (a0 >= nb) return;
-  const int K = big ? min(kKO, nb - C0) : min(kPW, nb - c0);
+  if (a0 >= np) return;
+  const int K = big ? min(kKO, np - C0) : min(kPW, np - c0);
   const int jlo = big ? 0 : C0;
-  const int jhi = big ? nb : min(C0 + kKO, nb);
+  const int jhi = big ? nb : min(C0 + kKO, np);
   const int j0 = jlo + blockIdx.x * kBN, i0 = blockIdx.y * kBM;
   if (j0 >= jhi || i0 >= nb) return;
   if (j0 >= a0 && j0 + kBN <= a0 + K) return;  // the tile lies inside the eliminated columns
@@ -397,36 +397,28 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(Slab3Params P, int 
 }
 
 // ------------------------------------------------------------------ driver
-// One factor group (slabs of one kind of subproblem sharing a stream).  setup()
-// sizes the launches once; block(k) enqueues the store of W_{k-1} and, for
-// k < n, the inversion of S_k.  The groups' blocks are enqueued alternately, so
-// that each stream always has queued work and the groups overlap on the GPU
-// (enqueued one group after the other, the host would block on the full launch
-// queue of the first group until that group was nearly done).
-template <typename R> struct Factor3Group {
+// The Gauss-Jordan steps on columns [0, np) of every matrix of one list (slabs
+// of one factor group, or nested-dissection fronts of one level): setup()
+// sizes the launches once, run(buf) enqueues the panels and updates.
+template <typename R> struct GjRun {
   Slab3Params P{};
   cudaLaunchConfig_t pc{};
   cudaLaunchAttribute pattr[1];
   dim3 igrid, bgrid;
   size_t usmem = 0;
-  int nbmax = 0, nlist = 0;
+  int nbmax = 0, npmax = 0, nlist = 0;
   const TcGroup* tc = nullptr;
   cudaStream_t s = nullptr;
 
-  cudaError_t setup(Handle& H, const int* d_list, int nlist_, int nbmax_, const TcGroup* tc_, cudaStream_t s_) {
-    nlist = nlist_;
+  cudaError_t setup(const Slab3Params& base, int nbmax_, int npmax_, const TcGroup* tc_, int num_sms,
+                    cudaStream_t s_) {
+    P = base;
+    nlist = base.nlist;
     nbmax = nbmax_;
+    npmax = npmax_;
     tc = tc_;
     s = s_;
     if (nlist <= 0) return cudaSuccess;
-    P.slabs = H.d_slabs;
-    P.list = d_list;
-    P.nlist = nlist;
-    P.n = H.n;
-    P.W = H.W;
-    P.A = H.A3;
-    P.piv = H.piv3;
-    P.err = H.err;
     const size_t esz = sizeof(Cx<R>);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -434,10 +426,10 @@ template <typename R> struct Factor3Group {
     const size_t static_bytes = 12288;  // the kernel's static shared arrays, with room
     const int rows_cap = (int)(((size_t)optin - static_bytes) / (kLDP * esz + sizeof(int)));
     // about 512 rows per CTA (the per-step row updates are issue-bound) while
-    // all clusters of the group fit in one wave (one CTA per SM), and at least
+    // all clusters of the list fit in one wave (one CTA per SM), and at least
     // as many CTAs as shared memory requires
     const int by_rows = std::min(kMaxCluster, (nbmax + 511) / 512);
-    const int by_sms = std::max(1, H.num_sms / std::max(nlist, 1));
+    const int by_sms = std::max(1, num_sms / std::max(nlist, 1));
     int CL = std::max((nbmax + rows_cap - 1) / rows_cap, std::min(by_rows, by_sms));
     if (CL < 1) CL = 1;
     if (CL > kMaxCluster) return cudaErrorInvalidValue;
@@ -466,18 +458,12 @@ template <typename R> struct Factor3Group {
     return cudaSuccess;
   }
 
-  cudaError_t block(Handle& H, const FactorCoefs<R>& F, int k) {
+  cudaError_t run(Handle& H, int buf) {
     if (nlist <= 0) return cudaSuccess;
-    const int n = H.n;
-    const int store = k > 0, form = k < n;
-    form_store_kernel<R><<<dim3(nbmax, nlist), 256, 0, s>>>(P, F, k, (k + 1) & 1, store, form);
-    H.launches += 1;
-    if (!form) return cudaGetLastError();
-    const int buf = k & 1;
     pc.attrs = pattr;  // the struct may have moved since setup
     cudaError_t e;
-    for (int C0 = 0; C0 < nbmax; C0 += kKO) {
-      for (int c0 = C0; c0 < std::min(C0 + kKO, nbmax); c0 += kPW) {
+    for (int C0 = 0; C0 < npmax; C0 += kKO) {
+      for (int c0 = C0; c0 < std::min(C0 + kKO, npmax); c0 += kPW) {
         e = cudaLaunchKernelEx(&pc, panel_kernel<R>, P, c0, C0, buf);
         if (e != cudaSuccess) return e;
         update_kernel<R><<<igrid, kUpdThreads, usmem, s>>>(P, C0, c0, buf, 0);
@@ -495,6 +481,44 @@ template <typename R> struct Factor3Group {
       H.launches += 2;
     }
     return cudaGetLastError();
+  }
+};
+
+// One factor group (slabs of one kind of subproblem sharing a stream).
+// block(k) enqueues the store of W_{k-1} and, for k < n, the inversion of S_k.
+// The groups' blocks are enqueued alternately, so that each stream always has
+// queued work and the groups overlap on the GPU (enqueued one group after the
+// other, the host would block on the full launch queue of the first group
+// until that group was nearly done).
+template <typename R> struct Factor3Group {
+  GjRun<R> gj;
+  int nbmax = 0, nlist = 0;
+  cudaStream_t s = nullptr;
+
+  cudaError_t setup(Handle& H, const int* d_list, int nlist_, int nbmax_, const TcGroup* tc_, cudaStream_t s_) {
+    nlist = nlist_;
+    nbmax = nbmax_;
+    s = s_;
+    Slab3Params P{};
+    P.slabs = H.d_slabs;
+    P.list = d_list;
+    P.nlist = nlist;
+    P.n = H.n;
+    P.W = H.W;
+    P.A = H.A3;
+    P.piv = H.piv3;
+    P.err = H.err;
+    return gj.setup(P, nbmax, nbmax, tc_, H.num_sms, s);
+  }
+
+  cudaError_t block(Handle& H, const FactorCoefs<R>& F, int k) {
+    if (nlist <= 0) return cudaSuccess;
+    const int n = H.n;
+    const int store = k > 0, form = k < n;
+    form_store_kernel<R><<<dim3(nbmax, nlist), 256, 0, s>>>(gj.P, F, k, (k + 1) & 1, store, form);
+    H.launches += 1;
+    if (!form) return cudaGetLastError();
+    return gj.run(H, k & 1);
   }
 };
 
@@ -517,6 +541,17 @@ template <typename R> cudaError_t factor_groups(Handle& H, const FactorCoefs<R>&
 }
 
 }  // namespace
+
+cudaError_t gj_partial(Handle& H, const Slab3Params& P, int nbmax, int npmax, const TcGroup* tc, cudaStream_t s) {
+  if (H.prec == ASP_PREC_C128) {
+    GjRun<double> g;
+    cudaError_t e = g.setup(P, nbmax, npmax, nullptr, H.num_sms, s);
+    return e != cudaSuccess ? e : g.run(H, 0);
+  }
+  GjRun<float> g;
+  cudaError_t e = g.setup(P, nbmax, npmax, tc, H.num_sms, s);
+  return e != cudaSuccess ? e : g.run(H, 0);
+}
 
 // Factors every slab: each factor group (the M slabs; the R and L slabs) on its
 // own stream, forked from and joined back into the caller's.

@@ -157,10 +157,12 @@ struct Slab {
   int prof;           // offset of its sweep-axis coefficients (SweepCoef table)
   int nb;             // block size n*w
   int ld;             // row stride of a stored block (nb rounded up to 4)
+  int np;             // Gauss-Jordan steps: columns [0, np), pivots from rows [0, np) (nb: a full inversion)
   int src_plane;      // FILL modes: 0-based global x3 plane of the incoming trace
   int src_sweep;      // FILL modes: 1 if the trace includes the sweep field there
   long long woff;     // element offset of block 0 of its factor (n blocks of nb x ld)
   long long aoff;     // element offset of its factor-time work area (slab_work_elems)
+  long long zbo;      // offset of the work area's pivot-row buffers from aoff (2*nb*ld for a slab)
   long long poff;     // int offset of its pivot tables (3 * nb)
   long long zoff;     // element offset of its solve scratch (n * nb * max_rhs)
 };
@@ -191,6 +193,50 @@ struct Slab3Params {
   int* piv;           // pivot tables: piv_row[nb], col_of_row[nb], row_step[nb]
   int* err;
 };
+
+// ---- 3D slab subproblems by nested dissection (nd3d.cu; Section 4: the
+// unknowns of a slab are grouped along x3 into columns, and the n x n grid of
+// columns is ordered by nested dissection).  The separator tree depends on n
+// only; a slab of width w has w unknowns per column.  Node fields, kNdNodeInts
+// ints per node: I columns, B columns, offset of its columns (I then B, each
+// ascending by id i2*n + i1), offset of its child map (the parent front column
+// position of each of its B columns; -1 for the root), first and second child
+// (-1: none), depth.
+constexpr int kNdNodeInts = 8;
+enum NdNodeField : int { ND_NCI = 0, ND_NCB, ND_OFFC, ND_OFFM, ND_C0, ND_C1, ND_DEPTH };
+constexpr int kNdLeafCols = 8;   // a region of at most this many columns is a leaf
+
+struct NdTree {
+  int n = 0, nn = 0, maxdepth = 0;
+  std::vector<int> node;   // nn * kNdNodeInts
+  std::vector<int> cols;
+  std::vector<int> cmap;
+  std::vector<std::vector<int>> at_depth;
+  int nc(int t) const { return node[t * kNdNodeInts + ND_NCI] + node[t * kNdNodeInts + ND_NCB]; }
+};
+
+// One node of one slab: front f = slab_rank * nn + node, with slab_rank the
+// slab's position in the handle's slab list.
+struct NdFront {
+  int slab, node, w, lds, ldb, pad;
+  long long xl;   // factor offset of [X; L] (ns x lds): X = F_II^-1, L = F_BI X
+  long long pf;   // factor offset of P = X F_IB (s x ldb)
+  long long zu;   // solve scratch: z (s rows) then u (B rows), max_rhs columns
+};
+
+struct NdSizes {
+  long long factor_elems = 0, work_elems = 0, piv_ints = 0, zu_elems = 0, nfronts = 0;
+  int max_front = 0;
+};
+// Builds the separator tree of an n x n grid of columns; returns false (with
+// *why) if a child column is missing from its parent's front.
+bool nd_build_tree(int n, NdTree& T, std::string* why);
+// Factor, work, pivot and scratch sizes of the nested-dissection path for the
+// given slab widths and kinds (in slab order) and factor element size;
+// chunk[i] receives the factor chunk of slab i within its group (the slabs of
+// one chunk are factored together).
+NdSizes nd_sizes(const NdTree& T, const std::vector<int>& widths, const std::vector<int>& kinds, int max_rhs,
+                 int esz, std::vector<int>* chunk);
 
 // Operand area and tensor maps of the tensor-core update (tcupdate.cu) for
 // one slab group.
@@ -259,6 +305,13 @@ cudaError_t launch_sum3(const void* a, const void* b, const void* c, double2* z,
                         int r_from, int l_below, int prec, cudaStream_t s);
 cudaError_t launch_matvec3d(const Handle& H, const double2* x, double2* y, int nrhs, cudaStream_t s);
 int factor3d(Handle& H, cudaStream_t s);
+// the Gauss-Jordan steps on columns [0, np) of every matrix of P.list (factor3d.cu)
+cudaError_t gj_partial(Handle& H, const Slab3Params& P, int nbmax, int npmax, const TcGroup* tc, cudaStream_t s);
+int nd_setup(Handle& H);
+int nd_factor(Handle& H, cudaStream_t s);
+void nd_release(Handle& H);
+// the slab solves of one batch (P.jobs) by the nested-dissection factors
+cudaError_t nd_solve(Handle& H, const Solve3Params& P, int NR, int nbmax, cudaStream_t s);
 int apply3d(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_t s);
 int subsolve3d(Handle& H, int slab, const double2* g, double2* v, int nrhs, cudaStream_t s);
 void release_jobs3(const Handle* H);
@@ -368,6 +421,22 @@ struct Handle {
     cudaEvent_t done = nullptr;
   };
   std::vector<FGroup> fgroups;
+
+  // nested dissection (slab_solver == ASP_SLAB_ND)
+  bool nd = false;
+  NdTree ndt;
+  int* d_ndtab = nullptr;       // node table, columns, child maps
+  NdFront* d_ndf = nullptr;     // every front [slab * nn + node]
+  Slab* d_ndslab = nullptr;     // engine view of every front (nb = front size, np = s)
+  int* d_ndlist = nullptr;      // front lists per (chunk, depth)
+  struct NdLevel { int off = 0, count = 0, nbmax = 0, npmax = 0, bmax = 0, depth = 0, group = 0; };
+  std::vector<NdLevel> nd_levels;   // in factor order: per group, per chunk, deepest depth first
+  std::vector<NdFront> ndf_host;
+  void* nd_zu = nullptr;        // solve scratch of every front
+  int nd_maxfront = 0;
+  // per depth: offset of its node list in d_ndtab, and the largest column
+  // counts (I + B, I, B) of its nodes
+  std::vector<int> nd_dep_off, nd_dep_nc, nd_dep_nci, nd_dep_ncb;
 
   // second stream for work that overlaps the caller's stream (factor time)
   cudaStream_t aux = nullptr;

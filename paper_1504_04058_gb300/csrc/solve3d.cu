@@ -463,7 +463,8 @@ int apply3d(Handle& H, const double2* r, double2* z, int nrhs, cudaStream_t s) {
     P.nitems = L.nitems;
     const bool first = l == 0;
     PhaseTok tk = phase_begin(H, first ? PH_EMBED : PH_FILL, s);
-    cudaError_t ce = launch_solve(H, P, J->NR, first ? H.nbmaxM : H.nbmaxRL, s);
+    const int nbmax = first ? H.nbmaxM : H.nbmaxRL;
+    cudaError_t ce = H.nd ? nd_solve(H, P, J->NR, nbmax, s) : launch_solve(H, P, J->NR, nbmax, s);
     phase_end(H, tk, s);
     if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("3D slab-solve launch: ") + cudaGetErrorString(ce));
   }
@@ -495,7 +496,7 @@ int subsolve3d(Handle& H, int slab, const double2* g, double2* v, int nrhs, cuda
   P.jobs = J->d + L.first;
   P.njobs = L.count;
   P.nitems = L.nitems;
-  cudaError_t ce = launch_solve(H, P, J->NR, S.nb, s);
+  cudaError_t ce = H.nd ? nd_solve(H, P, J->NR, S.nb, s) : launch_solve(H, P, J->NR, S.nb, s);
   if (ce != cudaSuccess) return fail(ASP_ERR_CUDA, std::string("3D subproblem launch: ") + cudaGetErrorString(ce));
   return ASP_OK;
 }

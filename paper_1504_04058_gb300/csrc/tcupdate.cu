@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(Slab3Params P, const long 
                                                       float* ahi, float* alo, float* bhi, float* blo) {
   const Slab S = P.slabs[P.list[blockIdx.y]];
   const int nb = S.nb, ld = S.ld;
-  if (C0 >= nb) return;
-  const int K = min(kSlabOuter, nb - C0);
+  if (C0 >= S.np) return;
+  const int K = min(kSlabOuter, S.np - C0);
   const int nbpad = (nb + kTM - 1) / kTM * kTM;
   const int tiles_j = nbpad / 32;  // this slab's tiles; grid.x covers the largest slab's
   const int tu = blockIdx.x / tiles_j, tj = blockIdx.x - tu * tiles_j;  // tu < kSlabOuter / 32
@@ -214,11 +214,11 @@ __device__ __forceinline__ TcTile tc_tile(const Slab3Params& P, const long long*
   T.ld = S.ld;
   T.i0 = by * kTM;
   T.j0 = bx * kTNc;
-  T.K = min(kSlabOuter, S.nb - C0);
+  T.K = min(kSlabOuter, S.np - C0);
   T.ra = rowA[z];
   T.aoff = S.aoff;
   T.poff = (int)S.poff;
-  T.valid = C0 < S.nb && T.j0 < S.nb && T.i0 < S.nb && !(T.j0 >= C0 && T.j0 + kTNc <= C0 + T.K);
+  T.valid = C0 < S.np && T.j0 < S.nb && T.i0 < S.nb && !(T.j0 >= C0 && T.j0 + kTNc <= C0 + T.K);
   return T;
 }
 

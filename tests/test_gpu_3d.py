@@ -7,7 +7,10 @@ path differs from the oracle only in the order of rounding; the complex64 path
 rounds factors and applies to FP32).  The 95^3 workload is too large for the
 oracle's banded LU, so it is checked by properties that hold at any size: the
 residual of slab solves against the assembled slab operator, and the FP64 true
-residual of the FGMRES solution.
+residual of the FGMRES solution.  Both slab solvers run every case: block
+elimination over the x2 planes ("block") and nested dissection of the slab's
+column grid ("nd", Section 4); both are exact, so they share the oracle and the
+tolerances.
 """
 import math
 
@@ -58,10 +61,13 @@ def small3(name):
     return W.small_problem(3, n, om, g, b, vel, nrhs=R, pml_aux=ga)
 
 
-def handle3(P, precision="c128", max_rhs=None, restart=40):
+SOLVERS = ["block", "nd"]
+
+
+def handle3(P, precision="c128", max_rhs=None, restart=40, solver="block"):
     import paper_1504_04058_gb300 as asp
     prm = asp.make_params(P.n, P.omega, P.pml, P.b, pml_aux=P.pml_aux or 0, C=P.C, precision=precision,
-                          max_rhs=max_rhs or P.nrhs, restart=restart, dim=3)
+                          max_rhs=max_rhs or P.nrhs, restart=restart, dim=3, slab_solver=solver)
     h = asp.asp_setup(P.c, prm)
     h.factor()
     return h
@@ -83,13 +89,15 @@ def test_matvec3d_matches_oracle(name):
     assert emax(y, yo) <= 1e-13, (emax(y, yo), rel(y, yo))
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("precision,tol", [("c128", 1e-11), ("c64", 2e-4)])
 @pytest.mark.parametrize("name", ["ragged_bump", "two_layers", "thin_aux", "wide_blocks"])
-def test_slab_solves_match_oracle(name, precision, tol):
-    """Every slab: GPU block-inverse solve vs the oracle's banded LU."""
+def test_slab_solves_match_oracle(name, precision, tol, solver):
+    """Every slab: GPU slab solve (block inverses or nested dissection) vs the
+    oracle's banded LU."""
     import paper_1504_04058_gb300 as asp
     P = small3(name)
-    h = handle3(P, precision, max_rhs=3)
+    h = handle3(P, precision, max_rhs=3, solver=solver)
     part = partition.make_partition(P.n, P.pml, P.b, P.pml_aux)
     rng = np.random.default_rng(1)
     worst = 0.0
@@ -107,11 +115,12 @@ def test_slab_solves_match_oracle(name, precision, tol):
     assert worst <= tol, worst
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4)])
 @pytest.mark.parametrize("name", list(SMALL3))
-def test_apply3d_matches_oracle(name, precision, tol):
+def test_apply3d_matches_oracle(name, precision, tol, solver):
     P = small3(name)
-    h = handle3(P, precision)
+    h = handle3(P, precision, solver=solver)
     z = host(h.apply_preconditioner(dev(P.f)))
     zo = oracle_pc3(P).apply(P.f)
     assert emax(z, zo) <= tol, (emax(z, zo), rel(z, zo))
@@ -126,14 +135,15 @@ def test_apply3d_right_hand_sides_independent():
         assert emax(z1[..., 0], z_all[..., r], single=True) <= 1e-12, rel(z1[..., 0], z_all[..., r])
 
 
-def test_fgmres3d_fp64_parity_and_iteration_counts():
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_fgmres3d_fp64_parity_and_iteration_counts(solver):
     P = W.small_problem(3, 19, 4 * math.pi, 3, 3, "bump", nrhs=2)
     pc = oracle_pc3(P)
     A = operator.helmholtz_matrix(3, P.n, P.omega, P.c, P.pml, P.C)
     uo, itso, _ = fgmres.solve(pc, A, P.f, tol=P.tol, restart=P.restart)
     k = int(itso.max())
     uk, _, _ = fgmres.solve(pc, A, P.f, tol=P.tol, restart=P.restart, fixed_iters=k)
-    h = handle3(P, "c128")
+    h = handle3(P, "c128", solver=solver)
     ug, _ = h.gmres_solve(dev(P.f), tol=0.0, maxit=k)
     assert emax(host(ug), uk) <= 1e-9, (emax(host(ug), uk), rel(host(ug), uk))
     ug, info = h.gmres_solve(dev(P.f), tol=P.tol, maxit=200)
@@ -156,13 +166,14 @@ def test_fgmres3d_c64_reaches_fp64_tolerance():
         assert np.linalg.norm(fr - A @ u[..., r].reshape(-1)) / np.linalg.norm(fr) <= P.tol
 
 
-def test_3d_n95_workload_properties():
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_3d_n95_workload_properties(solver):
     """The 95^3 workload (complex64 factors): slab solves leave a small residual
     against the assembled slab operator, and FGMRES reaches the FP64 true
     residual 1e-6."""
     import paper_1504_04058_gb300 as asp
     P = W.problem_3d_n95_bump()
-    h = handle3(P, "c64", max_rhs=1)
+    h = handle3(P, "c64", max_rhs=1, solver=solver)
     part = partition.make_partition(P.n, P.pml, P.b, None)
     rng = np.random.default_rng(3)
     for kind, code, p in (("M", asp.KIND_M, 1), ("M", asp.KIND_M, part.m // 2), ("R", asp.KIND_R, part.m),
@@ -187,3 +198,24 @@ def test_apply3d_wave_packet_sources():
     z = host(h.apply_preconditioner(dev(P.f)))
     zo = oracle_pc3(P).apply(P.f)
     assert emax(z, zo) <= 1e-10, (emax(z, zo), rel(z, zo))
+
+
+@pytest.mark.parametrize("name", ["ragged_bump", "wide_blocks", "five_rhs"])
+def test_nested_dissection_equals_block_elimination(name):
+    """Both slab solvers are exact, so their complex128 applies agree to rounding."""
+    P = small3(name)
+    zb = host(handle3(P, "c128", solver="block").apply_preconditioner(dev(P.f)))
+    zn = host(handle3(P, "c128", solver="nd").apply_preconditioner(dev(P.f)))
+    assert emax(zn, zb) <= 1e-11, (emax(zn, zb), rel(zn, zb))
+
+
+def test_nested_dissection_refactor_and_reuse():
+    """A second factorization on the same handle (the work area and pivot tables
+    reused) gives the same apply, and two applies in a row agree."""
+    P = small3("wide_blocks")
+    h = handle3(P, "c128", solver="nd")
+    z1 = host(h.apply_preconditioner(dev(P.f)))
+    h.factor()
+    z2 = host(h.apply_preconditioner(dev(P.f)))
+    z3 = host(h.apply_preconditioner(dev(P.f)))
+    assert emax(z2, z1) <= 1e-14 and emax(z3, z2) == 0.0

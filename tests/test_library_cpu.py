@@ -270,3 +270,68 @@ def test_footprint_with_explicit_widths(lib):
     wider = [8] * (P // 8 - 1) + [8 + P - 8 * (P // 8)]
     f1 = asp.asp_footprint_bytes(prm, widths=wider)
     assert f1 > 0 and f1 != f0
+
+
+def _nd_stats(lib, n, w):
+    st = (ctypes.c_longlong * 8)()
+    assert lib.asp_nd_plan_check(n, w, st, 8) == 0
+    return list(st)
+
+
+@pytest.mark.parametrize("n,w", [(3, 1), (5, 2), (8, 1), (10, 3), (15, 4), (31, 5), (47, 9), (95, 18)])
+def test_nested_dissection_plan_assembles_every_coupling_once(lib, n, w):
+    """Every directed stencil coupling of an n x n x w slab is assembled at
+    exactly one front (Section 4's nested dissection of the column grid): the
+    count equals the 7-point operator's nonzeros, none twice, none missing."""
+    nodes, depth, front, factor, assembled, nnz, dup, miss = _nd_stats(lib, n, w)
+    assert nnz == n * n * w + 2 * ((n - 1) * n * w + n * (n - 1) * w + n * n * (w - 1))
+    assert assembled == nnz and dup == 0 and miss == 0
+
+
+def test_nested_dissection_plan_shape_at_95(lib):
+    """n = 95: a leaf is a region of at most 8 columns, so the 95 x 95 grid is cut
+    10 times along every branch (2047 nodes).  The largest front is a child of
+    the root: its separator (47 columns) plus the root separator beside it
+    (95 columns), 18 planes each."""
+    nodes, depth, front, factor, *_ = _nd_stats(lib, 95, 18)
+    assert (nodes, depth) == (2047, 10)
+    assert front == (47 + 95) * 18
+    # the root stores X (1710 x 1710, rows padded to 4) and nothing else
+    assert factor > 1710 * 1712
+
+
+def test_nested_dissection_parameters(lib):
+    from paper_1504_04058_gb300 import make_params
+    nd2 = make_params(63, 20.0, 6, 4, slab_solver="nd")        # 2D: rejected
+    assert lib.asp_footprint_bytes(ctypes.byref(nd2)) == 0
+    blk = make_params(95, 48 * 3.141592653589793, 8, 4, precision="c64", dim=3)
+    nd3 = make_params(95, 48 * 3.141592653589793, 8, 4, precision="c64", dim=3, slab_solver="nd")
+    fb, fn = lib.asp_footprint_bytes(ctypes.byref(blk)), lib.asp_footprint_bytes(ctypes.byref(nd3))
+    assert fb > 0 and fn > 0
+    assert fn < fb  # fewer factor entries than the dense block inverses
+    bad = make_params(95, 48 * 3.141592653589793, 8, 4, precision="c64", dim=3)
+    bad.slab_solver = 7
+    assert lib.asp_footprint_bytes(ctypes.byref(bad)) == 0
+
+
+@pytest.mark.parametrize("n,w", [(13, 4), (31, 5), (95, 18)])
+def test_nested_dissection_plan_matches_the_oracle_tree(lib, n, w):
+    """The library's host plan and the oracle's separator tree are written
+    independently from the same rule; they must agree on the number of nodes,
+    the depth and the largest front."""
+    from oracle import nested_dissection as nd
+    nodes = nd.separator_tree(n, 8)
+
+    def bcols(t):
+        x0, x1, y0, y1 = t.region
+        out = 0
+        out += (x1 - x0) if y0 > 0 else 0
+        out += (x1 - x0) if y1 < n else 0
+        out += (y1 - y0) if x0 > 0 else 0
+        out += (y1 - y0) if x1 < n else 0
+        return out
+
+    front = max((len(t.own) + bcols(t)) * w for t in nodes)
+    depth = max(t.depth for t in nodes)
+    st = _nd_stats(lib, n, w)
+    assert (st[0], st[1], st[2]) == (len(nodes), depth, front)

@@ -570,3 +570,54 @@ def test_iteration_counts_within_the_papers_tables():
     for a, b in zip(sizes, sizes[1:]):
         growth = max(tb - ta for ta, tb in zip(tab[a], tab[b]))
         assert counts[b] - counts[a] <= max(growth, 1), (counts, growth)
+
+
+# ---- nested dissection of the 3D slab subproblems (Section 4)
+
+@pytest.mark.parametrize("name,n,gamma,b,gamma_a", [("ragged", 13, 3, 4, None), ("thin_aux", 15, 4, 3, 2)])
+def test_nested_dissection_solve_equals_sparse_direct_solve(name, n, gamma, b, gamma_a):
+    """Section 4 solves each slab subproblem by nested dissection after grouping
+    the unknowns along x3; the result is H^-1 g, so it must equal a sparse
+    direct solve (scipy's LU) of the same slab matrix for every H_q^M, H_p^R,
+    H_p^L of a 3D partition."""
+    import scipy.sparse.linalg as spl
+    from oracle import nested_dissection as nd
+    P = W.small_problem(3, n, 3 * math.pi, gamma, b, "bump", nrhs=1, pml_aux=gamma_a)
+    part = partition.make_partition(P.n, P.pml, P.b, gamma_a)
+    rng = np.random.default_rng(11)
+    for p in range(1, part.m + 1):
+        for kind in "MRL":
+            if (kind == "R" and p == 1) or (kind == "L" and p == part.m):
+                continue
+            H = subproblems.subproblem_matrix(3, P.n, P.omega, P.c, P.pml, P.C, part, p, kind, order="natural")
+            w = H.shape[0] // (P.n * P.n)
+            g = rng.standard_normal((H.shape[0], 2)) + 1j * rng.standard_normal((H.shape[0], 2))
+            x = nd.solve(nd.factor(H, P.n, w), g)
+            xr = spl.spsolve(H.tocsc(), g)
+            assert np.abs(x - xr).max() <= 1e-11 * np.abs(xr).max(), (p, kind)
+
+
+@pytest.mark.parametrize("n", [3, 5, 9, 13, 20])
+def test_nested_dissection_tree_is_a_dissection(n):
+    """Brute force on small grids: every column is owned by exactly one node;
+    a node's two children lie on either side of its separator line, so no
+    4-neighbour pair of columns joins the two children's regions; and every
+    leaf region holds at most 8 columns."""
+    from oracle import nested_dissection as nd
+    nodes = nd.separator_tree(n, 8)
+    owned = [c for t in nodes for c in t.own]
+    assert sorted(owned) == list(range(n * n))
+    for t in nodes:
+        x0, x1, y0, y1 = t.region
+        if not t.children:
+            assert (x1 - x0) * (y1 - y0) <= 8 and len(t.own) == (x1 - x0) * (y1 - y0)
+            continue
+        a, b = (nodes[c].region for c in t.children)
+        ra = {(x, y) for y in range(a[2], a[3]) for x in range(a[0], a[1])}
+        rb = {(x, y) for y in range(b[2], b[3]) for x in range(b[0], b[1])}
+        sep = {(c % n, c // n) for c in t.own}
+        assert ra | rb | sep == {(x, y) for y in range(y0, y1) for x in range(x0, x1)}
+        assert not (ra & rb) and not (ra & sep) and not (rb & sep)
+        for (x, y) in ra:
+            for q in ((x + 1, y), (x - 1, y), (x, y + 1), (x, y - 1)):
+                assert q not in rb
