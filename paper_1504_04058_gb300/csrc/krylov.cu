@@ -72,9 +72,12 @@ struct VecList {
 // EU elements per thread and loop iteration: independent FP64 chains in flight
 // (GB300 issues FP64 at 1/58 of the FP32 rate with a long result latency, so
 // a single dependent chain per thread leaves the FP64 pipe idle).
+// gate != nullptr: the launch does nothing when *gate == 0 (a pass that the
+// device decided to skip, so the host need not wait for the decision).
 template <int EU>
 __global__ void gs_dot_kernel(VecList V, int J, int want_norm, const double2* __restrict__ w, long long count,
-                              int nrhs, double2* __restrict__ partial) {
+                              int nrhs, double2* __restrict__ partial, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
   __shared__ double2 red[kVecThreads];
   const int bt = blockDim.x;
   const int t = threadIdx.x;
@@ -123,7 +126,8 @@ __global__ void gs_dot_kernel(VecList V, int J, int want_norm, const double2* __
 // out[j0 + j][r] = sum_b partial[b][j][r] for j < J, and nrm[r] = sum_b
 // partial[b][kDotChunk][r] when nrm != nullptr (fixed block order).
 __global__ void dot_finish_kernel(const double2* __restrict__ partial, int nblocks, int J, int nrhs, int j0,
-                                  double2* __restrict__ out, double2* __restrict__ nrm) {
+                                  double2* __restrict__ out, double2* __restrict__ nrm, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int slots = J + (nrm ? 1 : 0);
   if (idx >= slots * nrhs) return;
@@ -144,7 +148,8 @@ __global__ void dot_finish_kernel(const double2* __restrict__ partial, int nbloc
 // two independent partial sums, so several FP64 chains are in flight
 __global__ void gs_axpy_kernel(VecList V, int J, const double2* __restrict__ coef, int j0, double sgn,
                                double2* __restrict__ w, long long count, int nrhs, int want_norm,
-                               double2* __restrict__ partial) {
+                               double2* __restrict__ partial, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
   constexpr int EU = 4;
   __shared__ double2 red[kVecThreads];
   const int bt = blockDim.x;
@@ -428,7 +433,9 @@ struct Krylov {
 
   // out[j][r] = conj(V_j)^T w for j < J (chunks of kDotChunk); nrm[r] = ||w||^2
   // when nrm != nullptr (computed with the first chunk, or alone when J == 0).
-  cudaError_t dots(const double2* const* vs, int J, const double2* w, double2* out, double2* nrm) {
+  // gate: see gs_dot_kernel.
+  cudaError_t dots(const double2* const* vs, int J, const double2* w, double2* out, double2* nrm,
+                   const int* gate = nullptr) {
     // small J: more elements per thread; chunks of at most JM vectors per pass
     const int JM = J <= 2 ? 2 : (J <= 4 ? 4 : kDotChunk);
     for (int j0 = 0; j0 < J || (J == 0 && j0 == 0); j0 += JM) {
@@ -437,18 +444,22 @@ struct Krylov {
       for (int j = 0; j < Jc; ++j) L.v[j] = vs[j0 + j];
       for (int j = Jc; j < kDotChunk; ++j) L.v[j] = w;
       double2* nr = (j0 == 0) ? nrm : nullptr;
-      if (JM == 2) gs_dot_kernel<4><<<red_blocks, red_threads, 0, s>>>(L, Jc, nr ? 1 : 0, w, count, nrhs, partial);
-      else if (JM == 4) gs_dot_kernel<2><<<red_blocks, red_threads, 0, s>>>(L, Jc, nr ? 1 : 0, w, count, nrhs, partial);
-      else gs_dot_kernel<1><<<red_blocks, red_threads, 0, s>>>(L, Jc, nr ? 1 : 0, w, count, nrhs, partial);
+      if (JM == 2)
+        gs_dot_kernel<4><<<red_blocks, red_threads, 0, s>>>(L, Jc, nr ? 1 : 0, w, count, nrhs, partial, gate);
+      else if (JM == 4)
+        gs_dot_kernel<2><<<red_blocks, red_threads, 0, s>>>(L, Jc, nr ? 1 : 0, w, count, nrhs, partial, gate);
+      else
+        gs_dot_kernel<1><<<red_blocks, red_threads, 0, s>>>(L, Jc, nr ? 1 : 0, w, count, nrhs, partial, gate);
       const int slots = Jc + (nr ? 1 : 0);
-      dot_finish_kernel<<<(slots * nrhs + 127) / 128, 128, 0, s>>>(partial, red_blocks, Jc, nrhs, j0, out, nr);
+      dot_finish_kernel<<<(slots * nrhs + 127) / 128, 128, 0, s>>>(partial, red_blocks, Jc, nrhs, j0, out, nr, gate);
       H.launches += 2;
       if (J == 0) break;
     }
     return cudaGetLastError();
   }
   // w += sgn * sum_j coef[j] V_j; nrm[r] = ||w_new||^2 when nrm != nullptr
-  cudaError_t axpys(const double2* const* vs, int J, const double2* coef, double sgn, double2* w, double2* nrm) {
+  cudaError_t axpys(const double2* const* vs, int J, const double2* coef, double sgn, double2* w, double2* nrm,
+                    const int* gate = nullptr) {
     for (int j0 = 0; j0 < J; j0 += kDotChunk) {
       VecList L{};
       const int Jc = std::min(kDotChunk, J - j0);
@@ -456,10 +467,11 @@ struct Krylov {
       for (int j = Jc; j < kDotChunk; ++j) L.v[j] = vs[j0];
       const bool last = j0 + kDotChunk >= J;
       const bool want = last && nrm;
-      gs_axpy_kernel<<<red_blocks, red_threads, 0, s>>>(L, Jc, coef, j0, sgn, w, count, nrhs, want ? 1 : 0, partial);
+      gs_axpy_kernel<<<red_blocks, red_threads, 0, s>>>(L, Jc, coef, j0, sgn, w, count, nrhs, want ? 1 : 0, partial,
+                                                        gate);
       H.launches += 1;
       if (want) {
-        dot_finish_kernel<<<(nrhs + 127) / 128, 128, 0, s>>>(partial, red_blocks, 0, nrhs, 0, nullptr, nrm);
+        dot_finish_kernel<<<(nrhs + 127) / 128, 128, 0, s>>>(partial, red_blocks, 0, nrhs, 0, nullptr, nrm, gate);
         H.launches += 1;
       }
     }
@@ -549,14 +561,12 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
       CK(G.axpys(vl.data(), j + 1, G.K.h1, -1.0, w, G.K.hn2));
       reorth_check_kernel<<<1, 32, 0, s>>>(G.K, nrhs, j);
       H.launches += 1;
-      CK(cudaMemcpyAsync(H.h_flags + 1, G.K.need, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (H.h_flags[1] > 0) {
-        CK(G.dots(vl.data(), j + 1, w, G.K.h2, nullptr));
-        CK(G.axpys(vl.data(), j + 1, G.K.h2, -1.0, w, G.K.hn2));
-      } else {
-        CK(cudaMemsetAsync(G.K.h2, 0, sizeof(double2) * (j + 1) * nrhs, s));
-      }
+      // the second pass is enqueued always and runs only where the device found
+      // that some right-hand side needs it (K.need > 0); skipped, h2 stays 0 and
+      // w and ||w||^2 keep the first pass's values
+      CK(cudaMemsetAsync(G.K.h2, 0, sizeof(double2) * (j + 1) * nrhs, s));
+      CK(G.dots(vl.data(), j + 1, w, G.K.h2, nullptr, G.K.need));
+      CK(G.axpys(vl.data(), j + 1, G.K.h2, -1.0, w, G.K.hn2, G.K.need));
       ++its;
       arnoldi_update_kernel<<<gr, 128, 0, s>>>(G.K, nrhs, j, H.prm.restart, tol, its);
       H.launches += 1;
