@@ -312,8 +312,8 @@ Sizes sizes_for3(const asp_params* p, const Part& P, int num_sms) {
   }
   size_t nd_extra = 0;
   if (p->slab_solver == ASP_SLAB_ND) {
-    // nested dissection: its factors, work and pivots replace the block path's;
-    // no tensor-core operand area
+    // nested dissection: its factors, work, pivots and tensor-core operand
+    // areas replace the block path's
     NdTree T;
     std::string why;
     nd_build_tree(n, T, &why);
@@ -321,7 +321,8 @@ Sizes sizes_for3(const asp_params* p, const Part& P, int num_sms) {
     Z.W_elems = (size_t)ND.factor_elems;
     Z.A_elems = (size_t)ND.work_elems;
     Z.piv_elems = (size_t)ND.piv_ints;
-    nd_extra = (size_t)ND.zu_elems * Z.esz + (size_t)ND.nfronts * (sizeof(NdFront) + sizeof(Slab) + sizeof(int)) +
+    nd_extra = (size_t)ND.zu_elems * Z.esz + (size_t)ND.tc_floats * sizeof(float) +
+               (size_t)ND.nfronts * (sizeof(NdFront) + sizeof(Slab) + sizeof(int)) +
                (T.node.size() + T.cols.size() + T.cmap.size() + T.nn) * sizeof(int);
   } else if (p->factor_prec == ASP_PREC_C64) {
     Z.tc_floats = tc_group_floats(tc_rows_M) + tc_group_floats(tc_rows_RL);

@@ -226,8 +226,12 @@ struct NdFront {
 
 struct NdSizes {
   long long factor_elems = 0, work_elems = 0, piv_ints = 0, zu_elems = 0, nfronts = 0;
+  long long tc_floats = 0;  // complex64: tensor-core operand areas of the large-front levels
   int max_front = 0;
 };
+// Levels whose largest front has at least this many unknowns run their
+// rank-256 updates on the tensor cores (complex64).
+constexpr int kNdTcMinFront = 1024;
 // Builds the separator tree of an n x n grid of columns; returns false (with
 // *why) if a child column is missing from its parent's front.
 bool nd_build_tree(int n, NdTree& T, std::string* why);
@@ -429,10 +433,14 @@ struct Handle {
   NdFront* d_ndf = nullptr;     // every front [slab * nn + node]
   Slab* d_ndslab = nullptr;     // engine view of every front (nb = front size, np = s)
   int* d_ndlist = nullptr;      // front lists per (chunk, depth)
-  struct NdLevel { int off = 0, count = 0, nbmax = 0, npmax = 0, bmax = 0, depth = 0, group = 0; };
+  struct NdLevel { int off = 0, count = 0, nbmax = 0, npmax = 0, bmax = 0, depth = 0, group = 0, tc = -1; };
   std::vector<NdLevel> nd_levels;   // in factor order: per group, per chunk, deepest depth first
   std::vector<NdFront> ndf_host;
   void* nd_zu = nullptr;        // solve scratch of every front
+  // complex64: tensor-core update operands of the levels with large fronts
+  // (NdLevel::tc indexes nd_tcg; one operand area per factor group)
+  std::vector<TcGroup> nd_tcg;
+  float* nd_tc_area[2] = {nullptr, nullptr};
   int nd_maxfront = 0;
   // per depth: offset of its node list in d_ndtab, and the largest column
   // counts (I + B, I, B) of its nodes

@@ -19,7 +19,8 @@
 // (extend-add).  Gauss-Jordan steps on the I columns, with pivots searched in the
 // I rows only, leave X = F_II^-1, X F_IB, -F_BI X and the Schur complement
 // U = F_BB - F_BI X F_IB in the front (factor3d.cu's blocked engine with
-// np = |I|).  Stored: [X; L] with L = F_BI X, and P = X F_IB; U passes to the
+// np = |I|; at complex64 the levels whose fronts reach kNdTcMinFront unknowns
+// run its rank-256 updates on the tensor cores, tcupdate.cu).  Stored: [X; L] with L = F_BI X, and P = X F_IB; U passes to the
 // parent.
 //
 // Solve.  Forward (leaves to root): f_I = g restricted to I(t) plus the
@@ -163,6 +164,7 @@ NdSizes nd_sizes(const NdTree& T, const std::vector<int>& widths, const std::vec
     }
   }
   if (chunk) chunk->assign(widths.size(), 0);
+  std::vector<int> ckof(widths.size(), 0);
   // chunks per group (group 0: the M slabs; group 1: the R and L slabs),
   // greedily while both parity buffers stay inside the budget
   const long long budget = kNdGroupWorkBytes / esz;
@@ -196,8 +198,27 @@ NdSizes nd_sizes(const NdTree& T, const std::vector<int>& widths, const std::vec
       best0 = std::max(best0, e0);
       best1 = std::max(best1, e1);
       if (chunk) (*chunk)[i] = ck;
+      ckof[i] = ck;
     }
     Z.work_elems += best0 + best1;
+    if (esz == 8) {  // complex64: operand rows (fronts padded to 128) of each large-front level
+      long long best = 0;
+      for (int c = 0; c <= ck; ++c)
+        for (int d = 0; d < D; ++d) {
+          long long rows = 0;
+          int nbmax = 0;
+          for (size_t i = 0; i < widths.size(); ++i) {
+            if ((kinds[i] == KIND_M) != (g == 0) || ckof[i] != c) continue;
+            for (int t : T.at_depth[d]) {
+              const int ns = T.nc(t) * widths[i];
+              nbmax = std::max(nbmax, ns);
+              rows += (ns + 127) / 128 * 128;
+            }
+          }
+          if (nbmax >= kNdTcMinFront) best = std::max(best, rows);
+        }
+      Z.tc_floats += tc_group_floats(best);
+    }
   }
   return Z;
 }
@@ -829,6 +850,28 @@ int nd_setup(Handle& H) {
     }
     gbase += buf[0] + buf[1];
   }
+  // complex64: the levels with large fronts get tensor-core update operands
+  // (one area per factor group, shared by its levels, which run in order)
+  std::vector<std::vector<long long>> tc_rowA;
+  std::vector<long long> tc_rows;
+  std::vector<int> tc_group;
+  long long area_rows[2] = {0, 0};
+  if (H.prec == ASP_PREC_C64) {
+    for (auto& L : H.nd_levels) {
+      if (L.nbmax < kNdTcMinFront) continue;
+      std::vector<long long> ra;
+      long long rows = 0;
+      for (int e = 0; e < L.count; ++e) {
+        ra.push_back(rows);
+        rows += (es[lists[L.off + e]].nb + 127) / 128 * 128;
+      }
+      L.tc = (int)tc_rowA.size();
+      tc_rowA.push_back(ra);
+      tc_rows.push_back(rows);
+      tc_group.push_back(L.group);
+      area_rows[L.group] = std::max(area_rows[L.group], rows);
+    }
+  }
   // per-depth node lists and column maxima (the solve's grids)
   std::vector<int> tab(T.node.begin(), T.node.end());
   tab.insert(tab.end(), T.cols.begin(), T.cols.end());
@@ -869,6 +912,8 @@ int nd_setup(Handle& H) {
   dal((void**)&H.d_ndf, H.ndf_host.size() * sizeof(NdFront));
   dal((void**)&H.d_ndslab, es.size() * sizeof(Slab));
   dal((void**)&H.d_ndlist, std::max<size_t>(lists.size(), 1) * sizeof(int));
+  for (int g = 0; g < 2; ++g)
+    if (area_rows[g] > 0) dal((void**)&H.nd_tc_area[g], (size_t)tc_group_floats(area_rows[g]) * sizeof(float));
   if (!ok) {
     cudaGetLastError();
     return fail(ASP_ERR_OOM, "nested dissection: device allocation failed");
@@ -883,6 +928,11 @@ int nd_setup(Handle& H) {
   if (ok && cudaMemset(H.piv3, 0, (size_t)poff * sizeof(int)) != cudaSuccess) ok = false;
   if (ok && cudaMemset(H.W, 0, (size_t)xl * esz) != cudaSuccess) ok = false;
   if (!ok) return fail(ASP_ERR_CUDA, "nested dissection: uploading the plan");
+  H.nd_tcg.assign(tc_rowA.size(), TcGroup());
+  for (size_t i = 0; i < tc_rowA.size(); ++i) {
+    const int rc = tc_group_setup(H.nd_tcg[i], H.nd_tc_area[tc_group[i]], tc_rowA[i], tc_rows[i]);
+    if (rc != ASP_OK) return rc;
+  }
   return ASP_OK;
 }
 
@@ -892,6 +942,12 @@ void nd_release(Handle& H) {
   if (H.d_ndslab) cudaFree(H.d_ndslab);
   if (H.d_ndlist) cudaFree(H.d_ndlist);
   if (H.nd_zu) cudaFree(H.nd_zu);
+  for (auto& g : H.nd_tcg) tc_group_release(g);
+  H.nd_tcg.clear();
+  for (int g = 0; g < 2; ++g) {
+    if (H.nd_tc_area[g]) cudaFree(H.nd_tc_area[g]);
+    H.nd_tc_area[g] = nullptr;
+  }
   H.d_ndtab = nullptr;
   H.d_ndf = nullptr;
   H.d_ndslab = nullptr;
@@ -928,7 +984,8 @@ template <typename R> cudaError_t nd_level(Handle& H, const Handle::NdLevel& L, 
   P.A = H.A3;
   P.piv = H.piv3;
   P.err = H.err;
-  cudaError_t e = gj_partial(H, P, L.nbmax, L.npmax, nullptr, s);
+  const TcGroup* tc = L.tc >= 0 ? &H.nd_tcg[L.tc] : nullptr;  // complex64 large fronts: tensor cores
+  cudaError_t e = gj_partial(H, P, L.nbmax, L.npmax, tc, s);
   if (e != cudaSuccess) return e;
   nd_store_kernel<R><<<dim3(L.nbmax, L.count), 256, 0, s>>>(K);
   H.launches += 1;

@@ -219,3 +219,19 @@ def test_nested_dissection_refactor_and_reuse():
     z2 = host(h.apply_preconditioner(dev(P.f)))
     z3 = host(h.apply_preconditioner(dev(P.f)))
     assert emax(z2, z1) <= 1e-14 and emax(z3, z2) == 0.0
+
+
+def test_nested_dissection_tensor_core_fronts():
+    """One layer of n = 39 (H^M is A itself, w = 39): the top fronts have 1521
+    and 2262 unknowns, so their complex64 updates run on the tensor cores.  The
+    solution's residual against the oracle's assembled A, and its difference
+    from the block-elimination solve, stay at complex64 accuracy."""
+    P = W.small_problem(3, 39, 6 * math.pi, 3, 33, "bump", nrhs=2)
+    A = operator.helmholtz_matrix(3, P.n, P.omega, P.c, P.pml, P.C)
+    zn = host(handle3(P, "c64", solver="nd").apply_preconditioner(dev(P.f)))
+    zb = host(handle3(P, "c64", solver="block").apply_preconditioner(dev(P.f)))
+    for r in range(P.nrhs):
+        fr = P.f[..., r].reshape(-1)
+        res = np.linalg.norm(A @ zn[..., r].reshape(-1) - fr) / np.linalg.norm(fr)
+        assert res <= 1e-4, (r, res)
+    assert emax(zn, zb) <= 2e-4, (emax(zn, zb), rel(zn, zb))
