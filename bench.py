@@ -558,8 +558,23 @@ def run_asp(args, rank, world):
         precond_apply = []
         for nr, a_ms, ph in apply_runs:
             vec = 3 * P.n * P.n * nr * 16                      # r in, z out, and the complex64 copy of r
+            # per phase: the banded layer solves (M-solves: the M factors; fills: the R and L factors,
+            # each band read once as the paper's solves read it) and the sweep chain (the transfer maps
+            # this design reads), each against its own phase time
+            algn = algorithmic(P.n, P.pml, P.b, nr, 8, pml_aux, tc=tcm, widths=widths)
+            phase_hbm = {}
+            for phk in ("embed", "fill", "chain"):
+                byt = algn[phk]["bytes"] if phk == "chain" else algn[phk]["bytes"] - 2 * P.n * P.n * nr * 8
+                t_ms = ph.get(phk, 0.0)
+                phase_hbm[phk] = {"bytes": byt, "ms": t_ms,
+                                  "frac_of_measured_hbm": byt / (t_ms * 1e-3) / 1e9 / peaks["hbm_gbs"] if t_ms else None}
+            ls_bytes = phase_hbm["embed"]["bytes"] + phase_hbm["fill"]["bytes"]
+            ls_ms = ph.get("embed", 0.0) + ph.get("fill", 0.0)
+            phase_hbm["layer_solves"] = {"bytes": ls_bytes, "ms": ls_ms,
+                                         "frac_of_measured_hbm": ls_bytes / (ls_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
+                                         if ls_ms else None}
             precond_apply.append({
-                "nrhs": nr, "ms": a_ms, "phase_ms": ph,
+                "nrhs": nr, "ms": a_ms, "phase_ms": ph, "phase_hbm": phase_hbm,
                 "algorithmic_bytes": band_bytes + vec,
                 "GBps": (band_bytes + vec) / (a_ms * 1e-3) / 1e9,
                 "frac_of_measured_hbm": (band_bytes + vec) / (a_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
