@@ -254,8 +254,8 @@ def stored_factor_bytes(n, gamma, b, esz, gamma_a=None, widths=None, packed=True
 
 
 def _traffic_from_profile(kernel_phase):
-    """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+    """dram bytes per launch (ncu, the n=1023 workload) from the committed
+    summary, if it was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "btsolve_n1023_traffic.txt")
     try:
         kv = {}
@@ -265,9 +265,10 @@ def _traffic_from_profile(kernel_phase):
                 kv[k.strip()] = v.strip()
     except OSError:
         return None
-    src = os.path.join(ROOT, "paper_1504_04058_gb300", "csrc", "btsolve.cuh")
+    name, key = ("chain.cu", "chain_sha256_16") if kernel_phase == "chain" else ("btsolve.cuh", "btsolve_sha256_16")
+    src = os.path.join(ROOT, "paper_1504_04058_gb300", "csrc", name)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if kv.get("btsolve_sha256_16") != sha:
+    if kv.get(key) != sha:
         return None
     v = kv.get(f"{kernel_phase}_dram_bytes_per_launch")
     return float(v) if v else None
@@ -509,8 +510,10 @@ def run_asp(args, rank, world):
                 ach = alg[ph]["bytes"] / (avg_ms * 1e-3) / 1e9
                 r = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": ach / peaks["hbm_gbs"], "kernel": ph, "peak_source": f"hbm_gbs ({peak_kind})"}
-            # DRAM bytes per launch from the committed capture, if taken on this source
-            r["traffic"] = None if (ph in ("tmap", "tdiag") and tcm) else _traffic_from_profile(ph)
+            # DRAM bytes per launch from the committed capture of the n=1023 workload (default
+            # layers, complex64), if taken on this source
+            headline = (args.workload == "n1023" and args.precision == "c64" and not pml_aux and widths is None)
+            r["traffic"] = _traffic_from_profile(ph) if headline and ph in ("embed", "fill", "chain") else None
             r["avg_launch_ms"] = avg_ms
             r["launches_per_step"] = nl / args.steps
             r["hbm_view"] = {"algorithmic_bytes": alg[ph]["bytes"],
