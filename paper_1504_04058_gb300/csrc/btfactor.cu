@@ -22,11 +22,14 @@
 // Each inversion is Gauss-Jordan with partial pivoting inside the block, in
 // shared memory with implicit row exchanges and two ping-pong buffers: step c
 // picks the largest unused entry of column c as pivot (row r_c, found by every
-// warp redundantly so the step needs a single barrier), and after w steps the
+// warp redundantly so the step needs a single barrier; complex64 by one warp
+// max-reduction of a packed magnitude-and-row key), and after w steps the
 // inverse is W[i][j] = B[r_i][col(j)] with col(r) the column whose pivot row
 // was r.  Zero or non-finite pivots are reported as ASP_ERR_SMALL_PIVOT with the
 // subproblem index.  All arithmetic is in the factor precision R (the FP64
 // coefficients are converted once on the host for complex64).
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -86,42 +89,65 @@ __global__ void __launch_bounds__(kFactorThreads)
     C* dst = prev;
     uint64_t used = 0;
     for (int c = 0; c < w; ++c) {
-      R best = R(-1);
-      int bi = 0x7fffffff;
-      for (int r = lane; r < w; r += 32) {
-        if (!((used >> r) & 1ull)) {
-          const C v = src[r * ld + c];
-          const R a = v.x * v.x + v.y * v.y;
-          if (a > best || (a == best && r < bi)) { best = a; bi = r; }
+      int r;
+      R best;
+      if constexpr (std::is_same<R, float>::value) {
+        // one warp reduction: key = |entry|^2 (its bits order like the value)
+        // with the low 6 bits replaced by 63 - row, so ties (and values that
+        // differ in those bits only, 2^-17 relative) go to the lower row
+        unsigned key = 0u;
+        for (int q = lane; q < w; q += 32) {
+          if (!((used >> q) & 1ull)) {
+            const C v = src[q * ld + c];
+            const unsigned k = (__float_as_uint(v.x * v.x + v.y * v.y) & ~63u) | (unsigned)(63 - q);
+            key = key > k ? key : k;
+          }
         }
-      }
+        key = __reduce_max_sync(0xffffffffu, key);
+        r = 63 - (int)(key & 63u);
+        best = __uint_as_float(key & ~63u);
+      } else {
+        best = R(-1);
+        int bi = 0x7fffffff;
+        for (int q = lane; q < w; q += 32) {
+          if (!((used >> q) & 1ull)) {
+            const C v = src[q * ld + c];
+            const R a = v.x * v.x + v.y * v.y;
+            if (a > best || (a == best && q < bi)) { best = a; bi = q; }
+          }
+        }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const R ob = __shfl_xor_sync(0xffffffffu, best, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        for (int off = 16; off > 0; off >>= 1) {
+          const R ob = __shfl_xor_sync(0xffffffffu, best, off);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        r = bi;
       }
-      const int r = bi;
+      if (!(best > R(0)) || !isfinite(best)) bad = true;
+      r = min(max(r, 0), w - 1);  // a failed search is recorded above; stay inside the block
       used |= 1ull << r;
       if (tid == 0) { piv_row[c] = r; col_of_row[r] = c; }
-      if (!(best > R(0)) || !isfinite(best)) bad = true;
-      const C inv = crecip(src[r * ld + c]);
+      const C* prow = src + r * ld;
+      const C inv = crecip(prow[c]);
       if (row_ok) {
-        const C aic = src[i * ld + c];
-        const C f = cmul(aic, inv);
+        // the general update on every entry of the row, then the pivot row and
+        // column take their own values (same thread, so program order)
+        const C* srow = src + i * ld;
+        C* drow = dst + i * ld;
+        const C f = cmul(srow[c], inv);
+        if (i != r) {
 #pragma unroll 2
-        for (int j = jh; j < w; j += kColGroups) {
-          C v;
-          if (i == r) {
-            v = (j == c) ? inv : cmul(src[r * ld + j], inv);
-          } else if (j == c) {
-            v = f;
-            v.x = -v.x; v.y = -v.y;
-          } else {
-            v = src[i * ld + j];
-            cfms(v, f, src[r * ld + j]);
+          for (int j = jh; j < w; j += kColGroups) {
+            C v = srow[j];
+            cfms(v, f, prow[j]);
+            drow[j] = v;
           }
-          dst[i * ld + j] = v;
+          if (jh == (c & (kColGroups - 1))) drow[c] = cmake<R>(-f.x, -f.y);
+        } else {
+#pragma unroll 2
+          for (int j = jh; j < w; j += kColGroups) drow[j] = cmul(prow[j], inv);
+          if (jh == (c & (kColGroups - 1))) drow[c] = inv;
         }
       }
       __syncthreads();
