@@ -34,7 +34,8 @@ paper or mathematics fix independently of this code: closed-form eigenpairs of
 the PML-free operator, complex symmetry of the row-scaled operator (Section 3.1,
 practical remark 4), dense brute-force solves, the boundary-value-problem form
 of G~^R / G~^L, the naive-vs-accumulated identity of Section 2.2, the m=1
-special case (preconditioner = A^-1), and FGMRES against a dense solve.
+special case (preconditioner = A^-1), FGMRES against a dense solve, and the
+nested-dissection slab solve against a sparse direct solve.
 """
 
-from . import pml, operator, partition, subproblems, sweeping, fgmres  # noqa: F401
+from . import pml, operator, partition, subproblems, sweeping, fgmres, nested_dissection  # noqa: F401
