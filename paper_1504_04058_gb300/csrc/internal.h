@@ -231,7 +231,7 @@ struct NdSizes {
 };
 // Levels whose largest front has at least this many unknowns run their
 // rank-256 updates on the tensor cores (complex64).
-constexpr int kNdTcMinFront = 1024;
+constexpr int kNdTcMinFront = 512;
 // Builds the separator tree of an n x n grid of columns; returns false (with
 // *why) if a child column is missing from its parent's front.
 bool nd_build_tree(int n, NdTree& T, std::string* why);
