@@ -309,6 +309,14 @@ int asp_residual_norms_noalloc(const asp_params* p, const double* c, const void*
  * `stream`. */
 int asp_selftest_bounded_wait(int polls, void* stream);
 
+/* Host-side fault injection for tests of the allocation-failure path: after
+ * `after` more device allocations made by asp_setup / asp_setup_layers (0: the
+ * next one), one allocation is reported as failed without calling the CUDA
+ * allocator; the hook then disarms itself.  The setup must return ASP_ERR_OOM
+ * and leave no device memory behind.  after < 0 disarms the hook.  Host-only
+ * state, process-wide; returns ASP_OK. */
+int asp_testhook_fail_device_alloc(int after);
+
 /* Free everything the handle owns.  NULL is accepted; calling it twice on the
  * same pointer is undefined (the handle is gone after the first call). */
 void asp_destroy(asp_handle* h);

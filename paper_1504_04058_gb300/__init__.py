@@ -245,6 +245,13 @@ def asp_selftest_bounded_wait(polls: int = 4096, stream=None) -> int:
     return int(_lib.load().asp_selftest_bounded_wait(int(polls), ctypes.c_void_p(_stream_ptr(stream))))
 
 
+def asp_testhook_fail_device_alloc(after: int) -> None:
+    """Test hook: make the setup's device allocation number ``after`` (0: the
+    next one) fail as if the device were out of memory; the hook disarms itself
+    once it has fired.  ``after`` < 0 disarms it."""
+    _lib.check(_lib.load().asp_testhook_fail_device_alloc(int(after)), "asp_testhook_fail_device_alloc")
+
+
 def asp_setup(c, params: asp_params, widths=None) -> AspHandle:
     """Set up a handle for velocity ``c`` (n x n float64, numpy or CUDA tensor);
     ``widths``: physical layer widths summing to n + 2 - 2*pml (None: uniform

@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <string>
 #include <vector>
@@ -83,6 +84,23 @@ cudaError_t ensure_dyn_smem(const void* func, size_t bytes) {
 }
 
 void set_detail(const std::string& s) { g_detail = s; }
+
+// allocations left before the injected failure (-1: the hook is disarmed)
+std::atomic<int> g_alloc_fail_after{-1};
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  int left = g_alloc_fail_after.load();
+  while (left >= 0) {
+    if (g_alloc_fail_after.compare_exchange_weak(left, left - 1)) {
+      if (left == 0) {  // this allocation fails; the hook is now disarmed (-1)
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
 int fail(int code, const std::string& detail) {
   g_detail = detail;
   return code;
@@ -1145,14 +1163,22 @@ int asp_setup_layers(const asp_params* pin, const int* widths, int nwidths, cons
       }
   }
 
-  // ---- device allocations
+  // ---- device allocations (none when the footprint exceeds the free memory)
+  {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && Z.bytes > free_b) {
+      asp_destroy(hd);
+      return fail(ASP_ERR_OOM, "footprint " + std::to_string(Z.bytes) + " bytes exceeds the free device memory (" +
+                                   std::to_string(free_b) + " bytes)");
+    }
+  }
   const size_t esz = Z.esz;
   const int mr = p->max_rhs;
   bool ok = true;
   auto dal = [&](void** ptr, size_t bytes) {
     if (!ok) return;
     if (bytes == 0) bytes = 16;
-    if (cudaMalloc(ptr, bytes) != cudaSuccess) { ok = false; *ptr = nullptr; }
+    if (dev_malloc(ptr, bytes) != cudaSuccess) { ok = false; *ptr = nullptr; }
   };
   dal((void**)&H.k2, N * sizeof(double));
   dal((void**)&H.ca, n * sizeof(double2));
@@ -1278,13 +1304,19 @@ int asp_setup_layers(const asp_params* pin, const int* widths, int nwidths, cons
     }
   }
   // factor-precision copies of the layer coefficients
+  bool coef_oom = false;
   {
     const size_t nc = H.coef.size();
     std::vector<double2> upv(nc), dnv(nc), dgv(nc);
     for (size_t i = 0; i < nc; ++i) { upv[i] = H.coef[i].up; dnv[i] = H.coef[i].dn; dgv[i] = H.coef[i].dg; }
     auto put = [&](const void* hsrc, size_t bytes) -> void* {
       void* d = nullptr;
-      if (!up || cudaMalloc(&d, bytes ? bytes : 16) != cudaSuccess) { up = false; return nullptr; }
+      if (!up) return nullptr;
+      if (dev_malloc(&d, bytes ? bytes : 16) != cudaSuccess) {
+        up = false;
+        coef_oom = true;
+        return nullptr;
+      }
       H.coef_bufs.push_back(d);
       if (bytes && cudaMemcpy(d, hsrc, bytes, cudaMemcpyHostToDevice) != cudaSuccess) up = false;
       return d;
@@ -1330,6 +1362,8 @@ int asp_setup_layers(const asp_params* pin, const int* widths, int nwidths, cons
   if (up && cudaDeviceSynchronize() != cudaSuccess) up = false;
   if (!up) {
     asp_destroy(hd);
+    cudaGetLastError();
+    if (coef_oom) return fail(ASP_ERR_OOM, "device allocation of the layer coefficients failed");
     return fail(ASP_ERR_CUDA, "uploading the setup data");
   }
   *out = hd;
@@ -1494,6 +1528,11 @@ long long asp_take_launch_count(asp_handle* hd) {
   long long v = hd->h.launches;
   hd->h.launches = 0;
   return v;
+}
+
+int asp_testhook_fail_device_alloc(int after) {
+  g_alloc_fail_after.store(after < 0 ? -1 : after);
+  return ASP_OK;
 }
 
 int asp_selftest_bounded_wait(int polls, void* stream) {

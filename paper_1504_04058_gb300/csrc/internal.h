@@ -452,6 +452,9 @@ struct Handle {
 };
 
 void set_detail(const std::string& s);
+// Device allocation of the setup paths: cudaMalloc, unless the test hook
+// (asp_testhook_fail_device_alloc) has armed a failure for this allocation.
+cudaError_t dev_malloc(void** p, size_t bytes);
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it).
 cudaError_t ensure_dyn_smem(const void* func, size_t bytes);
 int fail(int code, const std::string& detail);

@@ -899,7 +899,7 @@ int nd_setup(Handle& H) {
   H.W_elems = (size_t)xl;
   bool ok = true;
   auto dal = [&](void** p, size_t bytes) {
-    if (ok && cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+    if (ok && dev_malloc(p, bytes ? bytes : 16) != cudaSuccess) {
       ok = false;
       *p = nullptr;
     }

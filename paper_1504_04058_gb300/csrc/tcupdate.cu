@@ -459,7 +459,7 @@ int tc_group_setup(TcGroup& G, float* area, const std::vector<long long>& rowA_h
     return fail(ASP_ERR_UNSUPPORTED, "tensor-map encoding for the tensor-core update failed");
   }
   G.maps = maps;
-  if (cudaMalloc(&G.rowA, rowA_host.size() * sizeof(long long)) != cudaSuccess)
+  if (dev_malloc((void**)&G.rowA, rowA_host.size() * sizeof(long long)) != cudaSuccess)
     return fail(ASP_ERR_OOM, "tensor-core update row table");
   if (cudaMemcpy(G.rowA, rowA_host.data(), rowA_host.size() * sizeof(long long), cudaMemcpyHostToDevice) !=
       cudaSuccess)
