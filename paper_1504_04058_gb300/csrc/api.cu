@@ -395,7 +395,7 @@ Sizes sizes_for(const asp_params* p, const Part& P, int num_sms, bool packed) {
   size_t n2, nd, ni;
   const size_t kst = krylov_state_bytes(p->restart, p->max_rhs, &n2, &nd, &ni);
   size_t bytes = 0;
-  bytes += Z.N * sizeof(double) + 3 * (size_t)n * sizeof(double2);              // k2, ca, cc, cd
+  bytes += 2 * Z.N * sizeof(double) + 3 * (size_t)n * sizeof(double2);          // k2, dgre, ca, cc, cd
   bytes += Z.coef * sizeof(SweepCoef) + Z.nsub * sizeof(SubDesc);
   bytes += Z.W_elems * Z.esz + Z.tmap_elems * Z.esz;
   if (tcm) bytes += (size_t)2 * (P.m - 2) * (n * 2 * 32 * sizeof(float2) + sizeof(TmMap));  // Gamma columns, map table
@@ -427,7 +427,11 @@ __global__ void to_prec_kernel(const double2* __restrict__ in, Cx<R>* __restrict
 
 // z = uM + uR (except on X_1, where there is no right-going part) + uL (except
 // on X_m).  Grid: blockIdx.y = sweep-axis index (x2 column in 2D, x3 plane in
-// 3D), blockIdx.x = chunk of its per_col elements.
+// 3D), blockIdx.x = chunk of its per_col elements.  The sum is taken in the
+// factor precision R and widened once: in complex64 the three parts carry the
+// layer solves' own relative error (far above FP32 rounding), and widening
+// each part to FP64 first would put six conversions and four additions per
+// element on GB300's narrow FP64 pipe.
 template <typename R>
 __global__ void sum3_kernel(const Cx<R>* __restrict__ a, const Cx<R>* __restrict__ b, const Cx<R>* __restrict__ c,
                             double2* __restrict__ z, long long per_col, int r_from, int l_below) {
@@ -435,11 +439,10 @@ __global__ void sum3_kernel(const Cx<R>* __restrict__ a, const Cx<R>* __restrict
   if (er >= per_col) return;
   const int col = blockIdx.y;  // 0-based x2 index
   const long long e = (long long)col * per_col + er;
-  const Cx<R> va = a[e];
-  double re = (double)va.x, im = (double)va.y;
-  if (col >= r_from) { const Cx<R> vb = b[e]; re += (double)vb.x; im += (double)vb.y; }
-  if (col < l_below) { const Cx<R> vc = c[e]; re += (double)vc.x; im += (double)vc.y; }
-  z[e] = make_double2(re, im);
+  Cx<R> v = a[e];
+  if (col >= r_from) { const Cx<R> vb = b[e]; v.x += vb.x; v.y += vb.y; }
+  if (col < l_below) { const Cx<R> vc = c[e]; v.x += vc.x; v.y += vc.y; }
+  z[e] = make_double2((double)v.x, (double)v.y);
 }
 
 int vec_grid(long long count, int sms) {
@@ -940,7 +943,7 @@ void asp_destroy(asp_handle* hd) {
     if (g.stream) cudaStreamDestroy(g.stream);
     if (g.done) cudaEventDestroy(g.done);
   }
-  void* ptrs[] = {H.k2, H.ca, H.cc, H.cd, H.d_subs, H.d_coef, H.W, H.tmap, H.d_toffR, H.d_toffL, H.d_tm, H.gdiag, H.r_lo,
+  void* ptrs[] = {H.k2, H.dgre, H.ca, H.cc, H.cd, H.d_subs, H.d_coef, H.W, H.tmap, H.d_toffR, H.d_toffL, H.d_tm, H.gdiag, H.r_lo,
                   H.uM, H.uR, H.uL, H.accR, H.accL, H.zscr, H.bar, H.V, H.Z, H.wv, H.red, H.hess, H.kstate,
                   H.kflags, H.err, H.d_slabs, H.d_slab_lists, H.A3, H.piv3, H.z3, H.tc_area};
   for (void* p : ptrs)
@@ -1027,6 +1030,19 @@ int asp_setup_layers(const asp_params* pin, const int* widths, int nwidths, cons
     ca[k] = hscale(hmul(sk, sm), ih2);
     cc[k] = hscale(hmul(sk, sp), ih2);
     cd[k] = hscale(hadd(ca[k], cc[k]), -1.0);
+  }
+  // the longest run of nodes with real stencil coefficients (sigma = 0 there)
+  {
+    int best_lo = 0, best_len = 0;
+    for (int k = 0; k < n;) {
+      if (ca[k].y != 0.0 || cc[k].y != 0.0 || cd[k].y != 0.0) { ++k; continue; }
+      int e = k;
+      while (e < n && ca[e].y == 0.0 && cc[e].y == 0.0 && cd[e].y == 0.0) ++e;
+      if (e - k > best_len) { best_len = e - k; best_lo = k; }
+      k = e;
+    }
+    H.real_lo = best_lo;
+    H.real_hi = best_lo + best_len;
   }
   std::vector<double> k2(N);
   for (long long i = 0; i < N; ++i) k2[i] = omega * omega / (ch[i] * ch[i]);
@@ -1181,6 +1197,7 @@ int asp_setup_layers(const asp_params* pin, const int* widths, int nwidths, cons
     if (dev_malloc(ptr, bytes) != cudaSuccess) { ok = false; *ptr = nullptr; }
   };
   dal((void**)&H.k2, N * sizeof(double));
+  if (H.dim == 2) dal((void**)&H.dgre, N * sizeof(double));
   dal((void**)&H.ca, n * sizeof(double2));
   dal((void**)&H.cc, n * sizeof(double2));
   dal((void**)&H.cd, n * sizeof(double2));
@@ -1238,6 +1255,14 @@ int asp_setup_layers(const asp_params* pin, const int* widths, int nwidths, cons
     if (up && bytes && cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) up = false;
   };
   cp(H.k2, k2.data(), N * sizeof(double));
+  if (H.dim == 2) {
+    // real part of the operator's diagonal, d_{i1} + d_{i2} + omega^2/c^2 (the matvec's)
+    std::vector<double> dre(N);
+    for (int i2 = 0; i2 < n; ++i2)
+      for (int i1 = 0; i1 < n; ++i1)
+        dre[(long long)i2 * n + i1] = cd[i1].x + cd[i2].x + k2[(long long)i2 * n + i1];
+    cp(H.dgre, dre.data(), N * sizeof(double));
+  }
   cp(H.ca, ca.data(), n * sizeof(double2));
   cp(H.cc, cc.data(), n * sizeof(double2));
   cp(H.cd, cd.data(), n * sizeof(double2));

@@ -339,9 +339,12 @@ struct Handle {
   // device: velocity term omega^2/c^2 (natural order), global x1/x2 stencil
   // coefficients per node (the same profile on both axes)
   double* k2 = nullptr;
+  double* dgre = nullptr;  // 2D: Re of the operator's diagonal, d_{i1}.x + d_{i2}.x + k2 (natural order)
   double2* ca = nullptr;  // a_k = s_k s_{k-1/2} / h^2
   double2* cc = nullptr;  // c_k = s_k s_{k+1/2} / h^2
   double2* cd = nullptr;  // d_k = -s_k (s_{k+1/2} + s_{k-1/2}) / h^2
+  // nodes [real_lo, real_hi) of an axis where a_k, c_k, d_k are real (outside the PML)
+  int real_lo = 0, real_hi = 0;
 
   // the same coefficients in the factor precision (owned device buffers)
   FactorCoefs<float> fc32;

@@ -32,31 +32,53 @@ __device__ __forceinline__ double2 dmul(double2 a, double2 b) { return cmul(a, b
 // ------------------------------------------------------------------ matvec
 // (Au)_{i1,i2} = a_{i1} u_{i1-1} + c_{i1} u_{i1+1} + a_{i2} u_{i2-1} + c_{i2} u_{i2+1}
 //                + (d_{i1} + d_{i2} + omega^2/c^2) u,  zero outside the grid.
-// Grid: blockIdx.y = x2 row, blockIdx.x = chunk of the row's n*nrhs elements;
+// One launch covers a region of the grid: rows r0 + blockIdx.y and columns
+// c0 + (element / nrhs), each skipping a gap [skip_lo, skip_lo + skip_n) of
+// indices, so that the interior box and the PML frame around it are separate
+// launches.  REAL: every coefficient of the region is real (sigma = 0, outside
+// the PML), and the products are real-by-complex, half the FP64 operations of
+// the complex products and the same values (up to the sign of zero results).
 // NRT is the number of right-hand sides when it is a compile-time constant
 // (0: runtime `nrhs`), so that the point index needs no runtime division.
-template <int NRT>
-__global__ void matvec_kernel(const double* __restrict__ k2, const double2* __restrict__ ca,
+struct MvRegion {
+  int r0, rskip_lo, rskip_n;  // rows: r0 + y, then + rskip_n from rskip_lo on
+  int c0, ncols, cskip_lo, cskip_n;
+};
+
+template <int NRT, bool REAL>
+__global__ void matvec_kernel(const double* __restrict__ dgre, const double2* __restrict__ ca,
                               const double2* __restrict__ cc, const double2* __restrict__ cd, int n,
-                              int nrhs_rt, const double2* __restrict__ x, double2* __restrict__ y) {
+                              int nrhs_rt, const double2* __restrict__ x, double2* __restrict__ y, MvRegion g) {
   const int nr = NRT > 0 ? NRT : nrhs_rt;
-  const int er = blockIdx.x * blockDim.x + threadIdx.x;  // element within the row
-  if (er >= n * nr) return;
-  const int i2 = blockIdx.y;
-  const int i1 = er / nr;
+  const int er = blockIdx.x * blockDim.x + threadIdx.x;  // element within the region's row
+  if (er >= g.ncols * nr) return;
+  int i2 = g.r0 + (int)blockIdx.y;
+  if (i2 >= g.rskip_lo) i2 += g.rskip_n;
+  int i1 = g.c0 + er / nr;
+  if (i1 >= g.cskip_lo) i1 += g.cskip_n;
+  const int r = er - (er / nr) * nr;
   const long long rowst = (long long)n * nr;
-  const long long e = (long long)i2 * rowst + er;
+  const long long e = (long long)i2 * rowst + (long long)i1 * nr + r;
   const double2 u = x[e];
-  const double2 d1 = cd[i1], d2 = cd[i2];
-  const double2 diag = make_double2(d1.x + d2.x + k2[(long long)i2 * n + i1], d1.y + d2.y);
-  // two independent partial sums (x1 and x2 neighbours) shorten the FP64 chain
-  double2 acc = dmul(diag, u);
-  double2 acc2 = make_double2(0.0, 0.0);
-  if (i1 > 0) cfma(acc, ca[i1], x[e - nr]);
-  if (i2 > 0) cfma(acc2, ca[i2], x[e - rowst]);
-  if (i1 < n - 1) cfma(acc, cc[i1], x[e + nr]);
-  if (i2 < n - 1) cfma(acc2, cc[i2], x[e + rowst]);
-  y[e] = make_double2(acc.x + acc2.x, acc.y + acc2.y);
+  const double2 a1 = ca[i1], c1 = cc[i1], a2 = ca[i2], c2 = cc[i2];
+  const double dg = dgre[(long long)i2 * n + i1];  // Re(d_{i1} + d_{i2}) + omega^2/c^2
+  // one accumulator: the FP64 pipe, not the dependent chain, bounds this kernel
+  double2 acc;
+  if constexpr (REAL) {
+    acc = make_double2(dg * u.x, dg * u.y);
+    if (i1 > 0) { const double2 v = x[e - nr]; acc.x = fma(a1.x, v.x, acc.x); acc.y = fma(a1.x, v.y, acc.y); }
+    if (i2 > 0) { const double2 v = x[e - rowst]; acc.x = fma(a2.x, v.x, acc.x); acc.y = fma(a2.x, v.y, acc.y); }
+    if (i1 < n - 1) { const double2 v = x[e + nr]; acc.x = fma(c1.x, v.x, acc.x); acc.y = fma(c1.x, v.y, acc.y); }
+    if (i2 < n - 1) { const double2 v = x[e + rowst]; acc.x = fma(c2.x, v.x, acc.x); acc.y = fma(c2.x, v.y, acc.y); }
+  } else {
+    const double2 diag = make_double2(dg, cd[i1].y + cd[i2].y);
+    acc = dmul(diag, u);
+    if (i1 > 0) cfma(acc, a1, x[e - nr]);
+    if (i2 > 0) cfma(acc, a2, x[e - rowst]);
+    if (i1 < n - 1) cfma(acc, c1, x[e + nr]);
+    if (i2 < n - 1) cfma(acc, c2, x[e + rowst]);
+  }
+  y[e] = acc;
 }
 
 struct VecList {
@@ -400,20 +422,41 @@ int grid_for(long long count, int threads, int sms) {
 
 }  // namespace
 
+template <int NRT>
+void matvec_regions(const Handle& H, const double2* x, double2* y, int nrhs, cudaStream_t s) {
+  const int n = H.n;
+  const int lo = H.real_lo, nb = H.real_hi - H.real_lo;
+  auto go = [&](bool real, int nrows, const MvRegion& g) {
+    const long long per_row = (long long)g.ncols * nrhs;
+    if (nrows <= 0 || per_row <= 0) return;
+    dim3 grid((unsigned)((per_row + kVecThreads - 1) / kVecThreads), (unsigned)nrows);
+    if (real)
+      matvec_kernel<NRT, true><<<grid, kVecThreads, 0, s>>>(H.dgre, H.ca, H.cc, H.cd, n, nrhs, x, y, g);
+    else
+      matvec_kernel<NRT, false><<<grid, kVecThreads, 0, s>>>(H.dgre, H.ca, H.cc, H.cd, n, nrhs, x, y, g);
+    const_cast<Handle&>(H).launches += 1;
+  };
+  const int kNone = 1 << 30;
+  if (nb <= 0) {
+    go(false, n, MvRegion{0, kNone, 0, 0, n, kNone, 0});
+    return;
+  }
+  go(true, nb, MvRegion{lo, kNone, 0, lo, nb, kNone, 0});          // interior box, real coefficients
+  go(false, n - nb, MvRegion{0, lo, nb, 0, n, kNone, 0});           // rows outside the box
+  go(false, nb, MvRegion{lo, kNone, 0, 0, n - nb, lo, nb});         // the box rows' PML columns
+}
+
 cudaError_t launch_matvec(const Handle& H, const double2* x, double2* y, int nrhs, cudaStream_t s) {
   if (H.dim == 3) return launch_matvec3d(H, x, y, nrhs, s);
-  const long long per_row = (long long)H.n * nrhs;
-  dim3 grid((unsigned)((per_row + kVecThreads - 1) / kVecThreads), (unsigned)H.n);
   switch (nrhs) {
-    case 1: matvec_kernel<1><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
-    case 2: matvec_kernel<2><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
-    case 4: matvec_kernel<4><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
-    case 8: matvec_kernel<8><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
-    case 16: matvec_kernel<16><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
-    case 32: matvec_kernel<32><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
-    default: matvec_kernel<0><<<grid, kVecThreads, 0, s>>>(H.k2, H.ca, H.cc, H.cd, H.n, nrhs, x, y); break;
+    case 1: matvec_regions<1>(H, x, y, nrhs, s); break;
+    case 2: matvec_regions<2>(H, x, y, nrhs, s); break;
+    case 4: matvec_regions<4>(H, x, y, nrhs, s); break;
+    case 8: matvec_regions<8>(H, x, y, nrhs, s); break;
+    case 16: matvec_regions<16>(H, x, y, nrhs, s); break;
+    case 32: matvec_regions<32>(H, x, y, nrhs, s); break;
+    default: matvec_regions<0>(H, x, y, nrhs, s); break;
   }
-  const_cast<Handle&>(H).launches += 1;
   return cudaGetLastError();
 }
 
@@ -547,6 +590,7 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
     H.launches += 1;
     CK(G.scale(rvec, G.K.inv, G.Vv(0)));
     first = false;
+    int jrun = 0;  // Arnoldi steps of this cycle: no right-hand side has more columns
     for (int j = 0; j < restart && its < maxit; ++j) {
       rc = apply_precond(H, G.Vv(j), G.Zv(j), nrhs, s);
       if (rc != ASP_OK) return rc;
@@ -568,6 +612,7 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
       CK(G.dots(vl.data(), j + 1, w, G.K.h2, nullptr, G.K.need));
       CK(G.axpys(vl.data(), j + 1, G.K.h2, -1.0, w, G.K.hn2, G.K.need));
       ++its;
+      jrun = j + 1;
       arnoldi_update_kernel<<<gr, 128, 0, s>>>(G.K, nrhs, j, H.prm.restart, tol, its);
       H.launches += 1;
       CK(G.scale(w, G.K.inv, w));
@@ -579,12 +624,13 @@ int gmres_run(Handle& H, const double2* f, double2* u, int nrhs, double tol, int
       active = H.h_flags[0];
       if (active == 0) break;
     }
-    // u += Z y  (per right-hand side, its own number of columns)
+    // u += Z y  (per right-hand side, its own number of columns; y is zero
+    // past them, so only the cycle's jrun basis vectors are read)
     ysolve_kernel<<<gr, 128, 0, s>>>(G.K, nrhs, H.prm.restart);
     H.launches += 1;
-    std::vector<const double2*> zl(restart);
-    for (int i = 0; i < restart; ++i) zl[i] = G.Zv(i);
-    CK(G.axpys(zl.data(), restart, G.K.y, 1.0, u, nullptr));
+    std::vector<const double2*> zl(std::max(jrun, 1));
+    for (int i = 0; i < jrun; ++i) zl[i] = G.Zv(i);
+    if (jrun > 0) CK(G.axpys(zl.data(), jrun, G.K.y, 1.0, u, nullptr));
     if (active == 0 || its >= maxit) break;
   }
   // true residual ||f - A u|| / ||f||

@@ -100,6 +100,20 @@ def test_matvec_matches_oracle(name):
     assert emax(y, yo) <= 1e-13, (emax(y, yo), rel(y, yo))
 
 
+@pytest.mark.parametrize("nrhs", [2, 8, 32])
+def test_matvec_compile_time_rhs_counts_match_oracle(nrhs):
+    # the instances for 2, 8 and 32 right-hand sides, PML and interior points
+    # (real coefficients outside the PML take the real-by-complex products)
+    P = W.small_problem(2, 37, 5 * math.pi, 5, 3, "layered", nrhs=nrhs)
+    h = handle(P)
+    rng = np.random.default_rng(nrhs)
+    x = rng.standard_normal(P.f.shape) + 1j * rng.standard_normal(P.f.shape)
+    y = host(h.matvec(dev(x)))
+    A = operator.helmholtz_matrix(2, P.n, P.omega, P.c, P.pml, P.C)
+    yo = (A @ x.reshape(P.n * P.n, -1)).reshape(x.shape)
+    assert emax(y, yo) <= 1e-13, (emax(y, yo), rel(y, yo))
+
+
 def test_matvec_config_n127():
     P = W.problem_2d_n127_const()
     h = handle(P)
