@@ -524,16 +524,17 @@ __global__ void __maxnreg__(80) tmap_tc_kernel(const __grid_constant__ TmParams 
 // Diagonal blocks of the subproblem inverse, Gamma_{n-1} = W_{n-1},
 // Gamma_k = W_k + (c_k a_{k+1}) W_k Gamma_{k+1} W_k, one CTA per map, in shared
 // memory; stores Gamma_k e_in and Gamma_k e_keep at gd[goff + (2k + f) kGS + i].
-// Thread t owns row i = t / 8 and columns j = t % 8 + 8u (u < 4) of the 32 x 32
-// working blocks; W_{k-1} is fetched into registers during step k.
-constexpr int kGdThreads = 256;
-
-__global__ void __launch_bounds__(kGdThreads) gdiag_kernel(const TmMap* __restrict__ maps, int n,
-                                                          const float2* __restrict__ W,
-                                                          const float2* __restrict__ ca,
-                                                          const float2* __restrict__ cc,
-                                                          const float2* __restrict__ s2inv, float2* __restrict__ gd,
-                                                          int packed) {
+// NU columns per thread: thread t owns row i = t / 8 and columns j = t % 8 + 8u
+// (u < NU) of the (8 NU) x (8 NU) working blocks, so a launch for blocks of at
+// most 24 columns (NU = 3, 192 threads) spends no lanes on padding; W_{k-1} is
+// fetched into registers during step k.
+template <int NU>
+__global__ void __launch_bounds__(64 * NU) gdiag_kernel(const TmMap* __restrict__ maps, int n,
+                                                       const float2* __restrict__ W,
+                                                       const float2* __restrict__ ca,
+                                                       const float2* __restrict__ cc,
+                                                       const float2* __restrict__ s2inv, float2* __restrict__ gd,
+                                                       int packed) {
   __shared__ float2 sW[32][33], sG[32][33], sP[32][33];
   const TmMap M = maps[blockIdx.x];
   const int w = M.w;
@@ -541,27 +542,27 @@ __global__ void __launch_bounds__(kGdThreads) gdiag_kernel(const TmMap* __restri
   const float2* Wsub = W + M.woff;
   float2* g = gd + M.goff;
   // W_k[i][j] = W'_k(i, j) / s2_j from the packed symmetric factor
-  float2 dinv[4];
+  float2 dinv[NU];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) dinv[u] = (j0 + 8 * u < w) ? s2inv[M.prof + j0 + 8 * u] : make_float2(0.f, 0.f);
-  auto fetch = [&](int k, float2 (&v)[4]) {
+  for (int u = 0; u < NU; ++u) dinv[u] = (j0 + 8 * u < w) ? s2inv[M.prof + j0 + 8 * u] : make_float2(0.f, 0.f);
+  auto fetch = [&](int k, float2 (&v)[NU]) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < NU; ++u) {
       const int jj = j0 + 8 * u;
       v[u] = (i >= w || jj >= w) ? make_float2(0.f, 0.f)
              : packed ? cmul(Wsub[(long long)k * M.bs + packed_index(i, jj)], dinv[u])
                       : Wsub[(long long)k * M.bs + (long long)jj * M.wp + i];
     }
   };
-  float2 wr[4];
+  float2 wr[NU];
   fetch(n - 1, wr);
 #pragma unroll
-  for (int u = 0; u < 4; ++u) { sG[i][j0 + 8 * u] = wr[u]; }
+  for (int u = 0; u < NU; ++u) { sG[i][j0 + 8 * u] = wr[u]; }
   if (n >= 2) fetch(n - 2, wr);
   __syncthreads();
   auto emit = [&](int k) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < NU; ++u) {
       const int jj = j0 + 8 * u;
       if (i < w && jj == M.jin) g[(long long)(2 * k) * kGS + i] = sG[i][jj];
       if (i < w && jj == M.keep) g[(long long)(2 * k + 1) * kGS + i] = sG[i][jj];
@@ -571,34 +572,34 @@ __global__ void __launch_bounds__(kGdThreads) gdiag_kernel(const TmMap* __restri
   float2 beta_next = n >= 2 ? cmul(cc[n - 2], ca[n - 1]) : make_float2(0.f, 0.f);
   for (int k = n - 2; k >= 0; --k) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) sW[i][j0 + 8 * u] = wr[u];
+    for (int u = 0; u < NU; ++u) sW[i][j0 + 8 * u] = wr[u];
     __syncthreads();
     if (k >= 1) fetch(k - 1, wr);  // in flight during this step
     // P = W_k Gamma_{k+1}
-    float2 acc[4];
+    float2 acc[NU];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+    for (int u = 0; u < NU; ++u) acc[u] = make_float2(0.f, 0.f);
     for (int l = 0; l < w; ++l) {
       const float2 a = sW[i][l];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) cfma(acc[u], a, sG[l][j0 + 8 * u]);
+      for (int u = 0; u < NU; ++u) cfma(acc[u], a, sG[l][j0 + 8 * u]);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) sP[i][j0 + 8 * u] = acc[u];
+    for (int u = 0; u < NU; ++u) sP[i][j0 + 8 * u] = acc[u];
     __syncthreads();
     // Gamma_k = W_k + beta P W_k
     const float2 beta = beta_next;
     if (k >= 1) beta_next = cmul(cc[k - 1], ca[k]);  // in flight during this step
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+    for (int u = 0; u < NU; ++u) acc[u] = make_float2(0.f, 0.f);
     for (int l = 0; l < w; ++l) {
       const float2 a = sP[i][l];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) cfma(acc[u], a, sW[l][j0 + 8 * u]);
+      for (int u = 0; u < NU; ++u) cfma(acc[u], a, sW[l][j0 + 8 * u]);
     }
     __syncthreads();  // every read of sG (previous block) is done
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < NU; ++u) {
       float2 v = sW[i][j0 + 8 * u];
       cfma(v, beta, acc[u]);
       sG[i][j0 + 8 * u] = v;
@@ -616,10 +617,17 @@ __global__ void __launch_bounds__(kGdThreads) gdiag_kernel(const TmMap* __restri
 cudaError_t launch_tmap_diag(Handle& H, cudaStream_t s) {
   const int nmaps = (int)H.tm_host.size();
   if (nmaps == 0) return cudaSuccess;
-  for (const TmMap& M : H.tm_host)
+  int wcap = 0;
+  for (const TmMap& M : H.tm_host) {
     if (M.w > kTmapTcMaxW) return cudaErrorInvalidValue;
-  gdiag_kernel<<<nmaps, kGdThreads, 0, s>>>(H.d_tm, H.n, (const float2*)H.W, H.fc32.ca, H.fc32.cc,
-                                            H.fc32.s2inv, (float2*)H.gdiag, H.packed ? 1 : 0);
+    wcap = std::max(wcap, M.w);
+  }
+  if (wcap <= 24)
+    gdiag_kernel<3><<<nmaps, 64 * 3, 0, s>>>(H.d_tm, H.n, (const float2*)H.W, H.fc32.ca, H.fc32.cc, H.fc32.s2inv,
+                                             (float2*)H.gdiag, H.packed ? 1 : 0);
+  else
+    gdiag_kernel<4><<<nmaps, 64 * 4, 0, s>>>(H.d_tm, H.n, (const float2*)H.W, H.fc32.ca, H.fc32.cc, H.fc32.s2inv,
+                                             (float2*)H.gdiag, H.packed ? 1 : 0);
   H.launches += 1;
   return cudaGetLastError();
 }
