@@ -16,9 +16,11 @@
 // kept as an explicit inverse, which turns every solve step into a dense
 // matrix product.
 //
-// One CTA of 256 threads factors one subproblem; the n block inversions are
-// sequential.  Thread t owns row i = t mod 64 and every fourth column
-// (j = t/64, t/64 + 4, ...) of the block, so no index arithmetic divides.
+// One CTA of 4 ROWS threads factors one subproblem; the n block inversions
+// are sequential.  Thread t owns row i = t mod ROWS and every fourth column
+// (j = t/ROWS, t/ROWS + 4, ...) of the block, so no index arithmetic divides.
+// A launch takes the smallest ROWS of 32, 48, 64 that covers its widest block,
+// so that few threads own no row (the pivot search runs in every warp).
 // Each inversion is Gauss-Jordan with partial pivoting inside the block, in
 // shared memory with implicit row exchanges and two ping-pong buffers: step c
 // picks the largest unused entry of column c as pivot (row r_c, found by every
@@ -28,6 +30,7 @@
 // was r.  Zero or non-finite pivots are reported as ASP_ERR_SMALL_PIVOT with the
 // subproblem index.  All arithmetic is in the factor precision R (the FP64
 // coefficients are converted once on the host for complex64).
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -37,11 +40,10 @@ namespace asp {
 
 namespace {
 
-constexpr int kFactorThreads = 256;
-constexpr int kColGroups = kFactorThreads / 64;  // threads sharing a row
+constexpr int kColGroups = 4;  // threads sharing a row
 
-template <typename R>
-__global__ void __launch_bounds__(kFactorThreads)
+template <typename R, int ROWS>
+__global__ void __launch_bounds__(ROWS * kColGroups)
     btfactor_kernel(const SubDesc* __restrict__ subs, int first, FactorCoefs<R> F, int n,
                     Cx<R>* __restrict__ Wout, int* err, int packed) {
   using C = Cx<R>;
@@ -55,8 +57,8 @@ __global__ void __launch_bounds__(kFactorThreads)
   __shared__ int piv_row[64];
   __shared__ int col_of_row[64];
   const int tid = threadIdx.x, lane = tid & 31;
-  const int i = tid & 63;        // my row
-  const int jh = tid >> 6;       // my first column (then every kColGroups-th)
+  const int i = tid % ROWS;  // my row
+  const int jh = tid / ROWS; // my first column (then every kColGroups-th)
   const bool row_ok = i < w;
   const Cx<R>* up = F.up + S.prof;
   const Cx<R>* dn = F.dn + S.prof;
@@ -177,20 +179,26 @@ __global__ void __launch_bounds__(kFactorThreads)
 cudaError_t launch_factor(Handle& H, int first, int count, cudaStream_t s) {
   const int nsub = count;
   if (nsub <= 0) return cudaSuccess;
+  int wmax = 0;  // the launch's widest block sets its shared memory and row count
+  for (int q = first; q < first + count; ++q) wmax = std::max(wmax, H.subs[q].w);
   const size_t esz = H.prec == ASP_PREC_C128 ? sizeof(double2) : sizeof(float2);
-  const size_t smem = 2 * (size_t)H.wmax * (H.wmax | 1) * esz;
+  const size_t smem = 2 * (size_t)wmax * (wmax | 1) * esz;
+  auto go = [&](auto kern, int rows, auto* W, const auto& F, int packed) -> cudaError_t {
+    cudaError_t e = ensure_dyn_smem((const void*)kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nsub, rows * kColGroups, smem, s>>>(H.d_subs, first, F, H.n, W, H.err, packed);
+    return cudaSuccess;
+  };
   cudaError_t e;
-  if (H.prec == ASP_PREC_C128) {
-    e = ensure_dyn_smem((const void*)btfactor_kernel<double>, smem);
-    if (e != cudaSuccess) return e;
-    btfactor_kernel<double><<<nsub, kFactorThreads, smem, s>>>(H.d_subs, first, H.fc64, H.n, (double2*)H.W,
-                                                                H.err, 0);
-  } else {
-    e = ensure_dyn_smem((const void*)btfactor_kernel<float>, smem);
-    if (e != cudaSuccess) return e;
-    btfactor_kernel<float><<<nsub, kFactorThreads, smem, s>>>(H.d_subs, first, H.fc32, H.n, (float2*)H.W,
-                                                               H.err, H.packed ? 1 : 0);
-  }
+  if (H.prec == ASP_PREC_C128)
+    e = wmax <= 32   ? go(btfactor_kernel<double, 32>, 32, (double2*)H.W, H.fc64, 0)
+        : wmax <= 48 ? go(btfactor_kernel<double, 48>, 48, (double2*)H.W, H.fc64, 0)
+                     : go(btfactor_kernel<double, 64>, 64, (double2*)H.W, H.fc64, 0);
+  else
+    e = wmax <= 32   ? go(btfactor_kernel<float, 32>, 32, (float2*)H.W, H.fc32, H.packed ? 1 : 0)
+        : wmax <= 48 ? go(btfactor_kernel<float, 48>, 48, (float2*)H.W, H.fc32, H.packed ? 1 : 0)
+                     : go(btfactor_kernel<float, 64>, 64, (float2*)H.W, H.fc32, H.packed ? 1 : 0);
+  if (e != cudaSuccess) return e;
   H.launches += 1;
   return cudaGetLastError();
 }
