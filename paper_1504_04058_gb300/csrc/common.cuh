@@ -49,7 +49,17 @@ template <typename R> __device__ __forceinline__ Cx<R> cvt(float2 a) { return cm
 // 1/z for complex z (used for pivots; z != 0 checked by the caller)
 template <typename C> __device__ __forceinline__ C crecip(C z) {
   auto d = z.x * z.x + z.y * z.y;
-  C r; r.x = z.x / d; r.y = -z.y / d; return r;
+  C r;
+  if constexpr (sizeof(z.x) == 4) {
+    // complex64: one correctly rounded reciprocal of |z|^2 and two products
+    // (within an ulp of the two divisions, and off the dependent chain of a
+    // Gauss-Jordan step's pivot for most of their latency)
+    const float rd = __frcp_rn(d);
+    r.x = z.x * rd; r.y = -z.y * rd;
+  } else {
+    r.x = z.x / d; r.y = -z.y / d;
+  }
+  return r;
 }
 
 // ------------------------------------------------------------- error word
