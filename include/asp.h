@@ -248,6 +248,15 @@ int asp_gmres_solve(asp_handle* h, const void* f, void* u, int nrhs, double tol,
  * (ASP_OK).  Synchronizes `stream`. */
 int asp_autotune(asp_handle* h, int nrhs, int* choice_host, double* ms_host, void* stream);
 
+/* asp_set_solve_shape: use the launch shape (cap, variant) -- one of the
+ * candidates asp_autotune times, listed there -- for the layer solves of kind
+ * 0 (M-solves) or 1 (sweep fills) in later applies with `nrhs` right-hand
+ * sides, instead of the default or the autotuned choice (2D handles).  Every
+ * shape computes the same result; this fixes the choice (reproducible runs,
+ * tests of each compiled tile).  ASP_ERR_INVALID for a shape that is not a
+ * candidate at this nrhs, ASP_ERR_UNSUPPORTED on 3D handles.  Host-only. */
+int asp_set_solve_shape(asp_handle* h, int nrhs, int kind, int cap, int variant);
+
 /* Number of kernel launches this handle has issued since the last call (the
  * counter is reset by the call).  Used to report how many of the library's
  * kernels ran in a timed region. */

@@ -141,6 +141,14 @@ class AspHandle:
         return {"embed": {"cap": int(choice[0]), "variant": int(choice[1]), "candidate_ms": [float(x) for x in ms[:3]]},
                 "fill": {"cap": int(choice[2]), "variant": int(choice[3]), "candidate_ms": [float(x) for x in ms[3:]]}}
 
+    def set_solve_shape(self, nrhs: int, kind: str, cap: int, variant: int = 0) -> None:
+        """Fix the launch shape of the M-solves (kind "embed") or the sweep fills
+        ("fill") for applies with ``nrhs`` right-hand sides: one of the
+        candidates asp_autotune times."""
+        k = {"embed": 0, "fill": 1}[kind]
+        _lib.check(_lib.load().asp_set_solve_shape(self._ptr, int(nrhs), k, int(cap), int(variant)),
+                   "asp_set_solve_shape")
+
     def factor(self, stream=None) -> None:
         _lib.check(_lib.load().asp_factor(self._ptr, ctypes.c_void_p(_stream_ptr(stream))), "asp_factor")
 

@@ -37,7 +37,7 @@ EXPORTS = [
     "asp_gmres_solve", "asp_take_launch_count", "asp_set_phase_timing", "asp_phase_times",
     "asp_destroy", "asp_error_string", "asp_last_error_detail", "asp_residual_norms_noalloc",
     "asp_selftest_bounded_wait", "asp_setup_layers", "asp_footprint_bytes_layers", "asp_layer_widths_from_velocity",
-    "asp_autotune", "asp_nd_plan_check", "asp_testhook_fail_device_alloc",
+    "asp_autotune", "asp_set_solve_shape", "asp_nd_plan_check", "asp_testhook_fail_device_alloc",
 ]
 NOALLOC_MAX_N = 4096
 NOALLOC_MAX_RHS = 64
@@ -104,6 +104,7 @@ def load() -> ctypes.CDLL:
         "asp_gmres_solve": (I, [P, P, P, I, D, I, I, ctypes.POINTER(asp_solve_info), P]),
         "asp_take_launch_count": (ctypes.c_longlong, [P]),
         "asp_autotune": (I, [P, I, P, P, P]),
+        "asp_set_solve_shape": (I, [P, I, I, I, I]),
         "asp_nd_plan_check": (I, [I, I, P, I]),
         "asp_testhook_fail_device_alloc": (I, [I]),
         "asp_set_phase_timing": (I, [P, I]),

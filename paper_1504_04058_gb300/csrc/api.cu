@@ -787,11 +787,32 @@ int autotune(Handle& H, int nrhs, int* choice, double* ms_out, cudaStream_t s) {
   return rc;
 }
 
+int set_solve_shape(Handle& H, int nrhs, int kind, int cap, int variant) {
+  if (H.dim != 2) return fail(ASP_ERR_UNSUPPORTED, "3D slab solves have one launch shape");
+  if (kind != 0 && kind != 1) return fail(ASP_ERR_INVALID, "kind must be 0 (M-solves) or 1 (fills)");
+  const int wm = kind == 0 ? embed_wmax(H) : std::max(1, H.wmaxRL);
+  for (const Shape& c : tune_candidates(H, nrhs, wm))
+    if (c.cap == cap && c.variant == variant) {
+      JobCache& jc = cache_of(&H);
+      (kind == 0 ? jc.tuned_embed : jc.tuned_fill)[nrhs] = c;
+      (kind == 0 ? jc.embed : jc.fill).erase(nrhs);  // the next apply builds its jobs with it
+      return ASP_OK;
+    }
+  return fail(ASP_ERR_INVALID, "not a launch shape of this handle at this nrhs");
+}
+
 }  // namespace asp
 
 using namespace asp;
 
 extern "C" {
+
+int asp_set_solve_shape(asp_handle* hd, int nrhs, int kind, int cap, int variant) {
+  if (!hd) return fail(ASP_ERR_INVALID, "null handle");
+  Handle& H = hd->h;
+  if (nrhs < 1 || nrhs > H.prm.max_rhs) return fail(ASP_ERR_INVALID, "nrhs out of range");
+  return set_solve_shape(H, nrhs, kind, cap, variant);
+}
 
 int asp_autotune(asp_handle* hd, int nrhs, int* choice_host, double* ms_host, void* stream) {
   if (!hd) return fail(ASP_ERR_INVALID, "null handle");

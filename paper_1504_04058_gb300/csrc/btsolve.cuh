@@ -393,6 +393,12 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
       }
     }
 
+    // per-thread ring slot of tile entry (a, c): the TC columns in adjacent
+    // pairs, so that one 16-byte copy fills both entries of a pair
+    auto sidx = [&](int a, int c) -> size_t {
+      if constexpr (TC == 1) return (size_t)a * NT + tid;
+      else return ((size_t)(a * (TC / 2) + (c >> 1)) * NT + tid) * 2 + (c & 1);
+    };
     auto load_step = [&](int q2) {
       if (q2 < L) {
         const int kk = blk(q2);
@@ -405,7 +411,7 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
               const C* src = in_base[a] + (long long)kk * in_step;
 #pragma unroll
               for (int c = 0; c < TC; ++c)
-                if (rhs_of(c) < nr) cp_async<CB>(slot + (size_t)(a * TC + c) * NT + tid, src + rhs_of(c));
+                if (rhs_of(c) < nr) cp_async<CB>(slot + sidx(a, c), src + rhs_of(c));
             }
           }
         } else if (kk >= k0 && kk <= n - 3) {
@@ -413,8 +419,16 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
           for (int a = 0; a < TR; ++a) {
             if (!row_ok[a]) continue;
             const C* src = zrow[a] + (long long)kk * zstep;
+            if constexpr (TC >= 2 && CB == 8) {
+              // a pair's two columns are adjacent in the scratch slot (16-byte
+              // aligned: the slot, the row stride NR and the pair's first column
+              // are even), so half the copies
 #pragma unroll
-            for (int c = 0; c < TC; ++c) cp_async<CB>(slot + (size_t)(a * TC + c) * NT + tid, src + rhs_of(c));
+              for (int c = 0; c < TC; c += 2) cp_async<16>(slot + sidx(a, c), src + rhs_of(c));
+            } else {
+#pragma unroll
+              for (int c = 0; c < TC; ++c) cp_async<CB>(slot + sidx(a, c), src + rhs_of(c));
+            }
           }
         }
       }
@@ -458,7 +472,7 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
               if (CLS == CLS_TMAP) {
                 if (k == rhs0 + rhs_of(c)) g = neg_ih2;
               } else {
-                g = slot[(size_t)(a * TC + c) * NT + tid];
+                g = slot[sidx(a, c)];
                 if (CLS == CLS_FILL) g = cmul(neg_ih2, g);
               }
             }
@@ -558,7 +572,7 @@ __global__ void __launch_bounds__(MAXT, MINB) btsolve_kernel(SolveParams P, Geom
 #pragma unroll
           for (int c = 0; c < TC; ++c) {
             C z = czero<R>();
-            if (k >= k0) z = (k == n - 2) ? zkeep[a][c] : slot[(size_t)(a * TC + c) * NT + tid];
+            if (k >= k0) z = (k == n - 2) ? zkeep[a][c] : slot[sidx(a, c)];
             x[c] = z;
             cfms(x[c], c_k, acc[a][c]);
           }

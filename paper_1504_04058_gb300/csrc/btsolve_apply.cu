@@ -8,8 +8,9 @@ namespace asp {
 // (PKT true, ASP_PREC_C64_SYM: four producer warps more, so the thread bounds
 // grow by 128 and the register bounds are relaxed).  Variant 0 is each
 // capacity's default tile; variant 1 the alternative the autotuner also times
-// (asp_autotune): other rows per thread at 32 right-hand sides, two lanes
-// instead of four splitting each block's columns at 1.
+// (asp_autotune): other rows per thread at 32 right-hand sides, eight lanes
+// instead of four splitting each block's columns at 1 (shorter inner loops,
+// one more shuffle round).
 template <bool PKT>
 cudaError_t apply_c64(Handle& H, const SolveParams& P, int cls, int cap, int variant, int wmax, cudaStream_t s) {
   using namespace bts;
@@ -17,10 +18,10 @@ cudaError_t apply_c64(Handle& H, const SolveParams& P, int cls, int cap, int var
   if (variant == 1) {
     if (cls == CLS_EMBED) {
       if (cap == 32) return run<float, 2, 2, 8, 2, CLS_EMBED, 512 + X, 1, 3, 1, PKT>(H, P, wmax, s);
-      if (cap == 1) return run<float, 2, 1, 1, 1, CLS_EMBED, 512, 1, 6, 2, PKT>(H, P, wmax, s);
+      if (cap == 1) return run<float, 2, 1, 1, 1, CLS_EMBED, 512, 1, 6, 8, PKT>(H, P, wmax, s);
     } else {
       if (cap == 32) return run<float, 4, 2, 8, 2, CLS_FILL, 256 + X, PKT ? 1 : 2, 3, 1, PKT>(H, P, wmax, s);
-      if (cap == 1) return run<float, 2, 1, 1, 1, CLS_FILL, 512, 1, 6, 2, PKT>(H, P, wmax, s);
+      if (cap == 1) return run<float, 2, 1, 1, 1, CLS_FILL, 512, 1, 6, 8, PKT>(H, P, wmax, s);
     }
     return cudaErrorInvalidValue;
   }

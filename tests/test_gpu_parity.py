@@ -267,6 +267,35 @@ def test_fgmres_with_arbitrary_layer_widths_matches_oracle():
         assert abs(info[r]["iterations"] - int(itso[r])) <= 1, (info[r], itso[r])
 
 
+@pytest.mark.parametrize("precision,tol", [("c64", 2e-4), ("c64sym", 2e-4)])
+def test_every_layer_solve_shape_matches_oracle(precision, tol):
+    """Each launch shape asp_autotune can pick (default and alternative tiles,
+    the next smaller column capacity), fixed by asp_set_solve_shape for the
+    M-solves and the fills in turn, at 33 and at 1 right-hand side, on the
+    headline's layer widths (PML 20, b = 4: M-layers 42 wide, R/L layers 23)."""
+    import paper_1504_04058_gb300 as asp
+    from paper_1504_04058_gb300 import _lib
+    P = W.small_problem(2, 127, 16 * math.pi, 20, 4, "layered", nrhs=33)
+    h = handle(P, precision)
+    zo = oracle_pc(P).apply(P.f)
+    shapes = {33: [(32, 0), (32, 1), (16, 0)], 1: [(1, 0), (1, 1), (2, 0)]}
+    for nr, cands in shapes.items():
+        f = P.f[..., :nr]
+        for kind in ("embed", "fill"):
+            for cap, var in cands:
+                if nr == 1 and (cap, var) == (2, 0):  # not a candidate at 1 right-hand side
+                    with pytest.raises(_lib.AspError):
+                        h.set_solve_shape(nr, kind, cap, var)
+                    continue
+                h.set_solve_shape(nr, kind, cap, var)
+                z = host(h.apply_preconditioner(dev(f)))
+                e = emax(z, zo[..., :nr])
+                assert e <= tol, (nr, kind, cap, var, e)
+    with pytest.raises(_lib.AspError):
+        h.set_solve_shape(33, "embed", 8, 0)
+    h.destroy()
+
+
 @pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4)])
 def test_autotuned_apply_matches_oracle(precision, tol):
     """asp_autotune times the candidate launch shapes of the layer solves on the
