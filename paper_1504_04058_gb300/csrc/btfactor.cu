@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(ROWS * kColGroups)
   __shared__ int piv_row[64];
   __shared__ int col_of_row[64];
   const int tid = threadIdx.x, lane = tid & 31;
+  constexpr int kCols = ROWS / kColGroups;  // most columns a thread owns (w <= ROWS)
   const int i = tid % ROWS;  // my row
   const int jh = tid / ROWS; // my first column (then every kColGroups-th)
   const bool row_ok = i < w;
@@ -76,7 +77,10 @@ __global__ void __launch_bounds__(ROWS * kColGroups)
     if (row_ok) {
       const C diag = cadd(cadd(dg[i], F.cd[k]), cmake<R>(F.k2[(long long)(S.lo - 1 + i) * n + k], R(0)));
       const int pr = (k > 0) ? piv_row[i] : 0;
-      for (int j = jh; j < w; j += kColGroups) {
+#pragma unroll
+      for (int u = 0; u < kCols; ++u) {
+        const int j = jh + u * kColGroups;
+        if (j >= w) break;
         C t = czero<R>();
         if (j == i) t = diag;
         else if (j == i + 1) t = up[i];
@@ -138,17 +142,25 @@ __global__ void __launch_bounds__(ROWS * kColGroups)
         const C* srow = src + i * ld;
         C* drow = dst + i * ld;
         const C f = cmul(srow[c], inv);
+        // fully unrolled over the thread's (at most ROWS / 4) columns, so that
+        // every load of the row update can be issued before its products
         if (i != r) {
-#pragma unroll 2
-          for (int j = jh; j < w; j += kColGroups) {
-            C v = srow[j];
-            cfms(v, f, prow[j]);
-            drow[j] = v;
+#pragma unroll
+          for (int u = 0; u < kCols; ++u) {
+            const int j = jh + u * kColGroups;
+            if (j < w) {
+              C v = srow[j];
+              cfms(v, f, prow[j]);
+              drow[j] = v;
+            }
           }
           if (jh == (c & (kColGroups - 1))) drow[c] = cmake<R>(-f.x, -f.y);
         } else {
-#pragma unroll 2
-          for (int j = jh; j < w; j += kColGroups) drow[j] = cmul(prow[j], inv);
+#pragma unroll
+          for (int u = 0; u < kCols; ++u) {
+            const int j = jh + u * kColGroups;
+            if (j < w) drow[j] = cmul(prow[j], inv);
+          }
           if (jh == (c & (kColGroups - 1))) drow[c] = inv;
         }
       }
