@@ -30,6 +30,11 @@
  *        keeps (the velocity field).  The library owns the device memory it
  *        allocates for a handle (factors, transfer maps, Krylov workspace) and
  *        frees it in asp_destroy.
+ * Threads.  One handle is used by one thread at a time (calls on the same
+ *        handle are not synchronized against each other); different handles may
+ *        be used concurrently from different threads, each on its own stream
+ *        (the serving loop does so).  Library-wide state (job-list caches, kernel
+ *        attributes, the test hook) is synchronized internally.
  * Errors.  Every int-returning call returns ASP_OK (0) or a negative ASP_ERR_*
  *        code; asp_error_string() names it and asp_last_error_detail() gives a
  *        one-line description of the most recent failure on the calling thread.
